@@ -1,0 +1,291 @@
+"""Pins of the FP64 oracle's Chebyshev, coarsening, multigrid and force parts
+(Secs. 3.1-3.4 of arXiv:2103.05034, and the HMC force derived from Sec. 6's
+action) against closed forms, dense linear algebra, identities, finite
+differences and the paper's printed counts (tests/golden/paper_counts.json)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cheby, coarse, dwf, force, krylov, mg
+
+M5 = 1.8
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_counts.json")))
+
+
+# ------------------------------------------------------------ Chebyshev scalars
+def test_chebyshev_recurrence_matches_trig_forms():
+    x = np.linspace(-1, 1, 101)
+    for n in (0, 1, 2, 7, 60):
+        assert np.allclose(cheby.cheb_T(n, x), np.cos(n * np.arccos(x)), atol=1e-12)
+    xo = np.array([1.01, 1.5, 3.0, -1.2])
+    for n in (3, 12, 40):
+        want = np.sign(xo) ** n * np.cosh(n * np.arccosh(np.abs(xo)))
+        assert np.allclose(cheby.cheb_T(n, xo), want, rtol=1e-10)
+
+
+def test_smoother_coeff_last_vanishes_and_interpolates():
+    for a, b, N in [(0.5, 60.0, 12), (0.1, 10.0, 7)]:
+        c = cheby.smoother_coeffs(a, b, N)
+        assert abs(c[N]) < 1e-14 * np.max(np.abs(c))
+        k = np.arange(N)
+        nodes = a + (b - a) * (np.cos(np.pi * (k + 0.5) / N) + 1) / 2
+        assert np.allclose(cheby.smoother_scalar(nodes, a, b, N), 1.0 / nodes, rtol=1e-12)
+
+
+def test_filter_gain_matches_paper_order_of_magnitude():
+    g = GOLD["filter_gain"]
+    x0 = 2 * (0.0 - g["lambda_lo"]) / (g["lambda_max"] - g["lambda_lo"]) - 1
+    gain = abs(cheby.cheb_T(g["m"], np.array([x0]))[0])
+    assert np.log10(gain) == pytest.approx(np.log10(g["gain_order_of_magnitude"]), abs=0.5)
+
+
+# ------------------------------------------------------------ operator level, dense tiny system
+@pytest.fixture(scope="module")
+def tiny():
+    L = (2, 2, 2, 2)
+    Ls = 4
+    mf = 0.05
+    U = synth.random_gauge(L, 0.7, 31)
+    shape = (2, 2, 2, 2, Ls, 4, 3)
+    n = int(np.prod(shape))
+    D = np.zeros((n, n), complex)
+    G = np.zeros((n, n), complex)
+    for i in range(n):
+        e = np.zeros(n, complex)
+        e[i] = 1
+        D[:, i] = dwf.ddw(U, e.reshape(shape), M5, mf).ravel()
+        G[:, i] = dwf.gamma5_r5(e.reshape(shape)).ravel()
+    return L, Ls, mf, U, shape, D, G
+
+
+def test_filter_and_smoother_vs_eigendecomposition(tiny):
+    L, Ls, mf, U, shape, D, G = tiny
+    A = D.conj().T @ D
+    lam, V = np.linalg.eigh(A)
+    v = synth.gaussian_spinor(L, Ls, 3)
+    appA = lambda w: dwf.mdagm(U, w, M5, mf)
+    lo, hi, order = 0.3, 70.0, 9
+    got = cheby.cheby_filter(appA, v, order, lo, hi).ravel()
+    xl = 2 * (lam - lo) / (hi - lo) - 1
+    want = V @ (cheby.cheb_T(order, xl) * (V.conj().T @ v.ravel()))
+    assert np.allclose(got, want, rtol=1e-10, atol=1e-10)
+    # smoother: p(M^dag M) M^dag with M = H (hermitian)
+    H = G @ D
+    appH = lambda w: dwf.hdw(U, w, M5, mf)
+    z, nA = cheby.smoother_apply(appH, appH, v, 0.5, 60.0, 12)
+    assert nA == 23
+    lamH, VH = np.linalg.eigh(H)
+    want = VH @ (cheby.smoother_scalar(lamH ** 2, 0.5, 60.0, 12) * lamH * (VH.conj().T @ v.ravel()))
+    assert np.allclose(z.ravel(), want, rtol=1e-10, atol=1e-10)
+
+
+def test_recursive_basis_vs_eigendecomposition_and_cost(tiny):
+    L, Ls, mf, U, shape, D, G = tiny
+    A = D.conj().T @ D
+    lam, V = np.linalg.eigh(A)
+    eta = synth.gaussian_spinor(L, Ls, 4)
+    calls = [0]
+
+    def appA(w):
+        calls[0] += 1
+        return dwf.mdagm(U, w, M5, mf)
+
+    m, delta, nvec, lo, lmax = 7, 3, 4, 0.2, 70.0
+    vecs = cheby.recursive_basis(appA, eta, m, delta, nvec, lo, lmax)
+    assert calls[0] == m + (nvec - 1) * delta
+    pre = cheby.cheb_T(m, 2 * (lam - lo) / (lmax - lo) - 1)
+    c0 = V.conj().T @ eta.ravel()
+    for k, phi in enumerate(vecs):
+        f = pre * cheby.cheb_T(k * delta, 2 * lam / lmax - 1)
+        want = V @ (f * c0)
+        want /= np.linalg.norm(want)
+        assert np.allclose(phi.ravel(), want, atol=1e-10)
+
+
+def test_recursive_cost_model_matches_paper():
+    """Cost m + (n-1) Delta of the recursive filter against the paper's counts and timings."""
+    g = GOLD["recursive_cost"]
+    assert (g["nvec"] - 1) * g["delta"] == g["further_multiplies"]
+    s = GOLD["setup_time_ratio"]
+    cost = lambda n: s["m"] + (n - 1) * s["delta"]
+    model = cost(s["A_filtered"]) / cost(s["B_filtered"])
+    assert model == pytest.approx(s["A_seconds"] / s["B_seconds"], abs=0.02)
+
+
+def test_rbcg_count_convention_matches_paper():
+    g = GOLD["rbcg_matmuls"]
+    for it, mm in zip(g["iterations"], g["full_matmuls"]):
+        assert 4 * it / 2 == mm  # four half-lattice hops = two full matmuls
+    h = GOLD["hdcr_outer"]
+    assert all(mm == 48 * o for o, mm in zip(h["outer"], h["fine_matmuls"]))
+
+
+# ------------------------------------------------------------ coarsening
+def make_basis(U, L, Ls, block, nvec, seed, mf):
+    """Chirality-projected, block-orthonormalised basis from lightly filtered noise."""
+    appA = lambda w: dwf.mdagm(U, w, M5, mf)
+    raw = [cheby.cheby_filter(appA, synth.gaussian_spinor(L, Ls, seed + i), 4, 0.5, 70.0)
+           for i in range(nvec)]
+    half = nvec // 2
+    vecs = [coarse.chiral_project(v, +1) for v in raw[:half]] + \
+           [coarse.chiral_project(v, -1) for v in raw[half:]]
+    return coarse.block_orthonormalise(vecs, block, [list(range(half)), list(range(half, nvec))])
+
+
+@pytest.fixture(scope="module", params=[((4, 4, 4, 4), (2, 2, 2, 2)), ((4, 4, 2, 8), (2, 2, 2, 2))])
+def coarse_case(request):
+    L, block = request.param
+    Ls = 4
+    mf = 0.1
+    U = synth.random_gauge(L, 0.5, 41)
+    basis = make_basis(U, L, Ls, block, 4, 100, mf)
+    return L, Ls, block, mf, U, basis
+
+
+def test_block_orthonormal_and_chiral(coarse_case):
+    L, Ls, block, mf, U, basis = coarse_case
+    nb = len(basis)
+    for j in range(nb):
+        for k in range(nb):
+            ip = coarse.block_inner(basis[j], basis[k], block)
+            assert np.allclose(ip, 1.0 if j == k else 0.0, atol=1e-13)
+    for k, phi in enumerate(basis):
+        sgn = 1 if k < nb // 2 else -1
+        assert np.allclose(dwf.gamma5_r5(phi), sgn * phi, atol=1e-14)
+
+
+def test_coarse_stencil_equals_bruteforce(coarse_case):
+    L, Ls, block, mf, U, basis = coarse_case
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    dense_stencil = coarse.coarse_dense_from_stencil(A)
+    dense_bf = coarse.coarse_dense_bruteforce(U, basis, block, M5, mf)
+    assert np.allclose(dense_stencil, dense_bf, atol=1e-12)
+    # coarse operator of a hermitian H is hermitian; stencil form of it
+    assert np.allclose(dense_bf, dense_bf.conj().T, atol=1e-12)
+    assert np.allclose(A[0], np.conj(np.swapaxes(A[0], -1, -2)), atol=1e-12)
+    for mu in range(4):
+        ax = (3, 2, 1, 0)[mu]
+        fwd = A[1 + 2 * mu]
+        bwd_next = np.roll(A[2 + 2 * mu], -1, axis=ax)
+        assert np.allclose(fwd, np.conj(np.swapaxes(bwd_next, -1, -2)), atol=1e-12)
+
+
+def test_coarse_inherits_gamma5_hermiticity(coarse_case):
+    """D_c = Gamma_5c A satisfies Gamma_5c D_c Gamma_5c = D_c^dag (Sec. 3.4)."""
+    L, Ls, block, mf, U, basis = coarse_case
+    dense = coarse.coarse_dense_bruteforce(U, basis, block, M5, mf)
+    nb = len(basis)
+    nc = dense.shape[0] // nb
+    g5c = np.kron(np.eye(nc), np.diag([1.0] * (nb // 2) + [-1.0] * (nb // 2)))
+    Dc = g5c @ dense
+    assert np.allclose(g5c @ Dc @ g5c, Dc.conj().T, atol=1e-12)
+    # and the restriction commutes with Gamma_5: P^dag Gamma_5 psi = Gamma_5c P^dag psi
+    psi = synth.gaussian_spinor(L, Ls, 77)
+    lhs = coarse.restrict(basis, dwf.gamma5_r5(psi), block)
+    rhs = coarse.restrict(basis, psi, block) * np.array([1.0] * (nb // 2) + [-1.0] * (nb // 2))
+    assert np.allclose(lhs, rhs, atol=1e-12)
+
+
+def test_coarse_apply_and_cgnr(coarse_case):
+    L, Ls, block, mf, U, basis = coarse_case
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    dense = coarse.coarse_dense_bruteforce(U, basis, block, M5, mf)
+    shp = A.shape[1:5] + (len(basis),)
+    v = synth.complex_gaussian(5, shp)
+    assert np.allclose(coarse.coarse_apply(A, v).ravel(), dense @ v.ravel(), atol=1e-12)
+    e, it = coarse.coarse_cgnr(A, v, 1e-12, 2000)
+    assert np.allclose(dense @ e.ravel(), v.ravel(), atol=1e-9 * np.linalg.norm(v))
+
+
+# ------------------------------------------------------------ V(1,1) and the MG solve
+def test_vcycle_identity_dense(tiny):
+    """The sequential x1, x2, x3 update (Eqs. 26-28) equals Eq. (31)'s
+    [S(1 - MQ) + Q + (1 - QM)S + S(MQM - M)S] r0.  Eq. (32) rewrites the last
+    term as + S P_L M S, but S(MQM - M)S = - S P_L M S: the sign is read from
+    Eq. (31), which follows from the sequence."""
+    L, Ls, mf, U, shape, D, G = tiny
+    H = G @ D
+    block = (2, 2, 2, 2)
+    basis = make_basis(U, L, Ls, block, 4, 500, mf)
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    n = H.shape[0]
+    P = np.stack([phi.ravel() for phi in basis], axis=1)  # one coarse site
+    Ac = P.conj().T @ H @ P
+    Q = P @ np.linalg.solve(Ac, P.conj().T)
+    appH = lambda w: dwf.hdw(U, w, M5, mf)
+    S = np.zeros((n, n), complex)
+    for i in range(n):
+        e = np.zeros(n, complex)
+        e[i] = 1
+        S[:, i] = cheby.smoother_apply(appH, appH, e.reshape(shape), 0.5, 60.0, 5)[0].ravel()
+    I = np.eye(n)
+    PL, PR = I - H @ Q, I - Q @ H
+    K = S @ (I - H @ Q) + Q + (I - Q @ H) @ S + S @ (H @ Q @ H - H) @ S
+    assert np.allclose(K, S @ PL + Q + PR @ S - S @ PL @ H @ S, atol=1e-10)
+    r0 = synth.gaussian_spinor(L, Ls, 8)
+    cnt = mg.MGCounter()
+    got = mg.vcycle(appH, r0, basis, A, block, (0.5, 60.0, 5), 1e-14, 5000, cnt)
+    assert np.allclose(got.ravel(), K @ r0.ravel(), rtol=1e-8, atol=1e-8 * np.linalg.norm(r0))
+    assert cnt.fine == 2 * 9 + 2
+
+
+def test_mg_solve_converges_to_dense_solution():
+    L = (4, 4, 4, 4)
+    Ls = 4
+    mf = 0.05
+    block = (2, 2, 2, 2)
+    U = synth.random_gauge(L, 0.5, 51)
+    basis = make_basis(U, L, Ls, block, 8, 600, mf)
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    b = synth.gaussian_spinor(L, Ls, 9)
+    x, it, hist, cnt = mg.mg_solve(U, b, basis, A, block, M5, mf, 1e-10,
+                                   smooth=(0.5, 60.0, 6), coarse_tol=0.02)
+    assert krylov.true_residual(U, x, b, M5, mf) <= 1e-10
+    xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e-7
+
+
+# ------------------------------------------------------------ force
+@pytest.fixture(scope="module")
+def force_case():
+    L = (4, 4, 4, 4)
+    Ls = 4
+    U = synth.random_gauge(L, 0.5, 61)
+    masses = [0.05, 0.3]
+    phis = [dwf.project_parity(synth.gaussian_spinor(L, Ls, 70 + i), L, 0) for i in range(2)]
+    G = force.force(U, phis, masses, M5)
+    return L, Ls, U, masses, phis, G
+
+
+def test_force_is_traceless_antihermitian(force_case):
+    L, Ls, U, masses, phis, G = force_case
+    assert np.allclose(G, -dwf.dagger(G), atol=1e-14)
+    assert np.allclose(np.trace(G, axis1=-2, axis2=-1), 0, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["global", "single_link"])
+def test_force_matches_finite_difference(force_case, kind):
+    L, Ls, U, masses, phis, G = force_case
+    if kind == "global":
+        Q = synth.random_su3_algebra(U.shape[:-2], 81)
+    else:
+        Q = np.zeros_like(U)
+        Q[1, 2, 3, 0, 2] = synth.random_su3_algebra((1,), 82)[0]
+    fd = force.finite_difference(U, phis, masses, M5, Q, 1e-5)
+    an = np.sum(np.trace(np.conj(np.swapaxes(G, -1, -2)) @ Q, axis1=-2, axis2=-1)).real
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3)
+
+
+def test_force_gauge_covariance(force_case):
+    L, Ls, U, masses, phis, G = force_case
+    g = synth.random_gauge_transform(L, 91)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Ug[..., mu, :, :] = g @ U[..., mu, :, :] @ dwf.dagger(dwf.shift(g, mu, +1))
+    phig = [dwf.apply_color(g, p) for p in phis]
+    Gg = force.force(Ug, phig, masses, M5)
+    want = np.einsum("tzyxab,tzyxmbc,tzyxdc->tzyxmad", g, G, g.conj())
+    assert np.allclose(Gg, want, atol=1e-10)
