@@ -1,0 +1,183 @@
+/*
+ * dwfmg.h -- C ABI of the GB300 (sm_103a) domain wall fermion multigrid hot path.
+ *
+ * Operators and algorithms: Boyle & Yamaguchi, "Comparison of Domain Wall
+ * Fermion Multigrid Methods", arXiv:2103.05034.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every call
+ * ---------------------------------------------------------------------------
+ * Lattice.  L[4] = {Lx, Ly, Lz, Lt}, each even; fifth dimension Ls in
+ *   {4, 8, 16, 24}.  Periodic boundaries in all four directions.  A 4D site
+ *   (x,y,z,t) has lexicographic index i4 = x + Lx*(y + Ly*(z + Lz*t)) and
+ *   parity (x+y+z+t) mod 2 (0 = even).  Vh = Lx*Ly*Lz*Lt/2 sites per parity;
+ *   the checkerboard index of a site is i4/2.
+ *
+ * Spin basis.  Chiral: gamma_k = [[0,-i sigma_k],[i sigma_k,0]] (k = x,y,z),
+ *   gamma_t = [[0,1],[1,0]], gamma_5 = gamma_x gamma_y gamma_z gamma_t =
+ *   diag(1,1,-1,-1); P_+- = (1 +- gamma_5)/2.
+ *
+ * Gauge field (input to dwf_ctx_create).  complex128, [T][Z][Y][X][mu][3][3],
+ *   mu = 0..3 is x,y,z,t, row-major colour matrices; U_mu(x) transports from
+ *   x+mu to x as in Eq. (2).  Host or device memory.
+ *
+ * Fermion fields (every other buffer).  Device memory unless a call says
+ *   otherwise.  Complex numbers are (re, im) pairs of the element type of the
+ *   precision argument:
+ *     DWF_F64  double   (16 bytes per complex)
+ *     DWF_F32  float    (8 bytes per complex)
+ *     DWF_F16S half     (4 bytes per complex; arithmetic is FP32)
+ *   A half field (one parity) is [Vh][spin 4][colour 3][Ls]: the fifth
+ *   dimension is innermost.  A full field is [parity 2][Vh][4][3][Ls] (the
+ *   even half first).  A batch of nrhs fields is nrhs such fields back to
+ *   back.  Buffers must be 16-byte aligned and must not overlap unless a call
+ *   says otherwise.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *   are asynchronous on that stream unless they return results to the host
+ *   (solvers, power method, setup), which synchronise once before returning.
+ *
+ * Ownership.  The caller owns every field buffer.  The library owns
+ *   dwf_ctx, dwf_coarse and dwf_mg objects and their workspaces; the matching
+ *   *_destroy call frees them.
+ *
+ * Errors.  Every call returns DWF_OK (0) or a negative status.  The library
+ *   never exits, aborts or traps; dwf_last_error() describes the last failure
+ *   of a context.  A CUDA error leaves the context usable only if the CUDA
+ *   context itself is still usable.
+ */
+#ifndef DWFMG_H
+#define DWFMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DWF_OK 0
+#define DWF_EINVAL (-1)   /* bad argument: size, pointer, alignment, precision */
+#define DWF_ENOMEM (-2)   /* device or host allocation failed */
+#define DWF_ENOCONV (-3)  /* solver hit maxiter before the tolerance */
+#define DWF_ENAN (-4)     /* NaN or Inf met in a solver or filter */
+#define DWF_ECUDA (-5)    /* a CUDA runtime call failed */
+#define DWF_ETIMEOUT (-6) /* a bounded device wait gave up */
+#define DWF_ERANGE (-7)   /* filter overflow: the spectrum is not inside [lo, hi] */
+
+#define DWF_F64 0
+#define DWF_F32 1
+#define DWF_F16S 2
+
+#define DWF_EVEN 0
+#define DWF_ODD 1
+
+/* Solver precision policies for rbcg_solve. */
+#define DWF_SOLVE_F64 0       /* every operation in FP64 */
+#define DWF_SOLVE_MIXED_F32 1 /* FP32 inner CG, FP64 reliable updates */
+#define DWF_SOLVE_MIXED_F16 2 /* FP16-storage inner CG, FP64 reliable updates */
+
+typedef struct dwf_ctx dwf_ctx;
+typedef struct dwf_coarse dwf_coarse;
+typedef struct dwf_mg dwf_mg;
+
+/* Statistics returned by the solvers.  "Matmuls" are counted in the paper's
+ * unit: one full-lattice application of D_DW (or H_DW); a red-black CG
+ * iteration (four half-lattice hopping terms) counts two (Sec. 5.1). */
+typedef struct dwf_solve_stats {
+  int iterations;            /* CG iterations, or outer GCR iterations (mg_solve) */
+  int reliable_updates;      /* FP64 residual recomputations (mixed policies) */
+  int coarse_iterations;     /* total coarse CG iterations (mg_solve) */
+  int status;                /* same as the return value */
+  double fine_matmuls;       /* full-lattice D_DW/H_DW applications, paper units */
+  double true_residual;      /* ||b - D_DW x|| / ||b|| in FP64 at exit */
+  double seconds;            /* wall time of the call (host clock) */
+  double setup_seconds;      /* mg_setup phases: subspace filter */
+  double coarse_op_seconds;  /* mg_setup phases: coarse operator build */
+} dwf_solve_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context for an L[0]xL[1]xL[2]xL[3]xLs Shamir DWF operator with
+ * domain-wall height M5 (Eq. 4-5; the paper leaves M5 open, the workloads use
+ * 1.8).  `gauge` is the complex128 link field described above, host or
+ * device; the context keeps parity-split copies of it in FP64, FP32 and FP16
+ * (forward links U_mu(x) and backward links U_mu(x-mu)^dag stored side by
+ * side per site).  Returns DWF_EINVAL for odd extents or unsupported Ls,
+ * DWF_ENOMEM if the copies do not fit.  Synchronises `stream`. */
+int dwf_ctx_create(dwf_ctx** ctx, const int L[4], int Ls, double M5,
+                   const void* gauge, void* stream);
+int dwf_ctx_destroy(dwf_ctx* ctx);
+const char* dwf_last_error(const dwf_ctx* ctx);
+/* Number of sites per parity (Vh) and the byte size of one half field of the
+ * given precision, for allocation by the caller. */
+int64_t dwf_half_sites(const dwf_ctx* ctx);
+int64_t dwf_half_bytes(const dwf_ctx* ctx, int prec);
+
+/* ------------------------------------------------------------------ operators */
+
+/* Wilson hopping term, Eq. (2), between parities: out (parity out_parity) =
+ * D_hop in (parity 1-out_parity), applied on every s-slice with the same
+ * links.  dagger=1 applies D_hop^dag (= gamma_5 D_hop gamma_5: the spin
+ * projectors (1 -+ gamma_mu) swap).  nrhs half fields in, nrhs out. */
+int dwf_dhop(dwf_ctx* ctx, void* out, const void* in, int out_parity, int dagger,
+             int prec, int nrhs, void* stream);
+
+/* Site-local part of D_DW, Eq. (4) without the hopping term of Eq. (5):
+ * (M psi)_s = (5-M5) psi_s - P_- psi_{s+1} - P_+ psi_{s-1}, with mf P_+
+ * psi_{Ls-1} at s = 0 and mf P_- psi_0 at s = Ls-1.  M_ee = M_oo = M.
+ * dwf_mooee applies M (or M^dag), dwf_mooee_inv applies M^-1 (or M^-dag),
+ * both on nrhs half fields; out may equal in. */
+int dwf_mooee(dwf_ctx* ctx, void* out, const void* in, double mf, int dagger,
+              int prec, int nrhs, void* stream);
+int dwf_mooee_inv(dwf_ctx* ctx, void* out, const void* in, double mf, int dagger,
+                  int prec, int nrhs, void* stream);
+
+/* Red-black Schur operator of Sec. 5.1 (Table 5, first prec-CGNR row):
+ * M_pc = M_ee - M_eo M_oo^-1 M_oe with M_eo = -1/2 D_hop(even<-odd).
+ * dwf_mpc applies M_pc (or M_pc^dag) and dwf_mpcdag_mpc applies
+ * M_pc^dag M_pc to nrhs even half fields.  Odd-parity temporaries come from
+ * the context's workspace. */
+int dwf_mpc(dwf_ctx* ctx, void* out, const void* in, double mf, int dagger,
+            int prec, int nrhs, void* stream);
+int dwf_mpcdag_mpc(dwf_ctx* ctx, void* out, const void* in, double mf, int prec,
+                   int nrhs, void* stream);
+
+/* Full-lattice D_DW (Eq. 4), its adjoint, and H_DW = Gamma_5 D_DW (Eq. 6,
+ * Gamma_5 = gamma_5 R_5) on nrhs full fields. */
+int dwf_ddw(dwf_ctx* ctx, void* out, const void* in, double mf, int dagger,
+            int prec, int nrhs, void* stream);
+int dwf_hdw(dwf_ctx* ctx, void* out, const void* in, double mf, int prec,
+            int nrhs, void* stream);
+
+/* ------------------------------------------------------------------ BLAS-1 */
+
+/* Global reductions with FP64 accumulation over n complex numbers of the
+ * given precision: *result = sum |a|^2, or (re, im) of sum conj(a) b.
+ * `result` is host memory; the call synchronises `stream`. */
+int dwf_norm2(dwf_ctx* ctx, double* result, const void* a, int64_t n, int prec, void* stream);
+int dwf_cdot(dwf_ctx* ctx, double* result2, const void* a, const void* b, int64_t n,
+             int prec, void* stream);
+
+/* ------------------------------------------------------------------ solvers */
+
+/* Red-black preconditioned CGNR (Sec. 5.1): solve D_DW x = b for a full
+ * field b (FP64, host or device), writing the full FP64 solution x (same
+ * memory kind as b).  Prepares b'_e = b_e - M_eo M_oo^-1 b_o, runs CG on
+ * M_pc^dag M_pc x_e = M_pc^dag b'_e and reconstructs x_o = M_oo^-1 (b_o -
+ * M_oe x_e).  Stops when the FP64 true residual ||b - D_DW x|| / ||b|| <= tol
+ * (returned in stats->true_residual), or returns DWF_ENOCONV after maxiter
+ * CG iterations.  policy is one of DWF_SOLVE_*.  stats may be NULL. */
+int rbcg_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int maxiter,
+               int policy, dwf_solve_stats* stats, void* stream);
+
+/* Power method estimate of the largest eigenvalue of D_DW^dag D_DW (Sec. 3.4),
+ * `iters` iterations from the FP64 full field v0 (device).  *lmax on host. */
+int dwf_power_max(dwf_ctx* ctx, double* lmax, const void* v0, double mf, int iters,
+                  void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWFMG_H */

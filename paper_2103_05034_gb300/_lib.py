@@ -1,0 +1,93 @@
+"""ctypes loader for libdwfmg.so (the C ABI declared in include/dwfmg.h).
+
+Loading fails loudly: there is no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdwfmg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "dwfmg.h")
+
+_lib = None
+
+DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ENOCONV, DWF_ENAN, DWF_ECUDA, DWF_ETIMEOUT, DWF_ERANGE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+F64, F32, F16S = 0, 1, 2
+SOLVE_F64, SOLVE_MIXED_F32, SOLVE_MIXED_F16 = 0, 1, 2
+STATUS_NAMES = {0: "DWF_OK", -1: "DWF_EINVAL", -2: "DWF_ENOMEM", -3: "DWF_ENOCONV",
+                -4: "DWF_ENAN", -5: "DWF_ECUDA", -6: "DWF_ETIMEOUT", -7: "DWF_ERANGE"}
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("reliable_updates", C.c_int),
+                ("coarse_iterations", C.c_int), ("status", C.c_int),
+                ("fine_matmuls", C.c_double), ("true_residual", C.c_double),
+                ("seconds", C.c_double), ("setup_seconds", C.c_double),
+                ("coarse_op_seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+_SIGS = {
+    "dwf_ctx_create": (I, [C.POINTER(P), C.POINTER(C.c_int), I, D, P, P]),
+    "dwf_ctx_destroy": (I, [P]),
+    "dwf_last_error": (C.c_char_p, [P]),
+    "dwf_half_sites": (I64, [P]),
+    "dwf_half_bytes": (I64, [P, I]),
+    "dwf_dhop": (I, [P, P, P, I, I, I, I, P]),
+    "dwf_mooee": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_mooee_inv": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_mpc": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_mpcdag_mpc": (I, [P, P, P, D, I, I, P]),
+    "dwf_ddw": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_hdw": (I, [P, P, P, D, I, I, P]),
+    "dwf_norm2": (I, [P, C.POINTER(D), P, I64, I, P]),
+    "dwf_cdot": (I, [P, C.POINTER(D), P, P, I64, I, P]),
+    "rbcg_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
+    "dwf_power_max": (I, [P, C.POINTER(D), P, D, I, P]),
+}
+
+
+def header_functions():
+    """Names of the functions declared in include/dwfmg.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                       txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "defined")))
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class DWFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(code, ctx=None):
+    if code != DWF_OK:
+        msg = lib().dwf_last_error(ctx).decode() if ctx else ""
+        raise DWFError(code, msg)
+    return code

@@ -1,0 +1,771 @@
+// C ABI: context, operators and the red-black CG solver (arXiv:2103.05034,
+// Sec. 2 and Sec. 5.1).  Every step of the path runs in this library's
+// kernels; the host only sequences launches and reads back scalars.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+
+#include "dhop_impl.cuh"
+#include "dwf_internal.cuh"
+
+// ------------------------------------------------------------------ errors
+int dwf_fail(dwf_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int dwf_cuda_check(dwf_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+                  ") in " + where;
+  return dwf_fail(c, DWF_ECUDA, m);
+}
+
+extern "C" const char* dwf_last_error(const dwf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+size_t dwf_complex_bytes(int prec) {
+  switch (prec) {
+    case DWF_F64:
+      return 16;
+    case DWF_F32:
+      return 8;
+    case DWF_F16S:
+      return 4;
+    default:
+      return 0;
+  }
+}
+
+bool dwf_is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void* dwf_workspace(dwf_ctx* c, int slot, size_t bytes) {
+  if (slot < 0 || slot >= DWF_NWS) return nullptr;
+  if (c->ws_bytes[slot] >= bytes && c->ws[slot]) return c->ws[slot];
+  if (c->ws[slot]) cudaFree(c->ws[slot]);
+  c->ws[slot] = nullptr;
+  c->ws_bytes[slot] = 0;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c->ws[slot] = p;
+  c->ws_bytes[slot] = bytes;
+  return p;
+}
+
+int dwf_reserve_partials(dwf_ctx* c, size_t n) {
+  if (c->partials_n >= n) return DWF_OK;
+  if (c->partials) cudaFree(c->partials);
+  c->partials = nullptr;
+  c->partials_n = 0;
+  if (cudaMalloc(&c->partials, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return dwf_fail(c, DWF_ENOMEM, "cannot allocate reduction partials");
+  }
+  c->partials_n = n;
+  return DWF_OK;
+}
+
+// ------------------------------------------------------------------ links
+// Canonical complex128 [T][Z][Y][X][mu][3][3] -> per output parity p
+// [Vh][8][3][3]: slot 2mu = U_mu(x), slot 2mu+1 = U_mu(x-mu)^dag.
+__global__ void k_build_links(const double2* __restrict__ U, double2* l64, float2* l32, int L0, int L1,
+                              int L2, int L3, int parity) {
+  const int Lxh = L0 / 2;
+  const long long Vh = (long long)L0 * L1 * L2 * L3 / 2;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= Vh * 8) return;
+  const int h = (int)(gid / 8), slot = (int)(gid % 8);
+  const int mu = slot / 2, bwd = slot & 1;
+  int rem = h / Lxh;
+  const int xh = h - rem * Lxh;
+  const int y = rem % L1;
+  rem /= L1;
+  const int z = rem % L2;
+  const int t = rem / L2;
+  int c[4] = {2 * xh + ((y + z + t + parity) & 1), y, z, t};
+  const int Ld[4] = {L0, L1, L2, L3};
+  if (bwd) c[mu] = (c[mu] == 0) ? Ld[mu] - 1 : c[mu] - 1;
+  const long long lex = c[0] + (long long)L0 * (c[1] + (long long)L1 * (c[2] + (long long)L2 * c[3]));
+  const double2* src = U + (lex * 4 + mu) * 9;
+  double2* d64 = l64 + gid * 9;
+  float2* d32 = l32 + gid * 9;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      double2 v = bwd ? make_double2(src[b * 3 + a].x, -src[b * 3 + a].y) : src[a * 3 + b];
+      d64[a * 3 + b] = v;
+      d32[a * 3 + b] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+extern "C" int dwf_ctx_create(dwf_ctx** out, const int L[4], int Ls, double M5, const void* gauge,
+                              void* stream) {
+  if (!out || !L || !gauge) return DWF_EINVAL;
+  *out = nullptr;
+  for (int m = 0; m < 4; m++)
+    if (L[m] < 2 || (L[m] & 1)) return DWF_EINVAL;
+  if (Ls != 4 && Ls != 8 && Ls != 16 && Ls != 24) return DWF_EINVAL;
+  const long long V4 = (long long)L[0] * L[1] * L[2] * L[3];
+  if (V4 / 2 * 12LL * Ls >= (1LL << 40) || V4 / 2 >= (1LL << 31) / 12) return DWF_EINVAL;
+  dwf_ctx* c = new (std::nothrow) dwf_ctx();
+  if (!c) return DWF_ENOMEM;
+  for (int m = 0; m < 4; m++) c->g.L[m] = L[m];
+  c->g.Lxh = L[0] / 2;
+  c->g.Vh = V4 / 2;
+  c->g.Ls = Ls;
+  c->M5 = M5;
+  cudaGetDevice(&c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t glinks = (size_t)V4 * 4 * 9;
+  const void* Ud = gauge;
+  void* tmp = nullptr;
+  int rc = DWF_OK;
+  if (!dwf_is_device_ptr(gauge)) {
+    if (cudaMalloc(&tmp, glinks * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return DWF_ENOMEM;
+    }
+    cudaMemcpyAsync(tmp, gauge, glinks * sizeof(double2), cudaMemcpyHostToDevice, st);
+    Ud = tmp;
+  }
+  for (int p = 0; p < 2 && rc == DWF_OK; p++) {
+    if (cudaMalloc(&c->links64[p], (size_t)c->g.Vh * 72 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->links32[p], (size_t)c->g.Vh * 72 * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = DWF_ENOMEM;
+      break;
+    }
+    const long long n = c->g.Vh * 8;
+    k_build_links<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2*)Ud, c->links64[p],
+                                                                c->links32[p], L[0], L[1], L[2], L[3], p);
+  }
+  if (rc == DWF_OK) {
+    if (cudaMalloc(&c->dscal, S_NSCAL * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->hscal, S_NSCAL * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = DWF_ENOMEM;
+    }
+  }
+  if (rc == DWF_OK) rc = dwf_reserve_partials(c, 1 << 16);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (tmp) cudaFree(tmp);
+  if (rc == DWF_OK && e != cudaSuccess) rc = DWF_ECUDA;
+  if (rc != DWF_OK) {
+    dwf_ctx_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DWF_OK;
+}
+
+extern "C" int dwf_ctx_destroy(dwf_ctx* c) {
+  if (!c) return DWF_OK;
+  for (int p = 0; p < 2; p++) {
+    if (c->links64[p]) cudaFree(c->links64[p]);
+    if (c->links32[p]) cudaFree(c->links32[p]);
+  }
+  for (int i = 0; i < DWF_NWS; i++)
+    if (c->ws[i]) cudaFree(c->ws[i]);
+  if (c->partials) cudaFree(c->partials);
+  if (c->dscal) cudaFree(c->dscal);
+  if (c->hscal) cudaFreeHost(c->hscal);
+  delete c;
+  return DWF_OK;
+}
+
+extern "C" int64_t dwf_half_sites(const dwf_ctx* c) { return c ? c->g.Vh : 0; }
+extern "C" int64_t dwf_half_bytes(const dwf_ctx* c, int prec) {
+  return c ? c->g.Vh * 12 * c->g.Ls * (int64_t)dwf_complex_bytes(prec) : 0;
+}
+
+static int64_t half_elems(const dwf_ctx* c) { return c->g.Vh * 12 * c->g.Ls; }
+
+// ------------------------------------------------------------------ launchers
+static void fill_fifth(const dwf_ctx* c, dwfk::HopParams& hp, const double* mf, int nrhs) {
+  const double d = 5.0 - c->M5;
+  hp.d = d;
+  for (int r = 0; r < nrhs && r < DWF_MAX_RHS; r++) {
+    const double m = mf ? mf[r] : 0.0;
+    hp.m[r] = m;
+    hp.kappa[r] = 1.0 / (1.0 + m * pow(d, -(double)c->g.Ls));
+    hp.dls1[r] = pow(d, 1.0 - (double)c->g.Ls);
+  }
+}
+
+int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* nblocks) {
+  if (h.nrhs < 1 || h.nrhs > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "nrhs out of range");
+  dwfk::HopParams hp;
+  memset(&hp, 0, sizeof(hp));
+  hp.out = h.out;
+  hp.in = h.in;
+  hp.aux = h.aux;
+  const int po = h.out_parity;
+  hp.links = (prec == DWF_F64) ? (const void*)c->links64[po] : (const void*)c->links32[po];
+  hp.L0 = c->g.L[0];
+  hp.L1 = c->g.L[1];
+  hp.L2 = c->g.L[2];
+  hp.L3 = c->g.L[3];
+  hp.Lxh = c->g.Lxh;
+  hp.Vh = (int)c->g.Vh;
+  hp.out_parity = po;
+  hp.sg = h.dagger ? -1.f : 1.f;
+  hp.alpha = h.alpha;
+  hp.aux_mode = h.aux_mode;
+  hp.inv_mode = h.inv_mode;
+  hp.g5r5 = h.g5r5;
+  hp.reduce = h.reduce;
+  hp.rhs_stride = h.rhs_stride ? h.rhs_stride : half_elems(c);
+  fill_fifth(c, hp, h.mf, h.nrhs);
+  if (h.reduce) {
+    const int SB = c->g.Ls >= 16 ? 8 : 128 / c->g.Ls;
+    const size_t nb = (size_t)((c->g.Vh + SB - 1) / SB) * h.nrhs;
+    int rc = dwf_reserve_partials(c, nb);
+    if (rc) return rc;
+  }
+  hp.partials = c->partials;
+  int rc;
+  switch (prec) {
+    case DWF_F64:
+      rc = dwf_launch_hop_f64(hp, c->g.Ls, h.nrhs, st, nblocks);
+      break;
+    case DWF_F32:
+      rc = dwf_launch_hop_f32(hp, c->g.Ls, h.nrhs, st, nblocks);
+      break;
+    case DWF_F16S:
+      rc = dwf_launch_hop_f16(hp, c->g.Ls, h.nrhs, st, nblocks);
+      break;
+    default:
+      return dwf_fail(c, DWF_EINVAL, "bad precision");
+  }
+  if (rc) return dwf_fail(c, rc, "unsupported Ls");
+  return DWF_OK;
+}
+
+int launch_mooee(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int inverse,
+                 int prec, int nrhs, int64_t rhs_stride, cudaStream_t st) {
+  if (nrhs < 1 || nrhs > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "nrhs out of range");
+  dwfk::HopParams hp;
+  memset(&hp, 0, sizeof(hp));
+  hp.Vh = (int)c->g.Vh;
+  fill_fifth(c, hp, mf, nrhs);
+  const long long rs = rhs_stride ? rhs_stride : half_elems(c);
+  int rc;
+  switch (prec) {
+    case DWF_F64:
+      rc = dwf_launch_mooee_f64(out, in, hp, dagger, inverse, c->g.Ls, nrhs, rs, st);
+      break;
+    case DWF_F32:
+      rc = dwf_launch_mooee_f32(out, in, hp, dagger, inverse, c->g.Ls, nrhs, rs, st);
+      break;
+    case DWF_F16S:
+      rc = dwf_launch_mooee_f16(out, in, hp, dagger, inverse, c->g.Ls, nrhs, rs, st);
+      break;
+    default:
+      return dwf_fail(c, DWF_EINVAL, "bad precision");
+  }
+  if (rc) return dwf_fail(c, rc, "unsupported Ls");
+  return DWF_OK;
+}
+
+// ------------------------------------------------------------------ argument checks
+static int check_fields(dwf_ctx* c, int prec, int nrhs, std::initializer_list<const void*> ptrs) {
+  if (!c) return DWF_EINVAL;
+  if (prec < DWF_F64 || prec > DWF_F16S) return dwf_fail(c, DWF_EINVAL, "bad precision");
+  if (nrhs < 1 || nrhs > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "nrhs out of range");
+  for (const void* p : ptrs) {
+    if (!p) return dwf_fail(c, DWF_EINVAL, "null field pointer");
+    if (((uintptr_t)p) & 15) return dwf_fail(c, DWF_EINVAL, "field pointer not 16-byte aligned");
+  }
+  return DWF_OK;
+}
+
+static HopLaunch hop_base(void* out, const void* in, int po, int dag, int nrhs, double alpha) {
+  HopLaunch h;
+  memset(&h, 0, sizeof(h));
+  h.out = out;
+  h.in = in;
+  h.out_parity = po;
+  h.dagger = dag;
+  h.nrhs = nrhs;
+  h.alpha = alpha;
+  return h;
+}
+
+// ------------------------------------------------------------------ operators
+extern "C" int dwf_dhop(dwf_ctx* c, void* out, const void* in, int out_parity, int dagger, int prec,
+                        int nrhs, void* stream) {
+  int rc = check_fields(c, prec, nrhs, {out, in});
+  if (rc) return rc;
+  if (out_parity != 0 && out_parity != 1) return dwf_fail(c, DWF_EINVAL, "bad parity");
+  HopLaunch h = hop_base(out, in, out_parity, dagger ? 1 : 0, nrhs, 1.0);
+  rc = launch_hop(c, h, prec, (cudaStream_t)stream, nullptr);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+static int mooee_common(dwf_ctx* c, void* out, const void* in, double mf, int dagger, int inverse,
+                        int prec, int nrhs, void* stream) {
+  int rc = check_fields(c, prec, nrhs, {out, in});
+  if (rc) return rc;
+  std::vector<double> m(nrhs, mf);
+  rc = launch_mooee(c, out, in, m.data(), dagger ? 1 : 0, inverse, prec, nrhs, 0, (cudaStream_t)stream);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int dwf_mooee(dwf_ctx* c, void* out, const void* in, double mf, int dagger, int prec,
+                         int nrhs, void* stream) {
+  return mooee_common(c, out, in, mf, dagger, 0, prec, nrhs, stream);
+}
+
+extern "C" int dwf_mooee_inv(dwf_ctx* c, void* out, const void* in, double mf, int dagger, int prec,
+                             int nrhs, void* stream) {
+  return mooee_common(c, out, in, mf, dagger, 1, prec, nrhs, stream);
+}
+
+// M_pc (dagger=0) or M_pc^dag (dagger=1) on nrhs even fields, odd temporary tmp.
+// M_pc    = M_ee + 1/2 D_eo M_oo^-1 (-1/2 D_oe)
+// M_pc^dag = M_ee^dag + 1/2 D^dag_eo M_oo^-dag (-1/2 D^dag_oe)
+static int mpc_apply(dwf_ctx* c, void* out, const void* in, void* tmp, const double* mf, int dagger,
+                     int prec, int nrhs, int reduce, cudaStream_t st, int* nparts) {
+  HopLaunch h1 = hop_base(tmp, in, 1, dagger, nrhs, -0.5);
+  h1.inv_mode = dagger ? 2 : 1;
+  h1.mf = mf;
+  int rc = launch_hop(c, h1, prec, st, nullptr);
+  if (rc) return rc;
+  HopLaunch h2 = hop_base(out, tmp, 0, dagger, nrhs, 0.5);
+  h2.aux = in;
+  h2.aux_mode = dagger ? 3 : 2;
+  h2.mf = mf;
+  h2.reduce = reduce;
+  return launch_hop(c, h2, prec, st, nparts);
+}
+
+enum { WS_TMP_O = 0, WS_TMP_E = 1 };
+
+extern "C" int dwf_mpc(dwf_ctx* c, void* out, const void* in, double mf, int dagger, int prec, int nrhs,
+                       void* stream) {
+  int rc = check_fields(c, prec, nrhs, {out, in});
+  if (rc) return rc;
+  if (out == in) return dwf_fail(c, DWF_EINVAL, "out must not alias in");
+  const size_t bytes = (size_t)dwf_half_bytes(c, prec) * nrhs;
+  void* tmp = dwf_workspace(c, WS_TMP_O, bytes);
+  if (!tmp) return dwf_fail(c, DWF_ENOMEM, "workspace");
+  std::vector<double> m(nrhs, mf);
+  rc = mpc_apply(c, out, in, tmp, m.data(), dagger ? 1 : 0, prec, nrhs, 0, (cudaStream_t)stream, nullptr);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int dwf_mpcdag_mpc(dwf_ctx* c, void* out, const void* in, double mf, int prec, int nrhs,
+                              void* stream) {
+  int rc = check_fields(c, prec, nrhs, {out, in});
+  if (rc) return rc;
+  if (out == in) return dwf_fail(c, DWF_EINVAL, "out must not alias in");
+  const size_t bytes = (size_t)dwf_half_bytes(c, prec) * nrhs;
+  void* tmp = dwf_workspace(c, WS_TMP_O, bytes);
+  void* y = dwf_workspace(c, WS_TMP_E, bytes);
+  if (!tmp || !y) return dwf_fail(c, DWF_ENOMEM, "workspace");
+  std::vector<double> m(nrhs, mf);
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = mpc_apply(c, y, in, tmp, m.data(), 0, prec, nrhs, 0, st, nullptr);
+  if (rc) return rc;
+  rc = mpc_apply(c, out, y, tmp, m.data(), 1, prec, nrhs, 0, st, nullptr);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+// Full-lattice D_DW (or D_DW^dag, or H_DW = Gamma_5 D_DW when g5 = 1) of nrhs full fields.
+static int ddw_apply(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int g5,
+                     int prec, int nrhs, cudaStream_t st) {
+  const int64_t he = half_elems(c);
+  const size_t cb = dwf_complex_bytes(prec);
+  for (int po = 0; po < 2; po++) {
+    HopLaunch h = hop_base((char*)out + po * he * cb, (const char*)in + (1 - po) * he * cb, po, dagger,
+                           nrhs, -0.5);
+    h.rhs_stride = 2 * he;
+    h.aux = (const char*)in + po * he * cb;
+    h.aux_mode = dagger ? 3 : 2;
+    h.mf = mf;
+    h.g5r5 = g5;
+    int rc = launch_hop(c, h, prec, st, nullptr);
+    if (rc) return rc;
+  }
+  return DWF_OK;
+}
+
+extern "C" int dwf_ddw(dwf_ctx* c, void* out, const void* in, double mf, int dagger, int prec, int nrhs,
+                       void* stream) {
+  int rc = check_fields(c, prec, nrhs, {out, in});
+  if (rc) return rc;
+  if (out == in) return dwf_fail(c, DWF_EINVAL, "out must not alias in");
+  std::vector<double> m(nrhs, mf);
+  rc = ddw_apply(c, out, in, m.data(), dagger ? 1 : 0, 0, prec, nrhs, (cudaStream_t)stream);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int dwf_hdw(dwf_ctx* c, void* out, const void* in, double mf, int prec, int nrhs,
+                       void* stream) {
+  int rc = check_fields(c, prec, nrhs, {out, in});
+  if (rc) return rc;
+  if (out == in) return dwf_fail(c, DWF_EINVAL, "out must not alias in");
+  std::vector<double> m(nrhs, mf);
+  rc = ddw_apply(c, out, in, m.data(), 0, 1, prec, nrhs, (cudaStream_t)stream);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+// ------------------------------------------------------------------ reductions (host results)
+static int read_scalars(dwf_ctx* c, int first, int n, cudaStream_t st) {
+  DWF_CUDA(c, cudaMemcpyAsync(c->hscal + first, c->dscal + first, n * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+  DWF_CUDA(c, cudaStreamSynchronize(st));
+  return DWF_OK;
+}
+
+static int norm2_dev(dwf_ctx* c, const void* a, int64_t n, int prec, int dst, cudaStream_t st) {
+  int np = 0;
+  int rc = blas_norm2_partials(c, a, n, prec, st, &np);
+  if (rc) return rc;
+  return blas_finalize(c, np, 1, dst, st);
+}
+
+extern "C" int dwf_norm2(dwf_ctx* c, double* result, const void* a, int64_t n, int prec, void* stream) {
+  int rc = check_fields(c, prec, 1, {a});
+  if (rc) return rc;
+  if (!result || n < 0) return dwf_fail(c, DWF_EINVAL, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = norm2_dev(c, a, n, prec, S_TMP0, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP0, 1, st);
+  if (rc) return rc;
+  *result = c->hscal[S_TMP0];
+  return DWF_OK;
+}
+
+extern "C" int dwf_cdot(dwf_ctx* c, double* result2, const void* a, const void* b, int64_t n, int prec,
+                        void* stream) {
+  int rc = check_fields(c, prec, 1, {a, b});
+  if (rc) return rc;
+  if (!result2 || n < 0) return dwf_fail(c, DWF_EINVAL, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int np = 0;
+  rc = blas_cdot_partials(c, a, b, n, prec, st, &np);
+  if (rc) return rc;
+  rc = blas_finalize(c, np, 2, S_TMP0, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP0, 2, st);
+  if (rc) return rc;
+  result2[0] = c->hscal[S_TMP0];
+  result2[1] = c->hscal[S_TMP0 + 1];
+  return DWF_OK;
+}
+
+// ------------------------------------------------------------------ red-black CGNR
+namespace {
+
+enum {
+  WS_B = 2,     // full FP64 source (host input)
+  WS_X = 3,     // full FP64 solution (host output)
+  WS_BP = 4,    // even FP64 b'_e
+  WS_RHS = 5,   // even FP64 M_pc^dag b'_e
+  WS_RHI = 6,   // even FP64 residual / scratch
+  WS_YHI = 7,   // even FP64 temporary
+  WS_OHI = 8,   // odd FP64 temporary
+  WS_XLO = 9,   // even inner x
+  WS_RLO = 10,  // even inner r
+  WS_P = 11,    // even p
+  WS_AP = 12,   // even Ap
+  WS_YLO = 13,  // even y = M_pc p
+  WS_OLO = 14,  // odd temporary
+  WS_FULL = 15  // full FP64 temporary (true residual)
+};
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double sec() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace
+
+// Inner CG operator: Ap = M_pc^dag M_pc p, with |M_pc p|^2 = <p, A p> reduced
+// into dscal[S_PAP] and alpha = rr / pAp computed on the device.
+static int cg_apply(dwf_ctx* c, void* Ap, const void* p, void* y, void* todd, const double* mf, int prec,
+                    cudaStream_t st) {
+  int np = 0;
+  int rc = mpc_apply(c, y, p, todd, mf, 0, prec, 1, 1, st, &np);
+  if (rc) return rc;
+  rc = blas_finalize_mode(c, np, 1, S_PAP, 1, st);
+  if (rc) return rc;
+  return mpc_apply(c, Ap, y, todd, mf, 1, prec, 1, 0, st, nullptr);
+}
+
+extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double tol, int maxiter,
+                          int policy, dwf_solve_stats* stats, void* stream) {
+  Timer timer;
+  if (!c || !x || !b) return DWF_EINVAL;
+  if (!(tol > 0) || maxiter < 1) return dwf_fail(c, DWF_EINVAL, "bad tol or maxiter");
+  if (policy < DWF_SOLVE_F64 || policy > DWF_SOLVE_MIXED_F16)
+    return dwf_fail(c, DWF_EINVAL, "bad policy");
+  if (policy == DWF_SOLVE_MIXED_F16) return dwf_fail(c, DWF_EINVAL, "FP16 policy not available");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int plo = policy == DWF_SOLVE_F64 ? DWF_F64 : DWF_F32;
+  const int64_t he = half_elems(c);
+  const size_t b64 = he * 16, blo = he * dwf_complex_bytes(plo);
+  dwf_solve_stats S;
+  memset(&S, 0, sizeof(S));
+
+  const bool host_b = !dwf_is_device_ptr(b);
+  const bool host_x = !dwf_is_device_ptr(x);
+  const double2* db = (const double2*)b;
+  double2* dx = (double2*)x;
+  if (host_b) {
+    void* w = dwf_workspace(c, WS_B, 2 * b64);
+    if (!w) return dwf_fail(c, DWF_ENOMEM, "workspace");
+    DWF_CUDA(c, cudaMemcpyAsync(w, b, 2 * b64, cudaMemcpyHostToDevice, st));
+    db = (const double2*)w;
+  }
+  if (host_x) {
+    void* w = dwf_workspace(c, WS_X, 2 * b64);
+    if (!w) return dwf_fail(c, DWF_ENOMEM, "workspace");
+    dx = (double2*)w;
+  }
+  if (((uintptr_t)db & 15) || ((uintptr_t)dx & 15)) return dwf_fail(c, DWF_EINVAL, "alignment");
+  void* bp = dwf_workspace(c, WS_BP, b64);
+  void* rhs = dwf_workspace(c, WS_RHS, b64);
+  void* rhi = dwf_workspace(c, WS_RHI, b64);
+  void* yhi = dwf_workspace(c, WS_YHI, b64);
+  void* ohi = dwf_workspace(c, WS_OHI, b64);
+  void* xlo = plo == DWF_F64 ? nullptr : dwf_workspace(c, WS_XLO, blo);
+  void* rlo = dwf_workspace(c, WS_RLO, blo);
+  void* p = dwf_workspace(c, WS_P, blo);
+  void* Ap = dwf_workspace(c, WS_AP, blo);
+  void* ylo = dwf_workspace(c, WS_YLO, blo);
+  void* olo = dwf_workspace(c, WS_OLO, blo);
+  if (!bp || !rhs || !rhi || !yhi || !ohi || (plo != DWF_F64 && !xlo) || !rlo || !p || !Ap || !ylo || !olo)
+    return dwf_fail(c, DWF_ENOMEM, "solver workspace");
+  const double2* b_e = db;
+  const double2* b_o = db + he;
+  double2* x_e = dx;
+  double2* x_o = dx + he;
+  int rc;
+  const double mfa[1] = {mf};
+  double matmuls = 0;  // in half-lattice hopping terms; /4*2 at the end
+
+  // |b|^2
+  rc = norm2_dev(c, db, 2 * he, DWF_F64, S_TMP1, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP1, 1, st);
+  if (rc) return rc;
+  const double bnorm = sqrt(c->hscal[S_TMP1]);
+  if (!(bnorm > 0)) {
+    DWF_CUDA(c, cudaMemsetAsync(dx, 0, 2 * b64, st));
+    if (host_x) DWF_CUDA(c, cudaMemcpyAsync(x, dx, 2 * b64, cudaMemcpyDeviceToHost, st));
+    DWF_CUDA(c, cudaStreamSynchronize(st));
+    if (stats) *stats = S;
+    return bnorm == 0 ? DWF_OK : dwf_fail(c, DWF_ENAN, "source is not finite");
+  }
+
+  // b'_e = b_e + 1/2 D_eo M_oo^-1 b_o
+  rc = launch_mooee(c, ohi, b_o, mfa, 0, 1, DWF_F64, 1, 0, st);
+  if (rc) return rc;
+  {
+    HopLaunch h = hop_base(bp, ohi, 0, 0, 1, 0.5);
+    h.aux = b_e;
+    h.aux_mode = 1;
+    rc = launch_hop(c, h, DWF_F64, st, nullptr);
+    if (rc) return rc;
+  }
+  // rhs = M_pc^dag b'_e
+  rc = mpc_apply(c, rhs, bp, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+  if (rc) return rc;
+  matmuls += 3;
+
+  // x_e = 0 (FP64 accumulator); the first reliable update sets r = rhs.
+  DWF_CUDA(c, cudaMemsetAsync(x_e, 0, b64, st));
+  void* xin = plo == DWF_F64 ? (void*)x_e : xlo;  // inner accumulator
+  const double delta = 0.1;
+  double true_res = 0, rr_hi = 0, rho = 1, rr_max = 0, rr_lo = 0;
+  bool have_x = false;
+
+  // Reliable update: x_hi += x_lo; y = b'_e - M_pc x_hi; true residual |y|/|b|;
+  // r_hi = M_pc^dag y; r_lo = r_hi.
+  auto reliable = [&]() -> int {
+    int r;
+    if (have_x && plo != DWF_F64) {
+      r = blas_axpby(c, 1.0, xlo, plo, 1.0, x_e, DWF_F64, he, st);
+      if (r) return r;
+    }
+    if (plo != DWF_F64) DWF_CUDA(c, cudaMemsetAsync(xlo, 0, blo, st));
+    if (have_x) {
+      r = mpc_apply(c, yhi, x_e, ohi, mfa, 0, DWF_F64, 1, 0, st, nullptr);
+      if (r) return r;
+      r = blas_axpby(c, 1.0, bp, DWF_F64, -1.0, yhi, DWF_F64, he, st);
+      if (r) return r;
+      r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+      if (r) return r;
+      matmuls += 4;
+      r = norm2_dev(c, yhi, he, DWF_F64, S_TMP2, st);
+      if (r) return r;
+    } else {
+      r = blas_copy(c, rhi, DWF_F64, rhs, DWF_F64, he, st);
+      if (r) return r;
+      r = norm2_dev(c, bp, he, DWF_F64, S_TMP2, st);
+      if (r) return r;
+    }
+    r = norm2_dev(c, rhi, he, DWF_F64, S_TMP3, st);
+    if (r) return r;
+    r = blas_copy(c, rlo, plo, rhi, DWF_F64, he, st);
+    if (r) return r;
+    r = norm2_dev(c, rlo, he, plo, S_RR, st);
+    if (r) return r;
+    r = read_scalars(c, S_TMP2, 2, st);
+    if (r) return r;
+    true_res = sqrt(c->hscal[S_TMP2]) / bnorm;
+    rr_hi = c->hscal[S_TMP3];
+    rho = rr_hi > 0 ? sqrt(c->hscal[S_TMP2] / rr_hi) : 1.0;
+    rr_max = rr_hi;
+    rr_lo = rr_hi;
+    have_x = true;
+    S.reliable_updates++;
+    if (!isfinite(true_res) || !isfinite(rr_hi)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
+    return DWF_OK;
+  };
+
+  rc = reliable();
+  if (rc) return rc;
+  S.reliable_updates = 0;
+  rc = blas_copy(c, p, plo, rlo, plo, he, st);
+  if (rc) return rc;
+  int it = 0;
+  const int check_every = 8;
+  bool converged = true_res <= tol;
+  while (!converged && it < maxiter) {
+    rc = cg_apply(c, Ap, p, ylo, olo, mfa, plo, st);
+    if (rc) return rc;
+    int np = 0;
+    rc = blas_cg_xr(c, xin, rlo, p, Ap, he, plo, S_ALPHA, st, &np);
+    if (rc) return rc;
+    rc = blas_finalize_mode(c, np, 1, S_RRNEW, 2, st);
+    if (rc) return rc;
+    rc = blas_cg_p(c, p, rlo, he, plo, S_BETA, st);
+    if (rc) return rc;
+    matmuls += 4;
+    it++;
+    if (it % check_every == 0 || it == maxiter) {
+      rc = read_scalars(c, S_RR, 1, st);
+      if (rc) return rc;
+      rr_lo = c->hscal[S_RR];
+      if (!isfinite(rr_lo)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
+      if (rr_lo > rr_max) rr_max = rr_lo;
+      const double predicted = rho * sqrt(rr_lo) / bnorm;
+      if (rr_lo < delta * delta * rr_max || predicted <= tol || it == maxiter) {
+        rc = reliable();
+        if (rc) return rc;
+        converged = true_res <= tol;
+        // continue the recurrence from the new residual: rr = |r_new|^2
+      }
+    }
+  }
+  S.iterations = it;
+
+  // x_o = M_oo^-1 (b_o + 1/2 D_oe x_e)
+  {
+    HopLaunch h = hop_base(x_o, x_e, 1, 0, 1, 0.5);
+    h.aux = b_o;
+    h.aux_mode = 1;
+    h.inv_mode = 1;
+    h.mf = mfa;
+    rc = launch_hop(c, h, DWF_F64, st, nullptr);
+    if (rc) return rc;
+  }
+  matmuls += 1;
+  // true residual ||b - D x|| / ||b|| in FP64
+  void* full = dwf_workspace(c, WS_FULL, 2 * b64);
+  if (!full) return dwf_fail(c, DWF_ENOMEM, "workspace");
+  rc = ddw_apply(c, full, dx, mfa, 0, 0, DWF_F64, 1, st);
+  if (rc) return rc;
+  matmuls += 2;
+  rc = blas_axpby(c, 1.0, db, DWF_F64, -1.0, full, DWF_F64, 2 * he, st);
+  if (rc) return rc;
+  rc = norm2_dev(c, full, 2 * he, DWF_F64, S_TMP2, st);
+  if (rc) return rc;
+  if (host_x) DWF_CUDA(c, cudaMemcpyAsync(x, dx, 2 * b64, cudaMemcpyDeviceToHost, st));
+  rc = read_scalars(c, S_TMP2, 1, st);
+  if (rc) return rc;
+  S.true_residual = sqrt(c->hscal[S_TMP2]) / bnorm;
+  S.fine_matmuls = matmuls / 2.0;
+  S.seconds = timer.sec();
+  S.status = S.true_residual <= tol ? DWF_OK : DWF_ENOCONV;
+  DWF_CUDA(c, cudaGetLastError());
+  if (stats) *stats = S;
+  if (S.status == DWF_ENOCONV) return dwf_fail(c, DWF_ENOCONV, "maxiter reached before tol");
+  return DWF_OK;
+}
+
+// ------------------------------------------------------------------ power method
+extern "C" int dwf_power_max(dwf_ctx* c, double* lmax, const void* v0, double mf, int iters,
+                             void* stream) {
+  int rc = check_fields(c, DWF_F64, 1, {v0});
+  if (rc) return rc;
+  if (!lmax || iters < 1) return dwf_fail(c, DWF_EINVAL, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = 2 * half_elems(c);
+  const size_t bytes = n * 16;
+  void* v = dwf_workspace(c, WS_FULL, bytes);
+  void* w = dwf_workspace(c, WS_B, bytes);
+  void* t = dwf_workspace(c, WS_X, bytes);
+  if (!v || !w || !t) return dwf_fail(c, DWF_ENOMEM, "workspace");
+  const double mfa[1] = {mf};
+  rc = norm2_dev(c, v0, n, DWF_F64, S_TMP0, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP0, 1, st);
+  if (rc) return rc;
+  double nv = sqrt(c->hscal[S_TMP0]);
+  if (!(nv > 0)) return dwf_fail(c, DWF_EINVAL, "zero start vector");
+  rc = blas_axpby(c, 1.0 / nv, v0, DWF_F64, 0.0, v, DWF_F64, n, st);
+  if (rc) return rc;
+  double lam = 0;
+  for (int k = 0; k < iters; k++) {
+    rc = ddw_apply(c, t, v, mfa, 0, 0, DWF_F64, 1, st);
+    if (rc) return rc;
+    rc = ddw_apply(c, w, t, mfa, 1, 0, DWF_F64, 1, st);
+    if (rc) return rc;
+    int np = 0;
+    rc = blas_cdot_partials(c, v, w, n, DWF_F64, st, &np);
+    if (rc) return rc;
+    rc = blas_finalize(c, np, 2, S_TMP0, st);
+    if (rc) return rc;
+    rc = norm2_dev(c, w, n, DWF_F64, S_TMP2, st);
+    if (rc) return rc;
+    rc = read_scalars(c, S_TMP0, 3, st);
+    if (rc) return rc;
+    lam = c->hscal[S_TMP0];
+    const double nw = sqrt(c->hscal[S_TMP2]);
+    if (!isfinite(nw) || !(nw > 0)) return dwf_fail(c, DWF_ENAN, "power method breakdown");
+    rc = blas_axpby(c, 1.0 / nw, w, DWF_F64, 0.0, v, DWF_F64, n, st);
+    if (rc) return rc;
+  }
+  DWF_CUDA(c, cudaStreamSynchronize(st));
+  *lmax = lam;
+  return DWF_OK;
+}

@@ -1,0 +1,416 @@
+// Wilson hopping term on every s-slice (arXiv:2103.05034, Sec. 2, Eq. 2) with
+// the fifth-dimension matrix of Eq. (4) fused into the epilogue.
+//
+// Data layout (see include/dwfmg.h): half field [Vh][spin 4][colour 3][Ls],
+// the fifth dimension innermost; links for an output parity are
+// [Vh][8][3][3] with slot 2mu = U_mu(x) and slot 2mu+1 = U_mu(x-mu)^dag.
+//
+// Thread mapping: one CTA handles SB consecutive checkerboard sites and all
+// Ls slices of each (blockDim = Ls*SB, s fastest), so
+//   * the 16 (or 24) threads of one site read each spinor component of a
+//     neighbour as one contiguous run of Ls complex numbers (coalesced), and
+//   * the site's 8 links are loaded once into shared memory and reused by all
+//     Ls threads (links cost 8*18 reals / Ls per output 5D site).
+// Spin projection (1 -+ gamma_mu) reduces each neighbour to a two-spinor
+// before the SU(3) multiply (chiral basis: gamma_mu = [[0,A],[A^dag,0]],
+// (1 - s gamma)psi = [h; -s A^dag h], h = psi_up - s A psi_dn).
+//
+// Epilogue, per CTA, on the Ls-vector of every (site, spin, colour):
+//   aux term   M psi_s = d psi_s - psi_{s-+1} (+ m psi at the wall), read from
+//              global memory (the neighbours in s are in the same CTA's lines)
+//   inverse    M_+^-1 by two O(Ls) sweeps (a forward geometric prefix sum F
+//              and a backward one G, x_s = kappa/d (F_s - m G_s)), run by 12
+//              threads per site on a padded shared-memory stage; M_-^-1 is the
+//              same on reversed s (M_- = M_+^T, chirality - = spins 2,3)
+//   Gamma_5    gamma_5 with s -> Ls-1-s on the store
+//   reduction  |out|^2 in FP64 per CTA
+#pragma once
+#include "dwf_internal.cuh"
+
+namespace dwfk {
+
+struct HopParams {
+  void* out;
+  const void* in;
+  const void* aux;
+  const void* links;
+  double* partials;
+  int L0, L1, L2, L3, Lxh;
+  int Vh;
+  int out_parity;
+  float sg;  // +1: D_hop, -1: D_hop^dag
+  double alpha;
+  int aux_mode, inv_mode, g5r5, reduce;
+  long long rhs_stride;
+  double d;
+  double m[DWF_MAX_RHS];
+  double kappa[DWF_MAX_RHS];
+  double dls1[DWF_MAX_RHS];
+};
+
+template <class R>
+__device__ __forceinline__ void cacc(cpx<R>& a, const cpx<R>& b) {
+  a.re += b.re;
+  a.im += b.im;
+}
+
+// acc += (1 - sg gamma_mu) U psi, spin-projected.
+template <class R, int MU>
+__device__ __forceinline__ void hop_dir(cpx<R> (&acc)[12], const cpx<R> (&ps)[12],
+                                        const cpx<R>* __restrict__ U, R sg) {
+  cpx<R> h0[3], h1[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<R> p0 = ps[c], p1 = ps[3 + c], p2 = ps[6 + c], p3 = ps[9 + c];
+    if (MU == 0) {  // A = -i sigma_1: h0 = p0 + s i p3, h1 = p1 + s i p2
+      h0[c] = cmake<R>(p0.re - sg * p3.im, p0.im + sg * p3.re);
+      h1[c] = cmake<R>(p1.re - sg * p2.im, p1.im + sg * p2.re);
+    } else if (MU == 1) {  // A = -i sigma_2: h0 = p0 + s p3, h1 = p1 - s p2
+      h0[c] = cmake<R>(p0.re + sg * p3.re, p0.im + sg * p3.im);
+      h1[c] = cmake<R>(p1.re - sg * p2.re, p1.im - sg * p2.im);
+    } else if (MU == 2) {  // A = -i sigma_3: h0 = p0 + s i p2, h1 = p1 - s i p3
+      h0[c] = cmake<R>(p0.re - sg * p2.im, p0.im + sg * p2.re);
+      h1[c] = cmake<R>(p1.re + sg * p3.im, p1.im - sg * p3.re);
+    } else {  // A = 1: h0 = p0 - s p2, h1 = p1 - s p3
+      h0[c] = cmake<R>(p0.re - sg * p2.re, p0.im - sg * p2.im);
+      h1[c] = cmake<R>(p1.re - sg * p3.re, p1.im - sg * p3.im);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    cpx<R> g0 = cmake<R>(0, 0), g1 = cmake<R>(0, 0);
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const cpx<R> u = U[a * 3 + b];
+      g0.re = fma(u.re, h0[b].re, g0.re);
+      g0.re = fma(-u.im, h0[b].im, g0.re);
+      g0.im = fma(u.re, h0[b].im, g0.im);
+      g0.im = fma(u.im, h0[b].re, g0.im);
+      g1.re = fma(u.re, h1[b].re, g1.re);
+      g1.re = fma(-u.im, h1[b].im, g1.re);
+      g1.im = fma(u.re, h1[b].im, g1.im);
+      g1.im = fma(u.im, h1[b].re, g1.im);
+    }
+    cacc(acc[a], g0);
+    cacc(acc[3 + a], g1);
+    // lower spins: -s A^dag g
+    if (MU == 0) {  // A^dag g = (i g1, i g0)
+      acc[6 + a].re = fma(sg, g1.im, acc[6 + a].re);
+      acc[6 + a].im = fma(-sg, g1.re, acc[6 + a].im);
+      acc[9 + a].re = fma(sg, g0.im, acc[9 + a].re);
+      acc[9 + a].im = fma(-sg, g0.re, acc[9 + a].im);
+    } else if (MU == 1) {  // A^dag g = (g1, -g0)
+      acc[6 + a].re = fma(-sg, g1.re, acc[6 + a].re);
+      acc[6 + a].im = fma(-sg, g1.im, acc[6 + a].im);
+      acc[9 + a].re = fma(sg, g0.re, acc[9 + a].re);
+      acc[9 + a].im = fma(sg, g0.im, acc[9 + a].im);
+    } else if (MU == 2) {  // A^dag g = (i g0, -i g1)
+      acc[6 + a].re = fma(sg, g0.im, acc[6 + a].re);
+      acc[6 + a].im = fma(-sg, g0.re, acc[6 + a].im);
+      acc[9 + a].re = fma(-sg, g1.im, acc[9 + a].re);
+      acc[9 + a].im = fma(sg, g1.re, acc[9 + a].im);
+    } else {  // A^dag g = (g0, g1)
+      acc[6 + a].re = fma(-sg, g0.re, acc[6 + a].re);
+      acc[6 + a].im = fma(-sg, g0.im, acc[6 + a].im);
+      acc[9 + a].re = fma(-sg, g1.re, acc[9 + a].re);
+      acc[9 + a].im = fma(-sg, g1.im, acc[9 + a].im);
+    }
+  }
+}
+
+template <int P, int LS>
+__device__ __forceinline__ void load_spinor(cpx<typename Prec<P>::R> (&ps)[12],
+                                            const typename Prec<P>::S* __restrict__ base, int s) {
+#pragma unroll
+  for (int c = 0; c < 12; c++) ps[c] = ld_c(base + c * LS + s);
+}
+
+// M_+^-1 (fwd=true) or M_-^-1 (fwd=false, reversed s) of one Ls-row, in place.
+template <class R, int LS>
+__device__ __forceinline__ void minv_row(cpx<R>* row, bool fwd, R d, R m, R kappa, R dls1) {
+  cpx<R> val[LS], G[LS];
+#pragma unroll
+  for (int q = 0; q < LS; q++) val[q] = row[fwd ? q : LS - 1 - q];
+  cpx<R> g = cmake<R>(0, 0);
+#pragma unroll
+  for (int q = LS - 1; q >= 0; q--) {
+    G[q] = g;
+    g.re = fma(d, g.re, dls1 * val[q].re);
+    g.im = fma(d, g.im, dls1 * val[q].im);
+  }
+  const R dinv = R(1) / d;
+  const R kd = kappa * dinv;
+  cpx<R> f = cmake<R>(0, 0);
+#pragma unroll
+  for (int q = 0; q < LS; q++) {
+    f.re = fma(f.re, dinv, val[q].re);
+    f.im = fma(f.im, dinv, val[q].im);
+    cpx<R> o;
+    o.re = kd * fma(-m, G[q].re, f.re);
+    o.im = kd * fma(-m, G[q].im, f.im);
+    row[fwd ? q : LS - 1 - q] = o;
+  }
+}
+
+template <int P, int LS, int SB>
+__global__ void __launch_bounds__(LS* SB) hop_kernel(const HopParams p) {
+  typedef typename Prec<P>::S S;
+  typedef typename Prec<P>::R R;
+  typedef typename Prec<P>::LS LT;
+  constexpr int NT = LS * SB;
+  __shared__ cpx<R> sU[SB * 72];
+  __shared__ cpx<R> stage[SB * 12 * (LS + 1)];
+  __shared__ double red[NT / 32 + 1];
+
+  const int tid = threadIdx.x;
+  const int sl = tid / LS;
+  const int s = tid - sl * LS;
+  const int site0 = blockIdx.x * SB;
+  const int rhs = blockIdx.y;
+  const int site = site0 + sl;
+  const bool active = site < p.Vh;
+
+  {
+    const LT* gl = (const LT*)p.links + (size_t)site0 * 72;
+    const int n = min(SB, p.Vh - site0) * 72;
+    for (int i = tid; i < n; i += NT) {
+      const LT v = gl[i];
+      sU[i] = cmake<R>((R)v.x, (R)v.y);
+    }
+  }
+  __syncthreads();
+
+  cpx<R> v[12];
+#pragma unroll
+  for (int c = 0; c < 12; c++) v[c] = cmake<R>(0, 0);
+
+  if (active) {
+    int rem = site / p.Lxh;
+    const int xh = site - rem * p.Lxh;
+    const int y = rem % p.L1;
+    rem /= p.L1;
+    const int z = rem % p.L2;
+    const int t = rem / p.L2;
+    const int x = 2 * xh + ((y + z + t + p.out_parity) & 1);
+    const S* in = (const S*)p.in + (size_t)rhs * p.rhs_stride;
+    const int Lxh = p.Lxh, L1 = p.L1, L2 = p.L2;
+    auto cbi = [&](int X, int Y, int Z, int T) { return ((T * L2 + Z) * L1 + Y) * Lxh + (X >> 1); };
+    const int xp = (x + 1 == p.L0) ? 0 : x + 1, xm = (x == 0) ? p.L0 - 1 : x - 1;
+    const int yp = (y + 1 == p.L1) ? 0 : y + 1, ym = (y == 0) ? p.L1 - 1 : y - 1;
+    const int zp = (z + 1 == p.L2) ? 0 : z + 1, zm = (z == 0) ? p.L2 - 1 : z - 1;
+    const int tp = (t + 1 == p.L3) ? 0 : t + 1, tm = (t == 0) ? p.L3 - 1 : t - 1;
+    const R sf = (R)p.sg;
+    const cpx<R>* U = sU + sl * 72;
+    cpx<R> ps[12];
+    load_spinor<P, LS>(ps, in + (size_t)cbi(xp, y, z, t) * 12 * LS, s);
+    hop_dir<R, 0>(v, ps, U + 0 * 9, sf);
+    load_spinor<P, LS>(ps, in + (size_t)cbi(xm, y, z, t) * 12 * LS, s);
+    hop_dir<R, 0>(v, ps, U + 1 * 9, -sf);
+    load_spinor<P, LS>(ps, in + (size_t)cbi(x, yp, z, t) * 12 * LS, s);
+    hop_dir<R, 1>(v, ps, U + 2 * 9, sf);
+    load_spinor<P, LS>(ps, in + (size_t)cbi(x, ym, z, t) * 12 * LS, s);
+    hop_dir<R, 1>(v, ps, U + 3 * 9, -sf);
+    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, zp, t) * 12 * LS, s);
+    hop_dir<R, 2>(v, ps, U + 4 * 9, sf);
+    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, zm, t) * 12 * LS, s);
+    hop_dir<R, 2>(v, ps, U + 5 * 9, -sf);
+    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, z, tp) * 12 * LS, s);
+    hop_dir<R, 3>(v, ps, U + 6 * 9, sf);
+    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, z, tm) * 12 * LS, s);
+    hop_dir<R, 3>(v, ps, U + 7 * 9, -sf);
+
+    const R alpha = (R)p.alpha;
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      v[c].re *= alpha;
+      v[c].im *= alpha;
+    }
+    if (p.aux_mode) {
+      const S* aux = (const S*)p.aux + (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS;
+      if (p.aux_mode == 1) {
+#pragma unroll
+        for (int c = 0; c < 12; c++) cacc(v[c], ld_c(aux + c * LS + s));
+      } else {
+        const bool dagM = p.aux_mode == 3;
+        const R d = (R)p.d, m = (R)p.m[rhs];
+        // chirality + (spins 0,1) non-dagger: M_+ couples s-1; chirality -: s+1
+        const int sm = s > 0 ? s - 1 : LS - 1;
+        const int sp = s < LS - 1 ? s + 1 : 0;
+        const R cm = s > 0 ? R(-1) : m;
+        const R cp = s < LS - 1 ? R(-1) : m;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+          const bool lower = (c < 6) != dagM;
+          const cpx<R> a = ld_c(aux + c * LS + s);
+          const cpx<R> an = ld_c(aux + c * LS + (lower ? sm : sp));
+          const R co = lower ? cm : cp;
+          v[c].re += fma(d, a.re, co * an.re);
+          v[c].im += fma(d, a.im, co * an.im);
+        }
+      }
+    }
+  }
+
+  if (p.inv_mode) {
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 12; c++) stage[(sl * 12 + c) * (LS + 1) + s] = v[c];
+    }
+    __syncthreads();
+    for (int w = tid; w < SB * 12; w += NT) {
+      const int sl2 = w / 12, c2 = w - sl2 * 12;
+      if (site0 + sl2 < p.Vh) {
+        const bool fwd = (c2 < 6) != (p.inv_mode == 2);
+        minv_row<R, LS>(stage + (sl2 * 12 + c2) * (LS + 1), fwd, (R)p.d, (R)p.m[rhs],
+                        (R)p.kappa[rhs], (R)p.dls1[rhs]);
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 12; c++) v[c] = stage[(sl * 12 + c) * (LS + 1) + s];
+    }
+  }
+
+  if (active) {
+    S* out = (S*)p.out + (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS;
+    if (p.g5r5) {
+      const int so = LS - 1 - s;
+#pragma unroll
+      for (int c = 0; c < 12; c++) {
+        cpx<R> o = v[c];
+        if (c >= 6) {
+          o.re = -o.re;
+          o.im = -o.im;
+        }
+        st_c(out + c * LS + so, o);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 12; c++) st_c(out + c * LS + s, v[c]);
+    }
+  }
+
+  if (p.reduce) {
+    double acc = 0.0;
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < 12; c++) acc += (double)v[c].re * v[c].re + (double)v[c].im * v[c].im;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < NT / 32; i++) tot += red[i];
+      p.partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    }
+  }
+}
+
+// Site-local M, M^dag, M^-1 or M^-dag of Eq. (4) on whole Ls-rows: one thread
+// per (site, spin, colour).
+template <int P, int LS>
+__global__ void __launch_bounds__(128) mooee_kernel(typename Prec<P>::S* out,
+                                                    const typename Prec<P>::S* in, int Vh,
+                                                    int dagger, int inverse, long long rhs_stride,
+                                                    HopParams p) {
+  typedef typename Prec<P>::R R;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (gid >= (long long)Vh * 12) return;
+  const int c = (int)(gid % 12);
+  const size_t off = (size_t)rhs * rhs_stride + (size_t)gid * LS;
+  cpx<R> row[LS];
+#pragma unroll
+  for (int q = 0; q < LS; q++) row[q] = ld_c(in + off + q);
+  const R d = (R)p.d, m = (R)p.m[rhs];
+  const bool plus_rule = (c < 6) != (dagger != 0);  // M_+ type (couples s-1)
+  if (inverse) {
+    minv_row<R, LS>(row, plus_rule, d, m, (R)p.kappa[rhs], (R)p.dls1[rhs]);
+  } else {
+    cpx<R> res[LS];
+#pragma unroll
+    for (int q = 0; q < LS; q++) {
+      int qn;
+      R co;
+      if (plus_rule) {
+        qn = q > 0 ? q - 1 : LS - 1;
+        co = q > 0 ? R(-1) : m;
+      } else {
+        qn = q < LS - 1 ? q + 1 : 0;
+        co = q < LS - 1 ? R(-1) : m;
+      }
+      res[q].re = fma(d, row[q].re, co * row[qn].re);
+      res[q].im = fma(d, row[q].im, co * row[qn].im);
+    }
+#pragma unroll
+    for (int q = 0; q < LS; q++) row[q] = res[q];
+  }
+#pragma unroll
+  for (int q = 0; q < LS; q++) st_c(out + off + q, row[q]);
+}
+
+template <int LS>
+struct HopShape {
+  static constexpr int SB = (LS >= 16) ? 8 : (128 / LS);
+};
+
+template <int P>
+int launch_hop_prec(const HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nblocks) {
+  dim3 grid;
+  grid.y = nrhs;
+  grid.z = 1;
+#define DWF_HOP_CASE(LSV)                                                        \
+  case LSV: {                                                                    \
+    constexpr int SB = HopShape<LSV>::SB;                                        \
+    grid.x = (hp.Vh + SB - 1) / SB;                                              \
+    hop_kernel<P, LSV, SB><<<grid, LSV * SB, 0, st>>>(hp);                       \
+    if (nblocks) *nblocks = grid.x * grid.y;                                     \
+    return DWF_OK;                                                               \
+  }
+  switch (Ls) {
+    DWF_HOP_CASE(4)
+    DWF_HOP_CASE(8)
+    DWF_HOP_CASE(16)
+    DWF_HOP_CASE(24)
+    default:
+      return DWF_EINVAL;
+  }
+#undef DWF_HOP_CASE
+}
+
+template <int P>
+int launch_mooee_prec(void* out, const void* in, const HopParams& hp, int dagger, int inverse,
+                      int Ls, int nrhs, long long rhs_stride, cudaStream_t st) {
+  typedef typename Prec<P>::S S;
+  dim3 grid((unsigned)((hp.Vh * 12LL + 127) / 128), nrhs, 1);
+#define DWF_MOO_CASE(LSV)                                                                    \
+  case LSV:                                                                                  \
+    mooee_kernel<P, LSV><<<grid, 128, 0, st>>>((S*)out, (const S*)in, hp.Vh, dagger, inverse, \
+                                               rhs_stride, hp);                              \
+    return DWF_OK;
+  switch (Ls) {
+    DWF_MOO_CASE(4)
+    DWF_MOO_CASE(8)
+    DWF_MOO_CASE(16)
+    DWF_MOO_CASE(24)
+    default:
+      return DWF_EINVAL;
+  }
+#undef DWF_MOO_CASE
+}
+
+}  // namespace dwfk
+
+// Per-precision entry points (defined in dhop_f64.cu, dhop_f32.cu, dhop_f16.cu).
+int dwf_launch_hop_f64(const dwfk::HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nb);
+int dwf_launch_hop_f32(const dwfk::HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nb);
+int dwf_launch_hop_f16(const dwfk::HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nb);
+int dwf_launch_mooee_f64(void* out, const void* in, const dwfk::HopParams& hp, int dagger,
+                         int inverse, int Ls, int nrhs, long long rs, cudaStream_t st);
+int dwf_launch_mooee_f32(void* out, const void* in, const dwfk::HopParams& hp, int dagger,
+                         int inverse, int Ls, int nrhs, long long rs, cudaStream_t st);
+int dwf_launch_mooee_f16(void* out, const void* in, const dwfk::HopParams& hp, int dagger,
+                         int inverse, int Ls, int nrhs, long long rs, cudaStream_t st);

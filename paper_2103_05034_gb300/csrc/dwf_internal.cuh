@@ -1,0 +1,180 @@
+// Internal declarations of the GB300 DWF multigrid library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dwfmg.h"
+
+#define DWF_MAX_RHS 64
+#define DWF_NWS 32  // workspace slots
+
+// ------------------------------------------------------------------ complex helpers
+template <class R>
+struct cpx {
+  R re, im;
+};
+
+template <class R>
+__device__ __forceinline__ cpx<R> cmake(R a, R b) {
+  cpx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+
+// Storage traits: element type of a complex number in memory and the real
+// type used for arithmetic.
+template <int P>
+struct Prec;
+template <>
+struct Prec<DWF_F64> {
+  typedef double2 S;  // stored complex
+  typedef double R;   // arithmetic
+  typedef double2 LS; // stored link element
+};
+template <>
+struct Prec<DWF_F32> {
+  typedef float2 S;
+  typedef float R;
+  typedef float2 LS;
+};
+template <>
+struct Prec<DWF_F16S> {
+  typedef __half2 S;
+  typedef float R;
+  typedef float2 LS;
+};
+
+__device__ __forceinline__ cpx<double> ld_c(const double2* p) {
+  double2 v = *p;
+  return cmake(v.x, v.y);
+}
+__device__ __forceinline__ cpx<float> ld_c(const float2* p) {
+  float2 v = *p;
+  return cmake(v.x, v.y);
+}
+__device__ __forceinline__ cpx<float> ld_c(const __half2* p) {
+  float2 v = __half22float2(*p);
+  return cmake(v.x, v.y);
+}
+__device__ __forceinline__ void st_c(double2* p, cpx<double> z) { *p = make_double2(z.re, z.im); }
+__device__ __forceinline__ void st_c(float2* p, cpx<float> z) { *p = make_float2(z.re, z.im); }
+__device__ __forceinline__ void st_c(__half2* p, cpx<float> z) {
+  *p = __floats2half2_rn(z.re, z.im);
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geom {
+  int L[4];   // Lx, Ly, Lz, Lt
+  int Lxh;    // Lx / 2
+  int64_t Vh; // sites per parity
+  int Ls;
+};
+
+// Fifth-dimension coefficients of M (Eq. 4) for one mass: d = 5 - M5,
+// kappa = 1/(1 + m d^-Ls), dls1 = d^(1-Ls).
+struct FifthCoef {
+  double m, kappa, dls1;
+};
+
+// ------------------------------------------------------------------ context
+struct dwf_ctx {
+  Geom g;
+  double M5;
+  int device;
+  // parity-split, double-stored links: links[p] is [Vh][8][3][3] complex,
+  // slot 2mu = U_mu(x), slot 2mu+1 = U_mu(x-mu)^dag, for sites x of parity p.
+  double2* links64[2];
+  float2* links32[2];
+  // workspace (grown on demand)
+  void* ws[DWF_NWS];
+  size_t ws_bytes[DWF_NWS];
+  double* partials;   // reduction partials
+  size_t partials_n;
+  double* dscal;      // device scalars for solvers
+  double* hscal;      // pinned host mirror
+  std::string err;
+};
+
+// Error helpers (host).
+int dwf_fail(dwf_ctx* c, int code, const std::string& msg);
+int dwf_cuda_check(dwf_ctx* c, cudaError_t e, const char* where);
+#define DWF_CUDA(ctx, call)                                         \
+  do {                                                              \
+    cudaError_t _e = (call);                                        \
+    if (_e != cudaSuccess) return dwf_cuda_check((ctx), _e, #call); \
+  } while (0)
+
+size_t dwf_complex_bytes(int prec);
+void* dwf_workspace(dwf_ctx* c, int slot, size_t bytes);
+bool dwf_is_device_ptr(const void* p);
+
+// ------------------------------------------------------------------ launchers
+// Hopping-term launch descriptor with the fused fifth-dimension epilogue:
+//   v   = alpha * D_hop^{(dagger)} in                      (hop part)
+//   v  += aux term: aux, M aux or M^dag aux                (aux_mode 1,2,3)
+//   v   = M^-1 v or M^-dag v                               (inv_mode 1,2)
+//   out = v, or Gamma_5 v (gamma_5 and s -> Ls-1-s)        (g5r5)
+//   partials[block] += |v|^2                               (reduce)
+struct HopLaunch {
+  void* out;
+  const void* in;
+  const void* aux;
+  int out_parity;
+  int dagger;
+  int nrhs;
+  int64_t rhs_stride;  // complex elements between consecutive rhs fields
+  double alpha;
+  int aux_mode;        // 0 none, 1 aux, 2 M aux, 3 M^dag aux
+  int inv_mode;        // 0 none, 1 M^-1, 2 M^-dag
+  int g5r5;
+  int reduce;          // 1: |out|^2 partials into ctx->partials
+  const double* mf;    // host array [nrhs] of masses (aux_mode>=2 or inv_mode>0)
+};
+
+int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* nblocks);
+int launch_mooee(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int inverse,
+                 int prec, int nrhs, int64_t rhs_stride, cudaStream_t st);
+
+// BLAS-1 (blas.cu).  n = number of complex elements.
+int blas_norm2_partials(dwf_ctx* c, const void* a, int64_t n, int prec, cudaStream_t st, int* nparts);
+int blas_cdot_partials(dwf_ctx* c, const void* a, const void* b, int64_t n, int prec,
+                       cudaStream_t st, int* nparts);
+// Sum nparts partials (width 1 or 2 doubles) into dscal[dst..dst+width-1].
+int blas_finalize(dwf_ctx* c, int nparts, int width, int dst, cudaStream_t st);
+// As blas_finalize, then mode 1: alpha = rr/pAp; mode 2: beta = rrnew/rr, rr = rrnew.
+int blas_finalize_mode(dwf_ctx* c, int nparts, int width, int dst, int mode, cudaStream_t st);
+// Grow the reduction-partials buffer to at least n doubles.
+int dwf_reserve_partials(dwf_ctx* c, size_t n);
+// y = a*x + b*y with real host scalars, any precisions (x, y may differ).
+int blas_axpby(dwf_ctx* c, double a, const void* x, int px, double b, void* y, int py, int64_t n,
+               cudaStream_t st);
+// y = x converted between precisions.
+int blas_copy(dwf_ctx* c, void* y, int py, const void* x, int px, int64_t n, cudaStream_t st);
+// CG updates with device scalars (dscal indices), precision prec:
+//   x += alpha p; r -= alpha Ap; partials |r|^2
+int blas_cg_xr(dwf_ctx* c, void* x, void* r, const void* p, const void* Ap, int64_t n, int prec,
+               int ialpha, cudaStream_t st, int* nparts);
+//   p = r + beta p
+int blas_cg_p(dwf_ctx* c, void* p, const void* r, int64_t n, int prec, int ibeta, cudaStream_t st);
+// dscal[dst] = dscal[num] / dscal[den]
+int blas_scalar_div(dwf_ctx* c, int dst, int num, int den, cudaStream_t st);
+
+// Device scalar slots.
+enum {
+  S_RR = 0,    // |r|^2
+  S_PAP = 1,   // <p, A p>
+  S_ALPHA = 2,
+  S_BETA = 3,
+  S_RRNEW = 4,
+  S_TMP0 = 8,
+  S_TMP1 = 9,
+  S_TMP2 = 10,
+  S_TMP3 = 11,
+  S_NSCAL = 32
+};

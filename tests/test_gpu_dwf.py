@@ -1,0 +1,198 @@
+"""GPU parity of the fine operators and the red-black CG through the C ABI,
+against the FP64 oracle (Sec. 2 and Sec. 5.1 of arXiv:2103.05034).
+
+Tolerances (norm-wise relative): FP64 1e-12, FP32 1e-6 (operators with FP32
+arithmetic on O(1) data: ~10 roundings per output of relative size 6e-8),
+FP16 storage 2e-3 (one rounding of input and output at 4.9e-4 each, summed
+over 8 neighbours)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import dwf, krylov
+from paper_2103_05034_gb300 import ops
+from paper_2103_05034_gb300._lib import (DWF_EINVAL, F16S, F32, F64, SOLVE_F64, SOLVE_MIXED_F32,
+                                         DWFError)
+
+from gpu_helpers import dev_to_full_canon, dev_to_half, full_dev, half_dev, rel
+
+pytestmark = pytest.mark.gpu
+M5 = 1.8
+TOL = {F64: 1e-12, F32: 1e-6, F16S: 2e-3}
+
+CASES = [((4, 4, 4, 4), 8), ((2, 2, 2, 6), 8), ((4, 2, 2, 4), 4), ((4, 4, 2, 2), 16),
+         ((2, 4, 2, 2), 24)]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"L{'x'.join(map(str, c[0]))}_Ls{c[1]}")
+def case(request):
+    L, Ls = request.param
+    U = synth.random_gauge(L, 0.5, 7)
+    ctx = ops.Context(L, Ls, M5, U)
+    yield L, Ls, U, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [F64, F32, F16S])
+@pytest.mark.parametrize("dagger", [0, 1])
+@pytest.mark.parametrize("out_parity", [0, 1])
+def test_dhop_parity(case, prec, dagger, out_parity):
+    L, Ls, U, ctx = case
+    psi = synth.gaussian_spinor(L, Ls, 11)
+    src = dwf.project_parity(psi, L, 1 - out_parity)
+    inp = half_dev(psi, L, 1 - out_parity, prec)
+    out = torch.zeros_like(inp)
+    ops.dwf_dhop(ctx, out, inp, out_parity, dagger)
+    want = dwf.dhop(U, src, dag=bool(dagger))
+    from paper_2103_05034_gb300 import layout
+    want = layout.to_half(want, L, out_parity)
+    assert rel(dev_to_half(out, Ls), want) < TOL[prec]
+
+
+def test_dhop_batched(case):
+    L, Ls, U, ctx = case
+    nrhs = 3
+    psis = [synth.gaussian_spinor(L, Ls, 20 + i) for i in range(nrhs)]
+    inp = torch.cat([half_dev(p, L, 1, F32) for p in psis])
+    out = torch.zeros_like(inp)
+    ops.dwf_dhop(ctx, out, inp, 0, 0, nrhs=nrhs)
+    from paper_2103_05034_gb300 import layout
+    got = dev_to_half(out, Ls).reshape(nrhs, -1, 4, 3, Ls)
+    for i, p in enumerate(psis):
+        want = layout.to_half(dwf.dhop(U, dwf.project_parity(p, L, 1)), L, 0)
+        assert rel(got[i], want) < TOL[F32]
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("dagger", [0, 1])
+@pytest.mark.parametrize("mf", [0.01, 0.3])
+def test_mooee_and_inverse(case, prec, dagger, mf):
+    L, Ls, U, ctx = case
+    from paper_2103_05034_gb300 import layout
+    psi = dwf.project_parity(synth.gaussian_spinor(L, Ls, 12), L, 0)
+    inp = half_dev(psi, L, 0, prec)
+    out = torch.zeros_like(inp)
+    ops.dwf_mooee(ctx, out, inp, mf, dagger)
+    want = layout.to_half(dwf.mooee(psi, M5, mf, dag=bool(dagger)), L, 0)
+    assert rel(dev_to_half(out, Ls), want) < TOL[prec]
+    ops.dwf_mooee_inv(ctx, out, inp, mf, dagger)
+    want = layout.to_half(dwf.mooee_inv(psi, M5, mf, dag=bool(dagger)), L, 0)
+    assert rel(dev_to_half(out, Ls), want) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_mpc_and_normal_op(case, prec):
+    L, Ls, U, ctx = case
+    from paper_2103_05034_gb300 import layout
+    mf = 0.05
+    psi = dwf.project_parity(synth.gaussian_spinor(L, Ls, 13), L, 0)
+    inp = half_dev(psi, L, 0, prec)
+    out = torch.zeros_like(inp)
+    for dagger, fn in ((0, dwf.mpc), (1, dwf.mpc_dag)):
+        ops.dwf_mpc(ctx, out, inp, mf, dagger)
+        assert rel(dev_to_half(out, Ls), layout.to_half(fn(U, psi, M5, mf), L, 0)) < TOL[prec]
+    ops.dwf_mpcdag_mpc(ctx, out, inp, mf)
+    want = layout.to_half(dwf.mpcdag_mpc(U, psi, M5, mf), L, 0)
+    assert rel(dev_to_half(out, Ls), want) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_full_ddw_and_hdw(case, prec):
+    L, Ls, U, ctx = case
+    mf = 0.02
+    psi = synth.gaussian_spinor(L, Ls, 14)
+    inp = full_dev(psi, L, prec)
+    out = torch.zeros_like(inp)
+    for dagger in (0, 1):
+        ops.dwf_ddw(ctx, out, inp, mf, dagger)
+        want = dwf.ddw(U, psi, M5, mf, dag=bool(dagger))
+        assert rel(dev_to_full_canon(out, L, Ls), want) < TOL[prec]
+    ops.dwf_hdw(ctx, out, inp, mf)
+    assert rel(dev_to_full_canon(out, L, Ls), dwf.hdw(U, psi, M5, mf)) < TOL[prec]
+
+
+def test_reductions(case):
+    L, Ls, U, ctx = case
+    a = synth.gaussian_spinor(L, Ls, 15)
+    b = synth.gaussian_spinor(L, Ls, 16)
+    ad, bd = full_dev(a, L, F64), full_dev(b, L, F64)
+    assert abs(ops.dwf_norm2(ctx, ad) - dwf.norm2(a)) < 1e-12 * dwf.norm2(a)
+    ip = ops.dwf_cdot(ctx, ad, bd)
+    want = dwf.inner(a, b)
+    assert abs(ip - want) < 1e-12 * np.sqrt(dwf.norm2(a) * dwf.norm2(b))
+
+
+@pytest.mark.parametrize("policy", [SOLVE_F64, SOLVE_MIXED_F32])
+def test_rbcg_solution_parity(policy):
+    """4^4 x Ls=8, U = exp(0.3 i H), M5 = 1.8, mf = 0.01 (the small FP64
+    workload): GPU solution vs oracle solution."""
+    L, Ls, mf = (4, 4, 4, 4), 8, 0.01
+    U = synth.random_gauge(L, 0.3, synth.SEED_GAUGE)
+    b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE)
+    ctx = ops.Context(L, Ls, M5, U)
+    tol = 1e-10
+    bd = full_dev(b, L, F64)
+    x = torch.zeros_like(bd)
+    st = ops.rbcg_solve(ctx, x, bd, mf, tol, 20000, policy)
+    xg = dev_to_full_canon(x, L, Ls)
+    res = krylov.true_residual(U, xg, b, M5, mf)
+    assert res <= tol * 1.01, st
+    assert st["true_residual"] == pytest.approx(res, rel=1e-3, abs=1e-14)
+    xr, it, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert rel(xg, xr) < 1e-7
+    # iteration counts of the two CGs agree closely in FP64
+    if policy == SOLVE_F64:
+        xo, it10, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-10)
+        assert abs(st["iterations"] - it10) <= 0.05 * it10 + 8
+    ctx.close()
+
+
+def test_rbcg_host_buffers():
+    L, Ls, mf = (4, 4, 4, 4), 8, 0.05
+    U = synth.random_gauge(L, 0.3, 3)
+    b = synth.gaussian_spinor(L, Ls, 4)
+    ctx = ops.Context(L, Ls, M5, U)
+    from paper_2103_05034_gb300 import layout
+    bh = layout.complex_to_real(layout.to_full(b, L), F64)
+    xh = np.zeros_like(bh)
+    st = ops.rbcg_solve(ctx, xh, bh, mf, 1e-9, 5000, SOLVE_MIXED_F32)
+    xg = layout.from_full(layout.real_to_complex(xh).reshape(2, -1, 4, 3, Ls), L)
+    assert krylov.true_residual(U, xg, b, M5, mf) <= 1e-9 * 1.01
+    ctx.close()
+
+
+def test_rbcg_zero_source_and_maxiter():
+    L, Ls = (4, 4, 4, 4), 4
+    U = synth.random_gauge(L, 0.3, 5)
+    ctx = ops.Context(L, Ls, M5, U)
+    z = ctx.new_full(F64)
+    x = ctx.new_full(F64)
+    st = ops.rbcg_solve(ctx, x, z, 0.01, 1e-8, 10, SOLVE_MIXED_F32)
+    assert st["iterations"] == 0 and float(x.abs().max()) == 0.0
+    b = full_dev(synth.gaussian_spinor(L, Ls, 6), L, F64)
+    with pytest.raises(DWFError) as e:
+        ops.rbcg_solve(ctx, x, b, 0.01, 1e-12, 3, SOLVE_MIXED_F32)
+    assert e.value.code == -3
+    ctx.close()
+
+
+def test_bad_arguments_are_rejected(case):
+    L, Ls, U, ctx = case
+    a = ctx.new_half(F32)
+    with pytest.raises(DWFError) as e:
+        ops.dwf_dhop(ctx, a, a, 2)
+    assert e.value.code == DWF_EINVAL
+    with pytest.raises(DWFError):
+        ops.dwf_mpc(ctx, a, a, 0.01)
+    with pytest.raises(DWFError):
+        ops.dwf_dhop(ctx, a, a, 0, nrhs=0)
+
+
+def test_power_method(case):
+    L, Ls, U, ctx = case
+    mf = 0.05
+    v0 = synth.gaussian_spinor(L, Ls, 17)
+    got = ops.dwf_power_max(ctx, full_dev(v0, L, F64), mf, 30)
+    want = krylov.power_max(lambda v: dwf.mdagm(U, v, M5, mf), v0, 30)
+    assert got == pytest.approx(want, rel=1e-10)
