@@ -1,0 +1,382 @@
+"""Benchmark of the DWF multigrid hot path on GB300.
+
+Metric: D_hop HBM GB/s (the algorithmic bytes of every hopping-term launch of
+the step divided by the step's time), with the mixed-precision red-black CGNR
+solve to a true residual of 1e-8 (Sec. 5.1 of arXiv:2103.05034) as the step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--no-cpu-baseline] [--mg-compare]
+
+One step = one rbcg_solve (FP32 inner CG, FP64 reliable updates, FP64 true
+residual) of D_DW x = b from x = 0 on the 16^3x32, Ls = 16 smeared-random
+workload, inputs resident in HBM.  The L2 is flushed (a 512 MB write) before
+every timed step; each step is timed with CUDA events on the launching stream.
+
+N > 1 (torchrun): every rank solves its own source on its own GPU (replicas,
+weak scaling; the path has no exchange step on one GPU per problem); value =
+all ranks' bytes / max-over-ranks time.
+
+--impl reference: the FP64 numpy oracle timed on the host cores on a bounded
+sample of the same workload (one full-lattice D_hop per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "D_hop HBM GB/s (% of peak); MG vs FP64 RB-CG time to 1e-8 residual, same GPU"
+UNIT = "GB/s"
+
+
+# ---------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash(*rel):
+    h = hashlib.sha256()
+    for r in rel:
+        h.update(open(os.path.join(ROOT, r), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_key, shash):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(kernel_key)
+    except Exception:
+        return None
+    if not d or d.get("source_hash") != shash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def build_workload(name, rank):
+    w = synth.WORKLOADS[name]
+    L, Ls = w["L"], w["Ls"]
+    U = synth.random_gauge(L, w["eps"], synth.SEED_GAUGE, ape_steps=w["ape"])
+    b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE + rank)
+    return w, U, b
+
+
+# ---------------------------------------------------------------------- CPU oracle legs
+def oracle_dhop_sample(w, U, b):
+    """One full-lattice FP64 oracle D_hop; returns (seconds, algorithmic bytes)."""
+    from oracle import dwf
+    L, Ls = w["L"], w["Ls"]
+    t0 = time.perf_counter()
+    dwf.dhop(U, b)
+    dt = time.perf_counter() - t0
+    V5 = int(np.prod(L)) * Ls
+    nbytes = V5 * (24 * 16) + int(np.prod(L)) * 8 * 9 * 16  # FP64 spinors in+out, 8 links per site
+    return dt, nbytes
+
+
+def cpu_baseline_leg(w, U, b):
+    dt, nbytes = oracle_dhop_sample(w, U, b)
+    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full-lattice FP64 numpy D_hop at {'x'.join(map(str, w['L']))}x{w['Ls']} "
+                      f"({dt:.1f} s, single-threaded numpy)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, U, b = build_workload(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_dhop_sample(w, U, b)
+    times, nbytes = [], 0
+    for _ in range(args.steps):
+        dt, nb = oracle_dhop_sample(w, U, b)
+        times.append(dt)
+        nbytes += nb
+    tot = sum(times)
+    val = nbytes / tot / 1e9
+    sample = f"one full-lattice FP64 numpy D_hop at {'x'.join(map(str, w['L']))}x{w['Ls']} per step"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "oracle": "numpy FP64",
+                                             "l2": "n/a (host)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2103_05034_gb300 import layout, ops
+    from paper_2103_05034_gb300._lib import F32, F64, SOLVE_MIXED_F32
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w, U, b = build_workload(args.workload, rank)
+    L, Ls, M5, mf = w["L"], w["Ls"], w["M5"], w["mf"]
+    ctx = ops.Context(L, Ls, M5, U)
+    bfull = layout.complex_to_real(layout.to_full(b, L), F64)
+    bd = torch.from_numpy(bfull).to(dev)
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve(x, bb):
+        return ops.rbcg_solve(ctx, x, bb, mf, args.tol, 100000, SOLVE_MIXED_F32)
+
+    for _ in range(args.warmup):
+        xd.zero_()
+        solve(xd, bd)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    ops.dwf_reset_counters(ctx)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        st = solve(xd, bd)
+        ev[k][1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    launches, hop_bytes = ops.dwf_counters(ctx)
+    t_dev = sum(a.elapsed_time(bq) for a, bq in ev) / 1e3
+    t_max = t_dev
+    tot_bytes = hop_bytes
+    if world > 1:
+        tt = torch.tensor([t_dev, hop_bytes], dtype=torch.float64, device=dev)
+        tmax = tt.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_max, tot_bytes = float(tmax[0]), float(tt[1])
+    value = tot_bytes / t_max / 1e9
+
+    # ---- dominant kernel: the FP32 hopping term, timed alone with an L2 flush before each launch
+    inp = ctx.new_half(F32)
+    inp.copy_(torch.from_numpy(layout.complex_to_real(layout.to_half(b, L, 1), F32).reshape(-1)).to(dev))
+    out = torch.zeros_like(inp)
+    hop_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(20)]
+    for _ in range(3):
+        ops.dwf_dhop(ctx, out, inp, 0)
+    for k, (e0, e1) in enumerate(hop_ev):
+        flush.fill_(float(k))
+        e0.record(stream)
+        ops.dwf_dhop(ctx, out, inp, 0)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    hop_ms = float(np.mean([a.elapsed_time(bq) for a, bq in hop_ev]))
+    Vh = ctx.Vh
+    hop_alg_bytes = Vh * (Ls * 24 * 8 + 72 * 8)
+    peaks, peak_kind = measured_peaks()
+    achieved = hop_alg_bytes / (hop_ms / 1e3) / 1e9
+    shash = source_hash("paper_2103_05034_gb300/csrc/dhop_impl.cuh")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": profile_traffic(f"hop_kernel_f32_ls{Ls}_{args.workload}", shash),
+                "kernel": f"dwfk::hop_kernel<F32, Ls={Ls}> (dwf_dhop, plain epilogue)",
+                "launch_ms": hop_ms, "algorithmic_bytes_per_launch": hop_alg_bytes,
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "source_hash": shash}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    bh = torch.from_numpy(bfull).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    solve(xh, bh)  # warm
+    ops.dwf_reset_counters(ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_stats = []
+    for _ in range(args.steps):
+        e2e_stats.append(solve(xh, bh))
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    _, e2e_bytes = ops.dwf_counters(ctx)
+    if world > 1:
+        tt = torch.tensor([t_e2e, e2e_bytes], dtype=torch.float64, device=dev)
+        tm = tt.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_e2e, e2e_bytes = float(tm[0]), float(tt[1])
+    e2e = {"value": e2e_bytes / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 8),
+           "d2h_bytes_per_step": int(xh.numel() * 8),
+           "note": "rbcg_solve on pinned host b and x: H2D of b and D2H of x inside the call"}
+
+    line = None
+    if rank == 0:
+        s0 = stats[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": list(L), "Ls": Ls, "M5": M5, "mf": mf,
+                       "solver": "red-black CGNR, FP32 inner, FP64 reliable updates",
+                       "tol_true_residual": args.tol, "l2": "flushed (512 MB write) before each step",
+                       "parallelism": f"replicas{world}"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "roofline": roofline,
+            "e2e": e2e,
+            "solve": {"iterations": s0["iterations"], "reliable_updates": s0["reliable_updates"],
+                      "true_residual": s0["true_residual"], "fine_matmuls": s0["fine_matmuls"],
+                      "seconds": t_max / args.steps, "wall_seconds_all_steps": t_wall},
+        }
+        if args.cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline_leg(w, U, b)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_kernel(args):
+    """Kernel-only loop for profiling: `--kernel dhop_f32|dhop_f64|dhop_f16|mpcdagmpc_f32`
+    at the workload's size, warmup + steps launches, no solver."""
+    import torch
+
+    from paper_2103_05034_gb300 import layout, ops
+    from paper_2103_05034_gb300._lib import F16S, F32, F64
+
+    w, U, b = build_workload(args.workload, 0)
+    L, Ls = w["L"], w["Ls"]
+    ctx = ops.Context(L, Ls, w["M5"], U)
+    kind, prec_name = args.kernel.split("_")
+    prec = {"f64": F64, "f32": F32, "f16": F16S}[prec_name]
+    inp = torch.from_numpy(layout.complex_to_real(layout.to_half(b, L, 1), prec)).cuda()
+    out = torch.zeros_like(inp)
+    fn = {"dhop": lambda: ops.dwf_dhop(ctx, out, inp, 0),
+          "mpcdagmpc": lambda: ops.dwf_mpcdag_mpc(ctx, out, inp, w["mf"])}[kind]
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "ms_per_call": ms}))
+    ctx.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dwf_16x16x16x32_ls16", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--kernel", default=None,
+                    help="profile mode: dhop_f32, dhop_f64, dhop_f16 or mpcdagmpc_f32 alone")
+    args = ap.parse_args(argv)
+    if args.kernel:
+        return run_kernel(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

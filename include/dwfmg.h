@@ -114,6 +114,14 @@ const char* dwf_last_error(const dwf_ctx* ctx);
 int64_t dwf_half_sites(const dwf_ctx* ctx);
 int64_t dwf_half_bytes(const dwf_ctx* ctx, int prec);
 
+/* Kernel-launch and traffic counters of a context, for benchmarking:
+ * *launches = kernels this library launched through the context since the
+ * last reset; *hop_bytes = algorithmic (compulsory) bytes of the hopping-term
+ * launches among them: per launch Vh*(Ls*nrhs*(24 [+12 with an aux input])
+ * complex spinor numbers + 72 link complex numbers).  Host-side, no sync. */
+int dwf_counters(const dwf_ctx* ctx, int64_t* launches, double* hop_bytes);
+int dwf_reset_counters(dwf_ctx* ctx);
+
 /* ------------------------------------------------------------------ operators */
 
 /* Wilson hopping term, Eq. (2), between parities: out (parity out_parity) =
@@ -171,10 +179,141 @@ int dwf_cdot(dwf_ctx* ctx, double* result2, const void* a, const void* b, int64_
 int rbcg_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int maxiter,
                int policy, dwf_solve_stats* stats, void* stream);
 
+/* CG on the even normal equations M_pc^dag M_pc x = phi (Sec. 2.1, Eq. 9),
+ * the pseudofermion solve of HMC: phi and x are FP64 even half fields in
+ * device memory; stops when ||phi - M_pc^dag M_pc x|| / ||phi|| <= tol
+ * (FP64, recomputed at every reliable update).  policy DWF_SOLVE_F64 or
+ * DWF_SOLVE_MIXED_F32.  Synchronises. */
+int rbcg_normal_solve(dwf_ctx* ctx, void* x, const void* phi, double mf, double tol, int maxiter,
+                      int policy, dwf_solve_stats* stats, void* stream);
+
+/* Pseudofermion force (HMC context of Sec. 6; the paper prints no force, it
+ * is derived for the Schur operator of Sec. 5.1): for each of npf even fields
+ * X_i = (M_pc^dag M_pc)^-1 phi_i (mass mf[i], host array) this adds to
+ * `force` (device complex128 [T][Z][Y][X][mu][3][3], the gauge layout)
+ *   G_mu(x) = TA(U_mu(x) A_mu(x) - B_mu(x) U_mu(x)^dag),
+ * A_mu(x) = sum_s tr_spin[(1-gamma_mu) X'_s(x+mu) Y'_s(x)^dag],
+ * B_mu(x) = sum_s tr_spin[(1+gamma_mu) X'_s(x) Y'_s(x+mu)^dag],
+ * with Y = M_pc X, X' = X + M_oo^-1 M_oe X, Y' = Y + M_oo^-dag M_eo^dag Y and
+ * TA(M) = (M - M^dag)/2 - tr(M - M^dag)/6.  Convention: for U -> exp(eps Q) U
+ * with Q in su(3), dS/deps = sum Re tr(G^dag Q) where S = sum_i phi_i^dag
+ * (M_pc^dag M_pc)^-1 phi_i.  X: npf even half fields of precision prec (DWF_F64
+ * or DWF_F32), device memory. */
+int dwf_force(dwf_ctx* ctx, void* force, const void* X, const double* mf, int npf, int prec,
+              void* stream);
+
 /* Power method estimate of the largest eigenvalue of D_DW^dag D_DW (Sec. 3.4),
  * `iters` iterations from the FP64 full field v0 (device).  *lmax on host. */
 int dwf_power_max(dwf_ctx* ctx, double* lmax, const void* v0, double mf, int iters,
                   void* stream);
+
+/* ------------------------------------------------------------------ subspace setup */
+
+/* Chebyshev filter (Sec. 3.2, Eq. 23; Sec. 3.4, Eq. 34): out = T_order(x(A)) in
+ * for nrhs full fields, A = D_DW^dag D_DW, x(A) = 2(A - lo)/(hi - lo) - 1, by
+ * the three-term recurrence.  prec DWF_F64 or DWF_F32.  Returns DWF_ERANGE if
+ * the result overflows (the spectrum of A reaches far beyond [lo, hi]). */
+int cheby_filter(dwf_ctx* ctx, void* out, const void* in, int nrhs, double lo, double hi, int order,
+                 double mf, int prec, void* stream);
+
+/* Recursive subspace filter of Sec. 3.4 (Eqs. 34-37): phi_0 = T_m(2(A -
+ * lam_lo)/(lam_max - lam_lo) - 1) eta, then phi_k = T_{k delta}(2A/lam_max - 1)
+ * phi_0 for k = 1..nvec-1 as snapshots of one recurrence (cost m + (nvec-1)
+ * delta applications of A).  eta is one full field, phi receives nvec full
+ * fields, each normalised to unit norm.  Synchronises. */
+int cheby_recursive_basis(dwf_ctx* ctx, void* phi, const void* eta, double lam_lo, double lam_max,
+                          int m, int delta, int nvec, double mf, int prec, void* stream);
+
+/* Chirality projection (Sec. 3.4, last paragraph): out = (1 + sign Gamma_5)/2
+ * in on nrhs full fields, Gamma_5 = gamma_5 R_5; sign = +1 or -1; out may
+ * equal in.  prec DWF_F64 or DWF_F32. */
+int dwf_chiral_project(dwf_ctx* ctx, void* out, const void* in, int sign, int prec, int nrhs,
+                       void* stream);
+
+/* Block orthonormalisation of nb FP64 full fields in place so that P^dag P = 1
+ * (implied by Sec. 3.1, Eq. 18): blocks are block[0..3] 4D sites times all of
+ * Ls; vectors 0..nplus-1 and nplus..nb-1 (the two chiralities) are
+ * orthonormalised separately, in index order, by Cholesky-QR applied twice
+ * (the same Q as modified Gram-Schmidt in exact arithmetic).  Groups of at
+ * most 32 vectors.  DWF_ERANGE if the vectors are dependent on a block. */
+int block_orthonormalise(dwf_ctx* ctx, void* basis, int nb, int nplus, const int block[4],
+                         void* stream);
+
+/* ------------------------------------------------------------------ coarse operator */
+
+/* Little Dirac operator of H_DW (Sec. 3.1, Eq. 18; Table 1 "Coarsening H_DW"):
+ * A_d(x)_{jk} = <phi^x_j, H^(d) phi^{x+d}_k> for the 9 stencil directions d =
+ * 0 (self), +x, -x, +y, -y, +z, -z, +t, -t, on the coarse lattice L/block.
+ * basis: nb orthonormal block vectors as full fields of precision prec
+ * (DWF_F64 or DWF_F32); vectors 0..nplus-1 have Gamma_5 = +1.  The library
+ * owns the result (FP64 and FP32 copies). */
+int coarse_build(dwf_ctx* ctx, const void* basis, int nb, int nplus, const int block[4], double mf,
+                 int prec, dwf_coarse** coarse, void* stream);
+int coarse_destroy(dwf_coarse* coarse);
+/* Copy the FP64 operator to A (host or device, complex128 [nc][9][nb][nb],
+ * row j, column k) and/or its shape to dims = {Lc_x, Lc_y, Lc_z, Lc_t, nb}. */
+int coarse_export(const dwf_coarse* coarse, void* A, int* dims);
+/* out(x) = sum_d A_d(x) in(x+d) for nrhs coarse vectors, FP32 complex, layout
+ * [nc][nb][nrhs] (coarse site lexicographic in Lc, basis index, rhs). */
+int coarse_apply(dwf_coarse* coarse, void* out, const void* in, int nrhs, void* stream);
+/* Coarse solve of Table 1 ("Coarse solver: CGNR"): CG on A^2 e = A r for one
+ * FP32 coarse vector, stopping when the normal residual is below tol times its
+ * initial value or after maxiter iterations (*iters receives the count). */
+int coarse_solve(dwf_coarse* coarse, void* e, const void* r, double tol, int maxiter, int* iters,
+                 void* stream);
+/* Restriction P^dag (out: FP32 coarse [nc][nb][nrhs]) and prolongation P
+ * (out: nrhs full fields, += when accumulate) with a block basis of nb full
+ * fields of precision prec (DWF_F64 or DWF_F32). */
+int dwf_restrict(dwf_ctx* ctx, void* out, const void* in, const void* basis, int nb,
+                 const int block[4], int nrhs, int prec, void* stream);
+int dwf_prolong(dwf_ctx* ctx, void* out, const void* in, const void* basis, int nb,
+                const int block[4], int nrhs, int prec, int accumulate, void* stream);
+
+/* ------------------------------------------------------------------ HDCR multigrid */
+
+#define DWF_SUBSPACE_BATCH 0     /* nbasis Gaussians filtered together by T_order */
+#define DWF_SUBSPACE_RECURSIVE 1 /* nbasis/2 vectors from one Gaussian (Sec. 3.4) */
+
+/* Parameters of Table 1 (Algorithms A, B) and Table 12 (Algorithm H). */
+typedef struct dwf_mg_params {
+  int block[4];          /* 4D block; the block spans all of Ls */
+  int nbasis;            /* basis vectors after chirality projection (even, <= 64) */
+  int subspace_mode;     /* DWF_SUBSPACE_* */
+  double mf;             /* quark mass of D_DW */
+  double lambda_lo;      /* subspace lambda_lo */
+  double lambda_max;     /* subspace lambda_max (must bound spec(D^dag D)) */
+  int filter_order;      /* m (recursive) or the batch filter order */
+  int delta;             /* Delta of the recursive filter */
+  double smooth_lo;      /* smoother interval [a, b] of S_cheb([a,b],N) on H_DW^2 */
+  double smooth_hi;
+  int smooth_order;      /* N */
+  double coarse_tol;     /* coarse CG relative tolerance (0.02 in Table 12) */
+  int coarse_maxiter;
+  int nkrylov;           /* GCR restart length */
+  int maxiter;           /* outer iterations */
+} dwf_mg_params;
+
+/* Build the multigrid setup: filtered vectors from eta (nbasis FP64 full fields
+ * in batch mode, one in recursive mode; device memory), chirality projection
+ * ((1+Gamma_5)/2 for the first nbasis/2, (1-Gamma_5)/2 for the rest), FP64
+ * block orthonormalisation, FP32 basis storage and the little Dirac operator
+ * of H_DW.  Synchronises.  The context must outlive the setup. */
+int mg_setup(dwf_ctx* ctx, const dwf_mg_params* params, const void* eta, dwf_mg** mg, void* stream);
+int mg_destroy(dwf_mg* mg);
+/* Copy the FP32 basis (nbasis full fields) to out (host or device). */
+int mg_export_basis(const dwf_mg* mg, void* out);
+/* The setup's coarse operator (owned by the setup). */
+dwf_coarse* mg_coarse(dwf_mg* mg);
+/* The Chebyshev smoother S_cheb (Sec. 3.2, Eqs. 24-25, with M = M^dag = H_DW)
+ * and the V(1,1) preconditioner (Sec. 3.3, Eqs. 26-28, x0 = 0) applied to one
+ * FP32 full field.  Synchronise. */
+int mg_smooth(dwf_mg* mg, void* out, const void* in, void* stream);
+int mg_precondition(dwf_mg* mg, void* out, const void* in, void* stream);
+/* HDCR solve of D_DW x = b (Table 1: outer pGCR(H_DW)): flexible GCR on
+ * H_DW x = Gamma_5 b preconditioned by V(1,1), FP64 x and true residual, FP32
+ * directions; stops when ||b - D_DW x|| / ||b|| <= tol.  b, x: FP64 full
+ * fields, host or device.  stats->fine_matmuls counts H_DW applications. */
+int mg_solve(dwf_mg* mg, void* x, const void* b, double tol, dwf_solve_stats* stats, void* stream);
 
 #ifdef __cplusplus
 }

@@ -33,25 +33,15 @@ class SolveStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
-_SIGS = {
-    "dwf_ctx_create": (I, [C.POINTER(P), C.POINTER(C.c_int), I, D, P, P]),
-    "dwf_ctx_destroy": (I, [P]),
-    "dwf_last_error": (C.c_char_p, [P]),
-    "dwf_half_sites": (I64, [P]),
-    "dwf_half_bytes": (I64, [P, I]),
-    "dwf_dhop": (I, [P, P, P, I, I, I, I, P]),
-    "dwf_mooee": (I, [P, P, P, D, I, I, I, P]),
-    "dwf_mooee_inv": (I, [P, P, P, D, I, I, I, P]),
-    "dwf_mpc": (I, [P, P, P, D, I, I, I, P]),
-    "dwf_mpcdag_mpc": (I, [P, P, P, D, I, I, P]),
-    "dwf_ddw": (I, [P, P, P, D, I, I, I, P]),
-    "dwf_hdw": (I, [P, P, P, D, I, I, P]),
-    "dwf_norm2": (I, [P, C.POINTER(D), P, I64, I, P]),
-    "dwf_cdot": (I, [P, C.POINTER(D), P, P, I64, I, P]),
-    "rbcg_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
-    "dwf_power_max": (I, [P, C.POINTER(D), P, D, I, P]),
-}
+SUBSPACE_BATCH, SUBSPACE_RECURSIVE = 0, 1
+
+
+class MGParams(C.Structure):
+    _fields_ = [("block", C.c_int * 4), ("nbasis", C.c_int), ("subspace_mode", C.c_int),
+                ("mf", C.c_double), ("lambda_lo", C.c_double), ("lambda_max", C.c_double),
+                ("filter_order", C.c_int), ("delta", C.c_int), ("smooth_lo", C.c_double),
+                ("smooth_hi", C.c_double), ("smooth_order", C.c_int), ("coarse_tol", C.c_double),
+                ("coarse_maxiter", C.c_int), ("nkrylov", C.c_int), ("maxiter", C.c_int)]
 
 
 def header_functions():
@@ -91,3 +81,47 @@ def check(code, ctx=None):
         msg = lib().dwf_last_error(ctx).decode() if ctx else ""
         raise DWFError(code, msg)
     return code
+
+
+P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+_SIGS = {
+    "dwf_ctx_create": (I, [C.POINTER(P), C.POINTER(C.c_int), I, D, P, P]),
+    "dwf_ctx_destroy": (I, [P]),
+    "dwf_last_error": (C.c_char_p, [P]),
+    "dwf_half_sites": (I64, [P]),
+    "dwf_half_bytes": (I64, [P, I]),
+    "dwf_counters": (I, [P, C.POINTER(I64), C.POINTER(D)]),
+    "dwf_reset_counters": (I, [P]),
+    "dwf_dhop": (I, [P, P, P, I, I, I, I, P]),
+    "dwf_mooee": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_mooee_inv": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_mpc": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_mpcdag_mpc": (I, [P, P, P, D, I, I, P]),
+    "dwf_ddw": (I, [P, P, P, D, I, I, I, P]),
+    "dwf_hdw": (I, [P, P, P, D, I, I, P]),
+    "dwf_norm2": (I, [P, C.POINTER(D), P, I64, I, P]),
+    "dwf_cdot": (I, [P, C.POINTER(D), P, P, I64, I, P]),
+    "rbcg_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
+    "dwf_power_max": (I, [P, C.POINTER(D), P, D, I, P]),
+    "dwf_force": (I, [P, P, P, C.POINTER(D), I, I, P]),
+    "rbcg_normal_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
+    "cheby_filter": (I, [P, P, P, I, D, D, I, D, I, P]),
+    "cheby_recursive_basis": (I, [P, P, P, D, D, I, I, I, D, I, P]),
+    "dwf_chiral_project": (I, [P, P, P, I, I, I, P]),
+    "block_orthonormalise": (I, [P, P, I, I, C.POINTER(C.c_int), P]),
+    "coarse_build": (I, [P, P, I, I, C.POINTER(C.c_int), D, I, C.POINTER(P), P]),
+    "coarse_destroy": (I, [P]),
+    "coarse_export": (I, [P, P, C.POINTER(C.c_int)]),
+    "coarse_apply": (I, [P, P, P, I, P]),
+    "coarse_solve": (I, [P, P, P, D, I, C.POINTER(C.c_int), P]),
+    "dwf_restrict": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, P]),
+    "dwf_prolong": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, I, P]),
+    "mg_setup": (I, [P, C.POINTER(MGParams), P, C.POINTER(P), P]),
+    "mg_destroy": (I, [P]),
+    "mg_export_basis": (I, [P, P]),
+    "mg_coarse": (P, [P]),
+    "mg_smooth": (I, [P, P, P, P]),
+    "mg_precondition": (I, [P, P, P, P]),
+    "mg_solve": (I, [P, P, P, D, C.POINTER(SolveStats), P]),
+}
+

@@ -248,6 +248,24 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
       return dwf_fail(c, DWF_EINVAL, "bad precision");
   }
   if (rc) return dwf_fail(c, rc, "unsupported Ls");
+  c->launches++;
+  const double w = (double)dwf_complex_bytes(prec), wl = prec == DWF_F64 ? 16.0 : 8.0;
+  c->hop_bytes += (double)c->g.Vh * ((double)c->g.Ls * h.nrhs * (24.0 + (h.aux_mode ? 12.0 : 0.0)) * w +
+                                     72.0 * wl);
+  return DWF_OK;
+}
+
+extern "C" int dwf_counters(const dwf_ctx* c, int64_t* launches, double* hop_bytes) {
+  if (!c) return DWF_EINVAL;
+  if (launches) *launches = c->launches;
+  if (hop_bytes) *hop_bytes = c->hop_bytes;
+  return DWF_OK;
+}
+
+extern "C" int dwf_reset_counters(dwf_ctx* c) {
+  if (!c) return DWF_EINVAL;
+  c->launches = 0;
+  c->hop_bytes = 0;
   return DWF_OK;
 }
 
@@ -274,6 +292,7 @@ int launch_mooee(dwf_ctx* c, void* out, const void* in, const double* mf, int da
       return dwf_fail(c, DWF_EINVAL, "bad precision");
   }
   if (rc) return dwf_fail(c, rc, "unsupported Ls");
+  c->launches++;
   return DWF_OK;
 }
 
@@ -338,7 +357,7 @@ extern "C" int dwf_mooee_inv(dwf_ctx* c, void* out, const void* in, double mf, i
 // M_pc (dagger=0) or M_pc^dag (dagger=1) on nrhs even fields, odd temporary tmp.
 // M_pc    = M_ee + 1/2 D_eo M_oo^-1 (-1/2 D_oe)
 // M_pc^dag = M_ee^dag + 1/2 D^dag_eo M_oo^-dag (-1/2 D^dag_oe)
-static int mpc_apply(dwf_ctx* c, void* out, const void* in, void* tmp, const double* mf, int dagger,
+int mpc_apply(dwf_ctx* c, void* out, const void* in, void* tmp, const double* mf, int dagger,
                      int prec, int nrhs, int reduce, cudaStream_t st, int* nparts) {
   HopLaunch h1 = hop_base(tmp, in, 1, dagger, nrhs, -0.5);
   h1.inv_mode = dagger ? 2 : 1;
@@ -390,8 +409,8 @@ extern "C" int dwf_mpcdag_mpc(dwf_ctx* c, void* out, const void* in, double mf, 
 }
 
 // Full-lattice D_DW (or D_DW^dag, or H_DW = Gamma_5 D_DW when g5 = 1) of nrhs full fields.
-static int ddw_apply(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int g5,
-                     int prec, int nrhs, cudaStream_t st) {
+int ddw_apply(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int g5, int prec,
+              int nrhs, cudaStream_t st) {
   const int64_t he = half_elems(c);
   const size_t cb = dwf_complex_bytes(prec);
   for (int po = 0; po < 2; po++) {
@@ -433,14 +452,14 @@ extern "C" int dwf_hdw(dwf_ctx* c, void* out, const void* in, double mf, int pre
 }
 
 // ------------------------------------------------------------------ reductions (host results)
-static int read_scalars(dwf_ctx* c, int first, int n, cudaStream_t st) {
+int read_scalars(dwf_ctx* c, int first, int n, cudaStream_t st) {
   DWF_CUDA(c, cudaMemcpyAsync(c->hscal + first, c->dscal + first, n * sizeof(double),
                               cudaMemcpyDeviceToHost, st));
   DWF_CUDA(c, cudaStreamSynchronize(st));
   return DWF_OK;
 }
 
-static int norm2_dev(dwf_ctx* c, const void* a, int64_t n, int prec, int dst, cudaStream_t st) {
+int norm2_dev(dwf_ctx* c, const void* a, int64_t n, int prec, int dst, cudaStream_t st) {
   int np = 0;
   int rc = blas_norm2_partials(c, a, n, prec, st, &np);
   if (rc) return rc;
@@ -517,6 +536,117 @@ static int cg_apply(dwf_ctx* c, void* Ap, const void* p, void* y, void* todd, co
   rc = blas_finalize_mode(c, np, 1, S_PAP, 1, st);
   if (rc) return rc;
   return mpc_apply(c, Ap, y, todd, mf, 1, prec, 1, 0, st, nullptr);
+}
+
+// CG on M_pc^dag M_pc x_e = rhs with FP64 reliable updates.  With bp set (the
+// red-black solve) the stopping residual is the Schur residual |b'_e - M_pc x|
+// / bnorm, which equals the full true residual after reconstruction; without
+// it (normal-equation solve) it is |rhs - M^dag M x| / bnorm.  x_e holds the
+// FP64 solution; the caller owns every buffer.
+struct CGBufs {
+  void *rhs, *bp, *rhi, *yhi, *ohi, *xlo, *rlo, *p, *Ap, *ylo, *olo;
+};
+
+static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, double tol, int maxiter, int plo,
+                   const double* mfa, dwf_solve_stats& S, double& matmuls, cudaStream_t st) {
+  const int64_t he = half_elems(c);
+  const size_t b64 = he * 16, blo = he * dwf_complex_bytes(plo);
+  int rc;
+  DWF_CUDA(c, cudaMemsetAsync(x_e, 0, b64, st));
+  void* xin = plo == DWF_F64 ? (void*)x_e : B.xlo;  // inner accumulator
+  const double delta = 0.1;
+  double true_res = 0, rr_hi = 0, rho = 1, rr_max = 0, rr_lo = 0;
+  bool have_x = false;
+  void *rhi = B.rhi, *yhi = B.yhi, *ohi = B.ohi, *xlo = B.xlo, *rlo = B.rlo, *p = B.p, *Ap = B.Ap;
+
+  auto reliable = [&]() -> int {
+    int r;
+    if (have_x && plo != DWF_F64) {
+      r = blas_axpby(c, 1.0, xlo, plo, 1.0, x_e, DWF_F64, he, st);
+      if (r) return r;
+    }
+    if (plo != DWF_F64) DWF_CUDA(c, cudaMemsetAsync(xlo, 0, blo, st));
+    if (have_x) {
+      r = mpc_apply(c, yhi, x_e, ohi, mfa, 0, DWF_F64, 1, 0, st, nullptr);
+      if (r) return r;
+      if (B.bp) {  // y = b'_e - M_pc x; r = M_pc^dag y
+        r = blas_axpby(c, 1.0, B.bp, DWF_F64, -1.0, yhi, DWF_F64, he, st);
+        if (r) return r;
+        r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+        if (r) return r;
+        r = norm2_dev(c, yhi, he, DWF_F64, S_TMP2, st);
+      } else {  // r = rhs - M^dag M x
+        r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+        if (r) return r;
+        r = blas_axpby(c, 1.0, B.rhs, DWF_F64, -1.0, rhi, DWF_F64, he, st);
+        if (r) return r;
+        r = norm2_dev(c, rhi, he, DWF_F64, S_TMP2, st);
+      }
+      if (r) return r;
+      matmuls += 4;
+    } else {
+      r = blas_copy(c, rhi, DWF_F64, B.rhs, DWF_F64, he, st);
+      if (r) return r;
+      r = norm2_dev(c, B.bp ? B.bp : B.rhs, he, DWF_F64, S_TMP2, st);
+      if (r) return r;
+    }
+    r = norm2_dev(c, rhi, he, DWF_F64, S_TMP3, st);
+    if (r) return r;
+    r = blas_copy(c, rlo, plo, rhi, DWF_F64, he, st);
+    if (r) return r;
+    r = norm2_dev(c, rlo, he, plo, S_RR, st);
+    if (r) return r;
+    r = read_scalars(c, S_TMP2, 2, st);
+    if (r) return r;
+    true_res = sqrt(c->hscal[S_TMP2]) / bnorm;
+    rr_hi = c->hscal[S_TMP3];
+    rho = rr_hi > 0 ? sqrt(c->hscal[S_TMP2] / rr_hi) : 1.0;
+    rr_max = rr_hi;
+    rr_lo = rr_hi;
+    have_x = true;
+    S.reliable_updates++;
+    if (!isfinite(true_res) || !isfinite(rr_hi)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
+    return DWF_OK;
+  };
+
+  rc = reliable();
+  if (rc) return rc;
+  S.reliable_updates = 0;
+  rc = blas_copy(c, p, plo, rlo, plo, he, st);
+  if (rc) return rc;
+  int it = 0;
+  const int check_every = 8;
+  bool converged = true_res <= tol;
+  while (!converged && it < maxiter) {
+    rc = cg_apply(c, Ap, p, B.ylo, B.olo, mfa, plo, st);
+    if (rc) return rc;
+    int np = 0;
+    rc = blas_cg_xr(c, xin, rlo, p, Ap, he, plo, S_ALPHA, st, &np);
+    if (rc) return rc;
+    rc = blas_finalize_mode(c, np, 1, S_RRNEW, 2, st);
+    if (rc) return rc;
+    rc = blas_cg_p(c, p, rlo, he, plo, S_BETA, st);
+    if (rc) return rc;
+    matmuls += 4;
+    it++;
+    if (it % check_every == 0 || it == maxiter) {
+      rc = read_scalars(c, S_RR, 1, st);
+      if (rc) return rc;
+      rr_lo = c->hscal[S_RR];
+      if (!isfinite(rr_lo)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
+      if (rr_lo > rr_max) rr_max = rr_lo;
+      const double predicted = rho * sqrt(rr_lo) / bnorm;
+      if (rr_lo < delta * delta * rr_max || predicted <= tol || it == maxiter) {
+        rc = reliable();
+        if (rc) return rc;
+        converged = true_res <= tol;
+        // the recurrence continues from the new residual: rr = |r_new|^2
+      }
+    }
+  }
+  S.iterations = it;
+  S.true_residual = true_res;
+  return DWF_OK;
 }
 
 extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double tol, int maxiter,
@@ -600,93 +730,10 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
   if (rc) return rc;
   matmuls += 3;
 
-  // x_e = 0 (FP64 accumulator); the first reliable update sets r = rhs.
-  DWF_CUDA(c, cudaMemsetAsync(x_e, 0, b64, st));
-  void* xin = plo == DWF_F64 ? (void*)x_e : xlo;  // inner accumulator
-  const double delta = 0.1;
-  double true_res = 0, rr_hi = 0, rho = 1, rr_max = 0, rr_lo = 0;
-  bool have_x = false;
-
-  // Reliable update: x_hi += x_lo; y = b'_e - M_pc x_hi; true residual |y|/|b|;
-  // r_hi = M_pc^dag y; r_lo = r_hi.
-  auto reliable = [&]() -> int {
-    int r;
-    if (have_x && plo != DWF_F64) {
-      r = blas_axpby(c, 1.0, xlo, plo, 1.0, x_e, DWF_F64, he, st);
-      if (r) return r;
-    }
-    if (plo != DWF_F64) DWF_CUDA(c, cudaMemsetAsync(xlo, 0, blo, st));
-    if (have_x) {
-      r = mpc_apply(c, yhi, x_e, ohi, mfa, 0, DWF_F64, 1, 0, st, nullptr);
-      if (r) return r;
-      r = blas_axpby(c, 1.0, bp, DWF_F64, -1.0, yhi, DWF_F64, he, st);
-      if (r) return r;
-      r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
-      if (r) return r;
-      matmuls += 4;
-      r = norm2_dev(c, yhi, he, DWF_F64, S_TMP2, st);
-      if (r) return r;
-    } else {
-      r = blas_copy(c, rhi, DWF_F64, rhs, DWF_F64, he, st);
-      if (r) return r;
-      r = norm2_dev(c, bp, he, DWF_F64, S_TMP2, st);
-      if (r) return r;
-    }
-    r = norm2_dev(c, rhi, he, DWF_F64, S_TMP3, st);
-    if (r) return r;
-    r = blas_copy(c, rlo, plo, rhi, DWF_F64, he, st);
-    if (r) return r;
-    r = norm2_dev(c, rlo, he, plo, S_RR, st);
-    if (r) return r;
-    r = read_scalars(c, S_TMP2, 2, st);
-    if (r) return r;
-    true_res = sqrt(c->hscal[S_TMP2]) / bnorm;
-    rr_hi = c->hscal[S_TMP3];
-    rho = rr_hi > 0 ? sqrt(c->hscal[S_TMP2] / rr_hi) : 1.0;
-    rr_max = rr_hi;
-    rr_lo = rr_hi;
-    have_x = true;
-    S.reliable_updates++;
-    if (!isfinite(true_res) || !isfinite(rr_hi)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
-    return DWF_OK;
-  };
-
-  rc = reliable();
+  CGBufs B = {rhs, bp, rhi, yhi, ohi, xlo, rlo, p, Ap, ylo, olo};
+  rc = cg_core(c, x_e, B, bnorm, tol, maxiter, plo, mfa, S, matmuls, st);
   if (rc) return rc;
-  S.reliable_updates = 0;
-  rc = blas_copy(c, p, plo, rlo, plo, he, st);
-  if (rc) return rc;
-  int it = 0;
-  const int check_every = 8;
-  bool converged = true_res <= tol;
-  while (!converged && it < maxiter) {
-    rc = cg_apply(c, Ap, p, ylo, olo, mfa, plo, st);
-    if (rc) return rc;
-    int np = 0;
-    rc = blas_cg_xr(c, xin, rlo, p, Ap, he, plo, S_ALPHA, st, &np);
-    if (rc) return rc;
-    rc = blas_finalize_mode(c, np, 1, S_RRNEW, 2, st);
-    if (rc) return rc;
-    rc = blas_cg_p(c, p, rlo, he, plo, S_BETA, st);
-    if (rc) return rc;
-    matmuls += 4;
-    it++;
-    if (it % check_every == 0 || it == maxiter) {
-      rc = read_scalars(c, S_RR, 1, st);
-      if (rc) return rc;
-      rr_lo = c->hscal[S_RR];
-      if (!isfinite(rr_lo)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
-      if (rr_lo > rr_max) rr_max = rr_lo;
-      const double predicted = rho * sqrt(rr_lo) / bnorm;
-      if (rr_lo < delta * delta * rr_max || predicted <= tol || it == maxiter) {
-        rc = reliable();
-        if (rc) return rc;
-        converged = true_res <= tol;
-        // continue the recurrence from the new residual: rr = |r_new|^2
-      }
-    }
-  }
-  S.iterations = it;
+
 
   // x_o = M_oo^-1 (b_o + 1/2 D_oe x_e)
   {
@@ -717,6 +764,58 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
   S.seconds = timer.sec();
   S.status = S.true_residual <= tol ? DWF_OK : DWF_ENOCONV;
   DWF_CUDA(c, cudaGetLastError());
+  if (stats) *stats = S;
+  if (S.status == DWF_ENOCONV) return dwf_fail(c, DWF_ENOCONV, "maxiter reached before tol");
+  return DWF_OK;
+}
+
+extern "C" int rbcg_normal_solve(dwf_ctx* c, void* x, const void* phi, double mf, double tol, int maxiter,
+                                 int policy, dwf_solve_stats* stats, void* stream) {
+  Timer timer;
+  if (!c || !x || !phi) return DWF_EINVAL;
+  if (!(tol > 0) || maxiter < 1) return dwf_fail(c, DWF_EINVAL, "bad tol or maxiter");
+  if (policy != DWF_SOLVE_F64 && policy != DWF_SOLVE_MIXED_F32) return dwf_fail(c, DWF_EINVAL, "bad policy");
+  if (!dwf_is_device_ptr(x) || !dwf_is_device_ptr(phi)) return dwf_fail(c, DWF_EINVAL, "device buffers required");
+  if (((uintptr_t)x & 15) || ((uintptr_t)phi & 15)) return dwf_fail(c, DWF_EINVAL, "alignment");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int plo = policy == DWF_SOLVE_F64 ? DWF_F64 : DWF_F32;
+  const int64_t he = half_elems(c);
+  const size_t b64 = he * 16, blo = he * dwf_complex_bytes(plo);
+  dwf_solve_stats S;
+  memset(&S, 0, sizeof(S));
+  CGBufs B;
+  B.rhs = (void*)phi;
+  B.bp = nullptr;
+  B.rhi = dwf_workspace(c, WS_RHI, b64);
+  B.yhi = dwf_workspace(c, WS_YHI, b64);
+  B.ohi = dwf_workspace(c, WS_OHI, b64);
+  B.xlo = plo == DWF_F64 ? nullptr : dwf_workspace(c, WS_XLO, blo);
+  B.rlo = dwf_workspace(c, WS_RLO, blo);
+  B.p = dwf_workspace(c, WS_P, blo);
+  B.Ap = dwf_workspace(c, WS_AP, blo);
+  B.ylo = dwf_workspace(c, WS_YLO, blo);
+  B.olo = dwf_workspace(c, WS_OLO, blo);
+  if (!B.rhi || !B.yhi || !B.ohi || (plo != DWF_F64 && !B.xlo) || !B.rlo || !B.p || !B.Ap || !B.ylo || !B.olo)
+    return dwf_fail(c, DWF_ENOMEM, "solver workspace");
+  int rc = norm2_dev(c, phi, he, DWF_F64, S_TMP1, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP1, 1, st);
+  if (rc) return rc;
+  const double bnorm = sqrt(c->hscal[S_TMP1]);
+  if (!(bnorm > 0)) {
+    DWF_CUDA(c, cudaMemsetAsync(x, 0, b64, st));
+    DWF_CUDA(c, cudaStreamSynchronize(st));
+    if (stats) *stats = S;
+    return bnorm == 0 ? DWF_OK : dwf_fail(c, DWF_ENAN, "source is not finite");
+  }
+  const double mfa[1] = {mf};
+  double matmuls = 0;
+  rc = cg_core(c, (double2*)x, B, bnorm, tol, maxiter, plo, mfa, S, matmuls, st);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaStreamSynchronize(st));
+  S.fine_matmuls = matmuls / 2.0;
+  S.seconds = timer.sec();
+  S.status = S.true_residual <= tol ? DWF_OK : DWF_ENOCONV;
   if (stats) *stats = S;
   if (S.status == DWF_ENOCONV) return dwf_fail(c, DWF_ENOCONV, "maxiter reached before tol");
   return DWF_OK;

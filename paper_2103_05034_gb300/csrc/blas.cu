@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(BT) k_cdot(const typename Prec<P>::S* a, const
 // mode 0: dscal[dst..] = sums; 1: alpha = rr/pAp after storing pAp;
 // 2: beta = rrnew/rr, rr = rrnew after storing rrnew.
 __global__ void __launch_bounds__(BT) k_finalize(const double* part, int n, int width, double* dscal,
-                                                 int dst, int mode) {
+                                                 int dst, int mode, int base) {
   __shared__ double sh[BT / 32];
   for (int k = 0; k < width; k++) {
     double acc = 0.0;
@@ -66,11 +66,12 @@ __global__ void __launch_bounds__(BT) k_finalize(const double* part, int n, int 
     if (threadIdx.x == 0) dscal[dst + k] = t;
   }
   if (threadIdx.x == 0) {
+    double* q = dscal + base;
     if (mode == 1) {
-      dscal[S_ALPHA] = dscal[S_RR] / dscal[S_PAP];
+      q[S_ALPHA] = q[S_RR] / q[S_PAP];
     } else if (mode == 2) {
-      dscal[S_BETA] = dscal[S_RRNEW] / dscal[S_RR];
-      dscal[S_RR] = dscal[S_RRNEW];
+      q[S_BETA] = q[S_RRNEW] / q[S_RR];
+      q[S_RR] = q[S_RRNEW];
     }
   }
 }
@@ -134,6 +135,60 @@ __global__ void __launch_bounds__(BT) k_cg_p(typename Prec<P>::S* p, const typen
   }
 }
 
+template <int P>
+__global__ void __launch_bounds__(BT) k_axpbypcz(double a, const typename Prec<P>::S* x, double b,
+                                                 const typename Prec<P>::S* y, double cz,
+                                                 typename Prec<P>::S* z, long long n) {
+  typedef typename Prec<P>::R R;
+  for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    const auto xv = ld_c(x + i);
+    const auto yv = ld_c(y + i);
+    const auto zv = ld_c(z + i);
+    cpx<R> o;
+    o.re = (R)a * xv.re + (R)b * yv.re + (R)cz * zv.re;
+    o.im = (R)a * xv.im + (R)b * yv.im + (R)cz * zv.im;
+    st_c(z + i, o);
+  }
+}
+
+// Chebyshev step: tp <- ta * Ax + tb * x - tp (the next T), acc += cacc * tp.
+template <int P>
+__global__ void __launch_bounds__(BT) k_cheb_step(typename Prec<P>::S* tp, const typename Prec<P>::S* Ax,
+                                                  const typename Prec<P>::S* x, double ta, double tb,
+                                                  typename Prec<P>::S* acc, double cacc, long long n) {
+  typedef typename Prec<P>::R R;
+  for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    const auto av = ld_c(Ax + i);
+    const auto xv = ld_c(x + i);
+    const auto pv = ld_c(tp + i);
+    cpx<R> o;
+    o.re = (R)ta * av.re + (R)tb * xv.re - pv.re;
+    o.im = (R)ta * av.im + (R)tb * xv.im - pv.im;
+    st_c(tp + i, o);
+    if (acc) {
+      auto cv = ld_c(acc + i);
+      cv.re += (R)cacc * o.re;
+      cv.im += (R)cacc * o.im;
+      st_c(acc + i, cv);
+    }
+  }
+}
+
+// y += (ar + i ai) x, any precision pair.
+template <int PX, int PY>
+__global__ void __launch_bounds__(BT) k_caxpy(double ar, double ai, const typename Prec<PX>::S* x,
+                                              typename Prec<PY>::S* y, long long n) {
+  typedef typename Prec<PY>::R RY;
+  for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    const auto xv = ld_c(x + i);
+    const auto yv = ld_c(y + i);
+    cpx<RY> o;
+    o.re = (RY)((double)yv.re + ar * xv.re - ai * xv.im);
+    o.im = (RY)((double)yv.im + ar * xv.im + ai * xv.re);
+    st_c(y + i, o);
+  }
+}
+
 __global__ void k_div(double* dscal, int dst, int num, int den) { dscal[dst] = dscal[num] / dscal[den]; }
 
 int grid_for(long long n) {
@@ -165,6 +220,7 @@ int grid_for(long long n) {
 
 int blas_norm2_partials(dwf_ctx* c, const void* a, int64_t n, int prec, cudaStream_t st, int* nparts) {
   const int g = grid_for(n);
+  c->launches++;
   DWF_PREC_SWITCH(prec, (k_norm2<P><<<g, BT, 0, st>>>((const typename Prec<P>::S*)a, n, c->partials)));
   *nparts = g;
   return DWF_OK;
@@ -173,14 +229,16 @@ int blas_norm2_partials(dwf_ctx* c, const void* a, int64_t n, int prec, cudaStre
 int blas_cdot_partials(dwf_ctx* c, const void* a, const void* b, int64_t n, int prec, cudaStream_t st,
                        int* nparts) {
   const int g = grid_for(n);
+  c->launches++;
   DWF_PREC_SWITCH(prec, (k_cdot<P><<<g, BT, 0, st>>>((const typename Prec<P>::S*)a,
                                                        (const typename Prec<P>::S*)b, n, c->partials)));
   *nparts = g;
   return DWF_OK;
 }
 
-int blas_finalize_mode(dwf_ctx* c, int nparts, int width, int dst, int mode, cudaStream_t st) {
-  k_finalize<<<1, BT, 0, st>>>(c->partials, nparts, width, c->dscal, dst, mode);
+int blas_finalize_mode(dwf_ctx* c, int nparts, int width, int dst, int mode, cudaStream_t st, int base) {
+  c->launches++;
+  k_finalize<<<1, BT, 0, st>>>(c->partials, nparts, width, c->dscal, dst, mode, base);
   return DWF_OK;
 }
 
@@ -191,6 +249,7 @@ int blas_finalize(dwf_ctx* c, int nparts, int width, int dst, cudaStream_t st) {
 int blas_axpby(dwf_ctx* c, double a, const void* x, int px, double b, void* y, int py, int64_t n,
                cudaStream_t st) {
   const int g = grid_for(n);
+  c->launches++;
 #define DWF_AXPBY(PXV, PYV)                                                                        \
   if (px == PXV && py == PYV) {                                                                   \
     k_axpby<PXV, PYV><<<g, BT, 0, st>>>(a, (const typename Prec<PXV>::S*)x, b,                     \
@@ -217,6 +276,7 @@ int blas_copy(dwf_ctx* c, void* y, int py, const void* x, int px, int64_t n, cud
 int blas_cg_xr(dwf_ctx* c, void* x, void* r, const void* p, const void* Ap, int64_t n, int prec,
                int ialpha, cudaStream_t st, int* nparts) {
   const int g = grid_for(n);
+  c->launches++;
   DWF_PREC_SWITCH(prec, (k_cg_xr<P><<<g, BT, 0, st>>>(
                             (typename Prec<P>::S*)x, (typename Prec<P>::S*)r,
                             (const typename Prec<P>::S*)p, (const typename Prec<P>::S*)Ap, n,
@@ -227,13 +287,54 @@ int blas_cg_xr(dwf_ctx* c, void* x, void* r, const void* p, const void* Ap, int6
 
 int blas_cg_p(dwf_ctx* c, void* p, const void* r, int64_t n, int prec, int ibeta, cudaStream_t st) {
   const int g = grid_for(n);
+  c->launches++;
   DWF_PREC_SWITCH(prec, (k_cg_p<P><<<g, BT, 0, st>>>((typename Prec<P>::S*)p,
                                                        (const typename Prec<P>::S*)r, n, c->dscal,
                                                        ibeta)));
   return DWF_OK;
 }
 
+int blas_axpbypcz(dwf_ctx* c, double a, const void* x, double b, const void* y, double cz, void* z,
+                  int64_t n, int prec, cudaStream_t st) {
+  const int g = grid_for(n);
+  c->launches++;
+  DWF_PREC_SWITCH(prec, (k_axpbypcz<P><<<g, BT, 0, st>>>(a, (const typename Prec<P>::S*)x, b,
+                                                           (const typename Prec<P>::S*)y, cz,
+                                                           (typename Prec<P>::S*)z, n)));
+  return DWF_OK;
+}
+
+int blas_cheb_step(dwf_ctx* c, void* tp, const void* Ax, const void* x, double ta, double tb, void* acc,
+                   double cacc, int64_t n, int prec, cudaStream_t st) {
+  const int g = grid_for(n);
+  c->launches++;
+  DWF_PREC_SWITCH(prec, (k_cheb_step<P><<<g, BT, 0, st>>>((typename Prec<P>::S*)tp,
+                                                            (const typename Prec<P>::S*)Ax,
+                                                            (const typename Prec<P>::S*)x, ta, tb,
+                                                            (typename Prec<P>::S*)acc, cacc, n)));
+  return DWF_OK;
+}
+
+int blas_caxpy(dwf_ctx* c, double ar, double ai, const void* x, int px, void* y, int py, int64_t n,
+               cudaStream_t st) {
+  const int g = grid_for(n);
+  c->launches++;
+#define DWF_CAXPY(PXV, PYV)                                                                         \
+  if (px == PXV && py == PYV) {                                                                    \
+    k_caxpy<PXV, PYV><<<g, BT, 0, st>>>(ar, ai, (const typename Prec<PXV>::S*)x,                    \
+                                         (typename Prec<PYV>::S*)y, n);                             \
+    return DWF_OK;                                                                                 \
+  }
+  DWF_CAXPY(DWF_F64, DWF_F64)
+  DWF_CAXPY(DWF_F32, DWF_F64)
+  DWF_CAXPY(DWF_F32, DWF_F32)
+  DWF_CAXPY(DWF_F64, DWF_F32)
+#undef DWF_CAXPY
+  return dwf_fail(c, DWF_EINVAL, "bad precision pair");
+}
+
 int blas_scalar_div(dwf_ctx* c, int dst, int num, int den, cudaStream_t st) {
+  c->launches++;
   k_div<<<1, 1, 0, st>>>(c->dscal, dst, num, den);
   return DWF_OK;
 }

@@ -98,6 +98,8 @@ struct dwf_ctx {
   size_t partials_n;
   double* dscal;      // device scalars for solvers
   double* hscal;      // pinned host mirror
+  int64_t launches;   // kernel launches since the last counter reset
+  double hop_bytes;   // algorithmic bytes of hopping-term launches
   std::string err;
 };
 
@@ -148,7 +150,7 @@ int blas_cdot_partials(dwf_ctx* c, const void* a, const void* b, int64_t n, int 
 // Sum nparts partials (width 1 or 2 doubles) into dscal[dst..dst+width-1].
 int blas_finalize(dwf_ctx* c, int nparts, int width, int dst, cudaStream_t st);
 // As blas_finalize, then mode 1: alpha = rr/pAp; mode 2: beta = rrnew/rr, rr = rrnew.
-int blas_finalize_mode(dwf_ctx* c, int nparts, int width, int dst, int mode, cudaStream_t st);
+int blas_finalize_mode(dwf_ctx* c, int nparts, int width, int dst, int mode, cudaStream_t st, int base = 0);
 // Grow the reduction-partials buffer to at least n doubles.
 int dwf_reserve_partials(dwf_ctx* c, size_t n);
 // y = a*x + b*y with real host scalars, any precisions (x, y may differ).
@@ -162,6 +164,24 @@ int blas_cg_xr(dwf_ctx* c, void* x, void* r, const void* p, const void* Ap, int6
                int ialpha, cudaStream_t st, int* nparts);
 //   p = r + beta p
 int blas_cg_p(dwf_ctx* c, void* p, const void* r, int64_t n, int prec, int ibeta, cudaStream_t st);
+// z = a x + b y + c z (same precision)
+int blas_axpbypcz(dwf_ctx* c, double a, const void* x, double b, const void* y, double cz, void* z,
+                  int64_t n, int prec, cudaStream_t st);
+// Chebyshev recurrence step: tp = ta*Ax + tb*x - tp; acc += cacc*tp (acc may be NULL)
+int blas_cheb_step(dwf_ctx* c, void* tp, const void* Ax, const void* x, double ta, double tb, void* acc,
+                   double cacc, int64_t n, int prec, cudaStream_t st);
+// y += (ar + i ai) x, precisions (F64|F32) x (F64|F32)
+int blas_caxpy(dwf_ctx* c, double ar, double ai, const void* x, int px, void* y, int py, int64_t n,
+               cudaStream_t st);
+// Full-lattice D_DW / D_DW^dag / H_DW (g5 = 1) on nrhs full fields (api.cu).
+int ddw_apply(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int g5, int prec,
+              int nrhs, cudaStream_t st);
+int norm2_dev(dwf_ctx* c, const void* a, int64_t n, int prec, int dst, cudaStream_t st);
+// M_pc (dagger 0) or M_pc^dag (1) of nrhs even fields; tmp receives the odd
+// intermediate M_oo^-1 M_oe in (or its dagger form); reduce = |out|^2 partials.
+int mpc_apply(dwf_ctx* c, void* out, const void* in, void* tmp, const double* mf, int dagger, int prec,
+              int nrhs, int reduce, cudaStream_t st, int* nparts);
+int read_scalars(dwf_ctx* c, int first, int n, cudaStream_t st);
 // dscal[dst] = dscal[num] / dscal[den]
 int blas_scalar_div(dwf_ctx* c, int dst, int num, int den, cudaStream_t st);
 

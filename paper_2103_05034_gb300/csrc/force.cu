@@ -1,0 +1,210 @@
+// Pseudofermion force for HMC with the red-black operator of Sec. 5.1 of
+// arXiv:2103.05034 (the paper places its solvers inside HMC, Sec. 6; the force
+// is derived from first principles).  For S = phi^dag (M^dag M)^-1 phi,
+// M = M_pc, X = (M^dag M)^-1 phi (even), Y = M X, and the full fields
+// X' = X + M_oo^-1 M_oe X, Y' = Y + M_oo^-dag M_eo^dag Y:
+//   G_mu(x) = TA(U_mu(x) A_mu(x) - B_mu(x) U_mu(x)^dag),
+//   A_mu(x)_ab = sum_s Y'_s(x)^dag_b (1 - gamma_mu) X'_s(x+mu)_a,
+//   B_mu(x)_ab = sum_s Y'_s(x+mu)^dag_b (1 + gamma_mu) X'_s(x)_a,
+// so that dS/deps = sum Re tr(G^dag Q) for U -> exp(eps Q) U, Q in su(3).
+// Each spin trace is a two-spinor product: Y^dag (1 -+ gamma) X = h_Y^dag h_X
+// with both fields projected by the same (1 -+ gamma) half-spinor map.
+#include <string.h>
+
+#include <vector>
+
+#include "dhop_impl.cuh"
+#include "dwf_internal.cuh"
+
+namespace {
+
+template <class R, int MU>
+__device__ __forceinline__ void proj(cpx<R> (&h)[2][3], const cpx<R> (&ps)[12], R sg) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<R> p0 = ps[c], p1 = ps[3 + c], p2 = ps[6 + c], p3 = ps[9 + c];
+    if (MU == 0) {
+      h[0][c] = cmake<R>(p0.re - sg * p3.im, p0.im + sg * p3.re);
+      h[1][c] = cmake<R>(p1.re - sg * p2.im, p1.im + sg * p2.re);
+    } else if (MU == 1) {
+      h[0][c] = cmake<R>(p0.re + sg * p3.re, p0.im + sg * p3.im);
+      h[1][c] = cmake<R>(p1.re - sg * p2.re, p1.im - sg * p2.im);
+    } else if (MU == 2) {
+      h[0][c] = cmake<R>(p0.re - sg * p2.im, p0.im + sg * p2.re);
+      h[1][c] = cmake<R>(p1.re + sg * p3.im, p1.im - sg * p3.re);
+    } else {
+      h[0][c] = cmake<R>(p0.re - sg * p2.re, p0.im - sg * p2.im);
+      h[1][c] = cmake<R>(p1.re - sg * p3.re, p1.im - sg * p3.im);
+    }
+  }
+}
+
+// acc_ab += sum_k hx[k][a] conj(hy[k][b])
+template <class R>
+__device__ __forceinline__ void outer_acc(double2 (&acc)[9], const cpx<R> (&hx)[2][3], const cpx<R> (&hy)[2][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      R re = 0, im = 0;
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        re += hx[k][a].re * hy[k][b].re + hx[k][a].im * hy[k][b].im;
+        im += hx[k][a].im * hy[k][b].re - hx[k][a].re * hy[k][b].im;
+      }
+      acc[a * 3 + b].x += (double)re;
+      acc[a * 3 + b].y += (double)im;
+    }
+}
+
+template <int P, int MU, int LS>
+__device__ void link_force(double2 (&A)[9], double2 (&B)[9], const typename Prec<P>::S* Xx,
+                           const typename Prec<P>::S* Yx, const typename Prec<P>::S* Xy,
+                           const typename Prec<P>::S* Yy) {
+  typedef typename Prec<P>::R R;
+  for (int s = 0; s < LS; s++) {
+    cpx<R> xa[12], ya[12], xb[12], yb[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      xa[c] = ld_c(Xy + c * LS + s);  // X'(x+mu)
+      ya[c] = ld_c(Yx + c * LS + s);  // Y'(x)
+      xb[c] = ld_c(Xx + c * LS + s);  // X'(x)
+      yb[c] = ld_c(Yy + c * LS + s);  // Y'(x+mu)
+    }
+    cpx<R> hx[2][3], hy[2][3];
+    proj<R, MU>(hx, xa, R(1));
+    proj<R, MU>(hy, ya, R(1));
+    outer_acc<R>(A, hx, hy);
+    proj<R, MU>(hx, xb, R(-1));
+    proj<R, MU>(hy, yb, R(-1));
+    outer_acc<R>(B, hx, hy);
+  }
+}
+
+// One thread per link (parity, checkerboard site, mu); force[lex][mu] += G.
+template <int P, int LS>
+__global__ void __launch_bounds__(128) k_force(double2* force, const typename Prec<P>::S* Xf,
+                                               const typename Prec<P>::S* Yf, const double2* links_e,
+                                               const double2* links_o, int L0, int L1, int L2, int L3, int Vh) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= 2LL * Vh * 4) return;
+  const int mu = (int)(gid & 3);
+  const long long ps = gid >> 2;
+  const int p = (int)(ps / Vh);
+  const int h = (int)(ps - (long long)p * Vh);
+  const int Lxh = L0 / 2;
+  int rem = h / Lxh;
+  const int xh = h - rem * Lxh;
+  int x[4];
+  x[1] = rem % L1;
+  rem /= L1;
+  x[2] = rem % L2;
+  x[3] = rem / L2;
+  x[0] = 2 * xh + ((x[1] + x[2] + x[3] + p) & 1);
+  const int Ld[4] = {L0, L1, L2, L3};
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  y[mu] = (y[mu] + 1 == Ld[mu]) ? 0 : y[mu] + 1;
+  const long long ylex = y[0] + (long long)L0 * (y[1] + (long long)L1 * (y[2] + (long long)L2 * y[3]));
+  const long long xlex = x[0] + (long long)L0 * (x[1] + (long long)L1 * (x[2] + (long long)L2 * x[3]));
+  const long long row = 12LL * LS;
+  const typename Prec<P>::S* Xx = Xf + ((long long)p * Vh + h) * row;
+  const typename Prec<P>::S* Yx = Yf + ((long long)p * Vh + h) * row;
+  const typename Prec<P>::S* Xy = Xf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row;
+  const typename Prec<P>::S* Yy = Yf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row;
+  double2 A[9], B[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) A[i] = B[i] = make_double2(0, 0);
+  switch (mu) {
+    case 0: link_force<P, 0, LS>(A, B, Xx, Yx, Xy, Yy); break;
+    case 1: link_force<P, 1, LS>(A, B, Xx, Yx, Xy, Yy); break;
+    case 2: link_force<P, 2, LS>(A, B, Xx, Yx, Xy, Yy); break;
+    default: link_force<P, 3, LS>(A, B, Xx, Yx, Xy, Yy); break;
+  }
+  const double2* U = (p ? links_o : links_e) + ((long long)h * 8 + 2 * mu) * 9;
+  double2 Z[9];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      double re = 0, im = 0;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const double2 u = U[a * 3 + k], av = A[k * 3 + b];  // (U A)_ab
+        re += u.x * av.x - u.y * av.y;
+        im += u.x * av.y + u.y * av.x;
+        const double2 bv = B[a * 3 + k], ud = U[b * 3 + k];  // (B U^dag)_ab = B_ak conj(U_bk)
+        re -= bv.x * ud.x + bv.y * ud.y;
+        im -= bv.y * ud.x - bv.x * ud.y;
+      }
+      Z[a * 3 + b] = make_double2(re, im);
+    }
+  // TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6
+  const double trim = (Z[0].y + Z[4].y + Z[8].y) / 3.0;  // tr(Z - Z^dag)/6 = i Im tr Z / 3
+  double2* out = force + (xlex * 4 + mu) * 9;
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      double re = 0.5 * (Z[a * 3 + b].x - Z[b * 3 + a].x);
+      double im = 0.5 * (Z[a * 3 + b].y + Z[b * 3 + a].y);
+      if (a == b) im -= trim;
+      out[a * 3 + b].x += re;
+      out[a * 3 + b].y += im;
+    }
+}
+
+template <int P>
+int launch_force(dwf_ctx* c, double2* force, const void* Xf, const void* Yf, cudaStream_t st) {
+  const long long n = 2LL * c->g.Vh * 4;
+  const unsigned grid = (unsigned)((n + 127) / 128);
+  typedef typename Prec<P>::S S;
+  c->launches++;
+  switch (c->g.Ls) {
+    case 4: k_force<P, 4><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
+    case 8: k_force<P, 8><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
+    case 16: k_force<P, 16><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
+    default: k_force<P, 24><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
+  }
+  return DWF_OK;
+}
+
+}  // namespace
+
+extern "C" int dwf_force(dwf_ctx* c, void* force, const void* X, const double* mf, int npf, int prec,
+                         void* stream) {
+  if (!c || !force || !X || !mf || npf < 1) return DWF_EINVAL;
+  if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
+  if (!dwf_is_device_ptr(force) || !dwf_is_device_ptr(X)) return dwf_fail(c, DWF_EINVAL, "device buffers required");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t he = c->g.Vh * 12 * c->g.Ls;
+  const size_t cb = dwf_complex_bytes(prec);
+  char* Xf = (char*)dwf_workspace(c, 28, 2 * he * cb);
+  char* Yf = (char*)dwf_workspace(c, 29, 2 * he * cb);
+  if (!Xf || !Yf) return dwf_fail(c, DWF_ENOMEM, "force workspace");
+  for (int i = 0; i < npf; i++) {
+    const char* Xe = (const char*)X + (size_t)i * he * cb;
+    const double m1[1] = {mf[i]};
+    DWF_CUDA(c, cudaMemcpyAsync(Xf, Xe, he * cb, cudaMemcpyDeviceToDevice, st));
+    // X_o = M_oo^-1 (-1/2 D_oe X_e) and Y_e = M_ee X_e + 1/2 D_eo X_o  (= M_pc X_e)
+    int rc = mpc_apply(c, Yf, Xf, Xf + he * cb, m1, 0, prec, 1, 0, st, nullptr);
+    if (rc) return rc;
+    // Y_o = M_oo^-dag (-1/2 D^dag_oe Y_e)
+    HopLaunch h;
+    memset(&h, 0, sizeof(h));
+    h.out = Yf + he * cb;
+    h.in = Yf;
+    h.out_parity = 1;
+    h.dagger = 1;
+    h.nrhs = 1;
+    h.alpha = -0.5;
+    h.inv_mode = 2;
+    h.mf = m1;
+    rc = launch_hop(c, h, prec, st, nullptr);
+    if (rc) return rc;
+    rc = prec == DWF_F64 ? launch_force<DWF_F64>(c, (double2*)force, Xf, Yf, st)
+                         : launch_force<DWF_F32>(c, (double2*)force, Xf, Yf, st);
+    if (rc) return rc;
+  }
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}

@@ -1,0 +1,945 @@
+// HDCR multigrid (arXiv:2103.05034, Secs. 3.1-3.4, Table 1): Chebyshev
+// filters, chirality projection, block Cholesky-QR orthonormalisation, the
+// 9-point little Dirac operator of H_DW, coarse CG on A^2, the Chebyshev
+// smoother, the V(1,1) preconditioner and the flexible GCR outer solver.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "mg_kernels.cuh"
+
+using dwfmg::BlockGeom;
+
+struct dwf_coarse {
+  dwf_ctx* ctx;
+  BlockGeom g;
+  int nb, nplus;
+  double2* A64;  // [nc][9][nb][nb]
+  float2* A32;   // same layout, FP32
+  void* ws[6];
+  size_t ws_bytes[6];
+};
+
+struct dwf_mg {
+  dwf_ctx* ctx;
+  dwf_mg_params p;
+  BlockGeom g;
+  float2* basis;  // nb full FP32 fields
+  dwf_coarse* coarse;
+  double lambda_max_used;
+  double setup_seconds, coarse_op_seconds;
+};
+
+namespace {
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double sec() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+int64_t full_elems(const dwf_ctx* c) { return 2 * c->g.Vh * 12 * c->g.Ls; }
+
+int make_geom(dwf_ctx* c, const int block[4], BlockGeom* g) {
+  int b4 = 1, nc = 1;
+  for (int m = 0; m < 4; m++) {
+    if (block[m] < 1 || c->g.L[m] % block[m]) return dwf_fail(c, DWF_EINVAL, "block does not tile the lattice");
+    g->L[m] = c->g.L[m];
+    g->b[m] = block[m];
+    g->Lc[m] = c->g.L[m] / block[m];
+    b4 *= block[m];
+    nc *= g->Lc[m];
+  }
+  g->Lxh = c->g.Lxh;
+  g->Vh = (int)c->g.Vh;
+  g->Ls = c->g.Ls;
+  g->b4 = b4;
+  g->nc = nc;
+  return DWF_OK;
+}
+
+// Workspace slots used here (the solver slots of api.cu end at 15).
+enum { MW_T0 = 16, MW_T1, MW_T2, MW_T3, MW_T4, MW_T5, MW_T6, MW_T7, MW_T8, MW_T9, MW_T10, MW_T11 };
+
+void* ws(dwf_ctx* c, int slot, size_t bytes) { return dwf_workspace(c, slot, bytes); }
+
+// D^dag D on nrhs full fields via tmp.
+int mdagm(dwf_ctx* c, void* out, const void* in, void* tmp, double mf, int prec, int nrhs, cudaStream_t st) {
+  std::vector<double> m(nrhs, mf);
+  int rc = ddw_apply(c, tmp, in, m.data(), 0, 0, prec, nrhs, st);
+  if (rc) return rc;
+  return ddw_apply(c, out, tmp, m.data(), 1, 0, prec, nrhs, st);
+}
+
+// H_DW^2 on nrhs full fields via tmp.
+int hsq(dwf_ctx* c, void* out, const void* in, void* tmp, double mf, int prec, int nrhs, cudaStream_t st) {
+  std::vector<double> m(nrhs, mf);
+  int rc = ddw_apply(c, tmp, in, m.data(), 0, 1, prec, nrhs, st);
+  if (rc) return rc;
+  return ddw_apply(c, out, tmp, m.data(), 0, 1, prec, nrhs, st);
+}
+
+int check_finite(dwf_ctx* c, const void* v, int64_t n, int prec, cudaStream_t st, double* norm2) {
+  int rc = norm2_dev(c, v, n, prec, S_TMP3, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP3, 1, st);
+  if (rc) return rc;
+  if (norm2) *norm2 = c->hscal[S_TMP3];
+  if (!isfinite(c->hscal[S_TMP3])) return dwf_fail(c, DWF_ERANGE, "Chebyshev filter overflow: spectrum outside [lo, hi]");
+  return DWF_OK;
+}
+
+// T_order(x(A)) in -> out on nrhs full fields, x(A) = 2(A-lo)/(hi-lo) - 1, A = D^dag D.
+// With rescale, the pair (T_k, T_{k-1}) is divided by a common factor whenever
+// it grows past 1e15 (directions are kept, magnitudes are not).
+int filter_core(dwf_ctx* c, void* out, const void* in, int nrhs, double lo, double hi, int order, double mf,
+                int prec, bool rescale, cudaStream_t st, void** tprev_out = nullptr, void** tcur_out = nullptr) {
+  const int64_t n = full_elems(c) * nrhs;
+  const size_t bytes = n * dwf_complex_bytes(prec);
+  void* tp = ws(c, MW_T0, bytes);
+  void* tc = ws(c, MW_T1, bytes);
+  void* ax = ws(c, MW_T2, bytes);
+  void* tmp = ws(c, MW_T3, bytes);
+  if (!tp || !tc || !ax || !tmp) return dwf_fail(c, DWF_ENOMEM, "filter workspace");
+  const double a = 2.0 / (hi - lo), b = -(hi + lo) / (hi - lo);
+  int rc = blas_copy(c, tp, prec, in, prec, n, st);
+  if (rc) return rc;
+  if (order == 0) return blas_copy(c, out, prec, tp, prec, n, st);
+  rc = mdagm(c, ax, tp, tmp, mf, prec, nrhs, st);
+  if (rc) return rc;
+  rc = blas_axpbypcz(c, a, ax, b, tp, 0.0, tc, n, prec, st);  // T1 = x(A) T0
+  if (rc) return rc;
+  for (int k = 2; k <= order; k++) {
+    rc = mdagm(c, ax, tc, tmp, mf, prec, nrhs, st);
+    if (rc) return rc;
+    rc = blas_cheb_step(c, tp, ax, tc, 2 * a, 2 * b, nullptr, 0.0, n, prec, st);  // tp <- T_k
+    if (rc) return rc;
+    void* t = tp;
+    tp = tc;
+    tc = t;
+    if (rescale && k % 16 == 0) {
+      double nn = 0;
+      rc = check_finite(c, tc, n, prec, st, &nn);
+      if (rc) return rc;
+      if (nn > 1e30) {
+        const double f = 1.0 / sqrt(nn);
+        rc = blas_axpby(c, f, tc, prec, 0.0, tc, prec, n, st);
+        if (rc) return rc;
+        rc = blas_axpby(c, f, tp, prec, 0.0, tp, prec, n, st);
+        if (rc) return rc;
+      }
+    }
+  }
+  if (tprev_out) {
+    *tprev_out = tp;
+    *tcur_out = tc;
+  }
+  if (out) return blas_copy(c, out, prec, tc, prec, n, st);
+  return DWF_OK;
+}
+
+// Normalise each of nrhs fields of n complex numbers to unit norm (host loop).
+int normalise_fields(dwf_ctx* c, void* v, int nrhs, int64_t n, int prec, cudaStream_t st) {
+  const size_t cb = dwf_complex_bytes(prec);
+  for (int r = 0; r < nrhs; r++) {
+    char* p = (char*)v + r * n * cb;
+    double nn = 0;
+    int rc = check_finite(c, p, n, prec, st, &nn);
+    if (rc) return rc;
+    if (!(nn > 0)) return dwf_fail(c, DWF_ERANGE, "filtered vector vanished");
+    rc = blas_axpby(c, 1.0 / sqrt(nn), p, prec, 0.0, p, prec, n, st);
+    if (rc) return rc;
+  }
+  return DWF_OK;
+}
+
+template <int P>
+void launch_chiral(void* out, const void* in, long long n, int Ls, float sign, cudaStream_t st) {
+  dwfmg::k_chiral_project<P><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      (typename Prec<P>::S*)out, (const typename Prec<P>::S*)in, n, Ls, sign);
+}
+
+int chiral(dwf_ctx* c, void* out, const void* in, int sign, int prec, int nrhs, cudaStream_t st) {
+  const long long n = full_elems(c) * nrhs;
+  c->launches++;
+  switch (prec) {
+    case DWF_F64:
+      launch_chiral<DWF_F64>(out, in, n, c->g.Ls, (float)sign, st);
+      break;
+    case DWF_F32:
+      launch_chiral<DWF_F32>(out, in, n, c->g.Ls, (float)sign, st);
+      break;
+    default:
+      return dwf_fail(c, DWF_EINVAL, "bad precision");
+  }
+  return DWF_OK;
+}
+
+// out[xc][j][k] = <X_j, Y_k>_block (face-restricted for d > 0), FP64 results.
+int block_inner(dwf_ctx* c, const BlockGeom& g, const void* X, int nx, const void* Y, int ny, int prec,
+                double2* out, long long out_bstride, int out_ld, int d, int accumulate, cudaStream_t st) {
+  const long long fs = full_elems(c);
+  dim3 grid(g.nc, (nx + 31) / 32, (ny + 31) / 32);
+  c->launches++;
+  switch (prec) {
+    case DWF_F64:
+      dwfmg::k_block_inner<DWF_F64><<<grid, 256, 0, st>>>((const double2*)X, fs, nx, (const double2*)Y, fs, ny,
+                                                          out, out_bstride, out_ld, g, d, accumulate);
+      break;
+    case DWF_F32:
+      dwfmg::k_block_inner<DWF_F32><<<grid, 256, 0, st>>>((const float2*)X, fs, nx, (const float2*)Y, fs, ny,
+                                                          out, out_bstride, out_ld, g, d, accumulate);
+      break;
+    default:
+      return dwf_fail(c, DWF_EINVAL, "bad precision");
+  }
+  return DWF_OK;
+}
+
+// Y_k = sum_j X_j M[xc][j][k] per block (Y += when accumulate).
+int block_combine(dwf_ctx* c, const BlockGeom& g, void* Y, int ny, int py, const void* X, int nx, int px,
+                  const double2* M, long long m_bstride, int m_ld, int accumulate, cudaStream_t st) {
+  if (nx * ny > 1024) return dwf_fail(c, DWF_EINVAL, "block combine too wide");
+  const long long fs = full_elems(c);
+  c->launches++;
+  if (px == DWF_F64 && py == DWF_F64)
+    dwfmg::k_block_combine<DWF_F64, DWF_F64><<<g.nc, 256, 0, st>>>((double2*)Y, fs, ny, (const double2*)X, fs,
+                                                                   nx, M, m_bstride, m_ld, g, accumulate);
+  else if (px == DWF_F32 && py == DWF_F32)
+    dwfmg::k_block_combine<DWF_F32, DWF_F32><<<g.nc, 256, 0, st>>>((float2*)Y, fs, ny, (const float2*)X, fs,
+                                                                   nx, M, m_bstride, m_ld, g, accumulate);
+  else
+    return dwf_fail(c, DWF_EINVAL, "bad precision pair");
+  return DWF_OK;
+}
+
+int coarse_ws(dwf_coarse* C, int slot, size_t bytes, void** out) {
+  if (C->ws_bytes[slot] < bytes || !C->ws[slot]) {
+    if (C->ws[slot]) cudaFree(C->ws[slot]);
+    C->ws[slot] = nullptr;
+    C->ws_bytes[slot] = 0;
+    if (cudaMalloc(&C->ws[slot], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return dwf_fail(C->ctx, DWF_ENOMEM, "coarse workspace");
+    }
+    C->ws_bytes[slot] = bytes;
+  }
+  *out = C->ws[slot];
+  return DWF_OK;
+}
+
+int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cudaStream_t st) {
+  const long long n = (long long)C->g.nc * C->nb * nrhs;
+  C->ctx->launches++;
+  dwfmg::k_coarse_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1],
+                                                                     C->g.Lc[2], C->g.Lc[3], C->nb, nrhs);
+  return DWF_OK;
+}
+
+// CG on A^2 e = A r (one right-hand side, FP32 vectors), stopping when the
+// normal-equation residual falls below tol times its initial value.  The
+// scalars live in dscal slots base+S_*.
+int coarse_cg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxiter, int* iters, cudaStream_t st) {
+  dwf_ctx* c = C->ctx;
+  const int64_t n = (int64_t)C->g.nc * C->nb;
+  const size_t bytes = n * sizeof(float2);
+  void *b, *r, *p, *t, *Ap;
+  int rc2;
+  if ((rc2 = coarse_ws(C, 0, bytes, &b)) || (rc2 = coarse_ws(C, 1, bytes, &r)) || (rc2 = coarse_ws(C, 2, bytes, &p)) ||
+      (rc2 = coarse_ws(C, 3, bytes, &t)) || (rc2 = coarse_ws(C, 4, bytes, &Ap)))
+    return rc2;
+  const int base = 16;
+  int rcd = coarse_apply_dev(C, (float2*)b, rc, 1, st);
+  if (rcd) return rcd;
+  DWF_CUDA(c, cudaMemsetAsync(e, 0, bytes, st));
+  rcd = blas_copy(c, r, DWF_F32, b, DWF_F32, n, st);
+  if (rcd) return rcd;
+  rcd = blas_copy(c, p, DWF_F32, b, DWF_F32, n, st);
+  if (rcd) return rcd;
+  rcd = norm2_dev(c, b, n, DWF_F32, base + S_RR, st);
+  if (rcd) return rcd;
+  rcd = read_scalars(c, base + S_RR, 1, st);
+  if (rcd) return rcd;
+  const double bb = c->hscal[base + S_RR];
+  *iters = 0;
+  if (!(bb > 0)) return isfinite(bb) ? DWF_OK : dwf_fail(c, DWF_ENAN, "NaN in coarse solve");
+  const int check = 4;
+  for (int it = 1; it <= maxiter; it++) {
+    rcd = coarse_apply_dev(C, (float2*)t, (const float2*)p, 1, st);
+    if (rcd) return rcd;
+    int np = 0;
+    rcd = blas_norm2_partials(c, t, n, DWF_F32, st, &np);  // <p, A^2 p> = |A p|^2
+    if (rcd) return rcd;
+    rcd = blas_finalize_mode(c, np, 1, base + S_PAP, 1, st, base);
+    if (rcd) return rcd;
+    rcd = coarse_apply_dev(C, (float2*)Ap, (const float2*)t, 1, st);
+    if (rcd) return rcd;
+    rcd = blas_cg_xr(c, e, r, p, Ap, n, DWF_F32, base + S_ALPHA, st, &np);
+    if (rcd) return rcd;
+    rcd = blas_finalize_mode(c, np, 1, base + S_RRNEW, 2, st, base);
+    if (rcd) return rcd;
+    rcd = blas_cg_p(c, p, r, n, DWF_F32, base + S_BETA, st);
+    if (rcd) return rcd;
+    *iters = it;
+    if (it % check == 0 || it == maxiter) {
+      rcd = read_scalars(c, base + S_RR, 1, st);
+      if (rcd) return rcd;
+      const double rr = c->hscal[base + S_RR];
+      if (!isfinite(rr)) return dwf_fail(c, DWF_ENAN, "NaN in coarse solve");
+      if (rr <= tol * tol * bb) break;
+    }
+  }
+  return DWF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" int cheby_filter(dwf_ctx* c, void* out, const void* in, int nrhs, double lo, double hi, int order,
+                            double mf, int prec, void* stream) {
+  if (!c || !out || !in) return DWF_EINVAL;
+  if (nrhs < 1 || nrhs > DWF_MAX_RHS || order < 0 || !(hi > lo)) return dwf_fail(c, DWF_EINVAL, "bad filter arguments");
+  if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = filter_core(c, out, in, nrhs, lo, hi, order, mf, prec, false, st);
+  if (rc) return rc;
+  rc = check_finite(c, out, full_elems(c) * nrhs, prec, st, nullptr);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int cheby_recursive_basis(dwf_ctx* c, void* phi, const void* eta, double lam_lo, double lam_max, int m,
+                                     int delta, int nvec, double mf, int prec, void* stream) {
+  if (!c || !phi || !eta) return DWF_EINVAL;
+  if (nvec < 1 || m < 0 || delta < 1 || !(lam_max > lam_lo)) return dwf_fail(c, DWF_EINVAL, "bad filter arguments");
+  if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = full_elems(c);
+  const size_t cb = dwf_complex_bytes(prec);
+  // pre-filter (Eq. 34) into phi_0, normalised
+  int rc = filter_core(c, phi, eta, 1, lam_lo, lam_max, m, mf, prec, true, st);
+  if (rc) return rc;
+  rc = normalise_fields(c, phi, 1, n, prec, st);
+  if (rc) return rc;
+  // one recurrence of T_n(2A/lam_max - 1) phi_0 with snapshots at k*delta (Eqs. 35, 37)
+  const size_t bytes = n * cb;
+  void* tp = ws(c, MW_T4, bytes);
+  void* tc = ws(c, MW_T5, bytes);
+  void* ax = ws(c, MW_T6, bytes);
+  void* tmp = ws(c, MW_T7, bytes);
+  if (!tp || !tc || !ax || !tmp) return dwf_fail(c, DWF_ENOMEM, "filter workspace");
+  const double a = 2.0 / lam_max, b = -1.0;
+  rc = blas_copy(c, tp, prec, phi, prec, n, st);
+  if (rc) return rc;
+  int order = 0;
+  for (int k = 1; k < nvec; k++) {
+    while (order < k * delta) {
+      if (order == 0) {
+        rc = mdagm(c, ax, tp, tmp, mf, prec, 1, st);
+        if (rc) return rc;
+        rc = blas_axpbypcz(c, a, ax, b, tp, 0.0, tc, n, prec, st);
+      } else {
+        rc = mdagm(c, ax, tc, tmp, mf, prec, 1, st);
+        if (rc) return rc;
+        rc = blas_cheb_step(c, tp, ax, tc, 2 * a, 2 * b, nullptr, 0.0, n, prec, st);
+        void* t = tp;
+        tp = tc;
+        tc = t;
+      }
+      if (rc) return rc;
+      order++;
+    }
+    char* dst = (char*)phi + k * bytes;
+    rc = blas_copy(c, dst, prec, tc, prec, n, st);
+    if (rc) return rc;
+    rc = normalise_fields(c, dst, 1, n, prec, st);
+    if (rc) return rc;
+  }
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int dwf_chiral_project(dwf_ctx* c, void* out, const void* in, int sign, int prec, int nrhs,
+                                  void* stream) {
+  if (!c || !out || !in || (sign != 1 && sign != -1)) return DWF_EINVAL;
+  if (nrhs < 1) return dwf_fail(c, DWF_EINVAL, "nrhs");
+  int rc = chiral(c, out, in, sign, prec, nrhs, (cudaStream_t)stream);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int block_orthonormalise(dwf_ctx* c, void* basis, int nb, int nplus, const int block[4], void* stream) {
+  if (!c || !basis || !block) return DWF_EINVAL;
+  if (nb < 1 || nplus < 0 || nplus > nb || nplus > 32 || nb - nplus > 32)
+    return dwf_fail(c, DWF_EINVAL, "groups of at most 32 vectors");
+  BlockGeom g;
+  int rc = make_geom(c, block, &g);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = full_elems(c);
+  const size_t gbytes = (size_t)g.nc * nb * nb * sizeof(double2);
+  double2* G = (double2*)ws(c, MW_T8, gbytes);
+  double2* Ri = (double2*)ws(c, MW_T9, gbytes);
+  void* tmp = ws(c, MW_T10, (size_t)n * nb * 16);
+  int* fail = (int*)ws(c, MW_T11, sizeof(int) * 4);
+  if (!G || !Ri || !tmp || !fail) return dwf_fail(c, DWF_ENOMEM, "orthonormalisation workspace");
+  for (int pass = 0; pass < 2; pass++) {  // Cholesky-QR, twice
+    rc = block_inner(c, g, basis, nb, basis, nb, DWF_F64, G, (long long)nb * nb, nb, 0, 0, st);
+    if (rc) return rc;
+    DWF_CUDA(c, cudaMemsetAsync(Ri, 0, gbytes, st));
+    DWF_CUDA(c, cudaMemsetAsync(fail, 0, sizeof(int), st));
+    c->launches++;
+    dwfmg::k_block_cholinv<<<dim3(g.nc, 2), 32, 0, st>>>(G, Ri, nb, nplus, fail);
+    rc = block_combine(c, g, tmp, nb, DWF_F64, basis, nb, DWF_F64, Ri, (long long)nb * nb, nb, 0, st);
+    if (rc) return rc;
+    DWF_CUDA(c, cudaMemcpyAsync(basis, tmp, (size_t)n * nb * 16, cudaMemcpyDeviceToDevice, st));
+    int hfail = 0;
+    DWF_CUDA(c, cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DWF_CUDA(c, cudaStreamSynchronize(st));
+    if (hfail) return dwf_fail(c, DWF_ERANGE, "basis vectors linearly dependent on a block");
+  }
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+// ---------------------------------------------------------------------- coarse operator
+extern "C" int coarse_build(dwf_ctx* c, const void* basis, int nb, int nplus, const int block[4], double mf,
+                            int prec, dwf_coarse** out, void* stream) {
+  if (!c || !basis || !block || !out) return DWF_EINVAL;
+  *out = nullptr;
+  if (nb < 1 || nb > DWF_MAX_RHS || nplus < 0 || nplus > nb) return dwf_fail(c, DWF_EINVAL, "bad nbasis");
+  if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
+  BlockGeom g;
+  int rc = make_geom(c, block, &g);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  dwf_coarse* C = new (std::nothrow) dwf_coarse();
+  if (!C) return DWF_ENOMEM;
+  C->ctx = c;
+  C->g = g;
+  C->nb = nb;
+  C->nplus = nplus;
+  const size_t na = (size_t)g.nc * 9 * nb * nb;
+  if (cudaMalloc(&C->A64, na * sizeof(double2)) != cudaSuccess || cudaMalloc(&C->A32, na * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    coarse_destroy(C);
+    return dwf_fail(c, DWF_ENOMEM, "coarse operator");
+  }
+  const int64_t n = full_elems(c);
+  const size_t fb = (size_t)n * nb * dwf_complex_bytes(prec);
+  void* H = ws(c, MW_T8, fb);
+  void* W = ws(c, MW_T9, fb);
+  if (!H || !W) {
+    coarse_destroy(C);
+    return dwf_fail(c, DWF_ENOMEM, "coarse build workspace");
+  }
+  std::vector<double> m(nb, mf);
+  // H_DW phi_k for all k; the eight face terms are split off one direction at a time
+  rc = ddw_apply(c, H, basis, m.data(), 0, 1, prec, nb, st);
+  const long long bstride = 9LL * nb * nb;
+  for (int d = 1; d <= 8 && rc == DWF_OK; d++) {
+    const unsigned nblk = (unsigned)((2LL * g.Vh * g.Ls + 127) / 128);
+    dim3 grid(nblk, nb);
+    c->launches++;
+#define DWF_FACE(PV, LSV)                                                                                  \
+  dwfmg::k_face_hop<PV, LSV><<<grid, 128, 0, st>>>((typename Prec<PV>::S*)W,                                \
+                                                    (const typename Prec<PV>::S*)basis, n,                 \
+                                                    (const typename Prec<PV>::LS*)(PV == DWF_F64 ? (void*)c->links64[0] : (void*)c->links32[0]), \
+                                                    (const typename Prec<PV>::LS*)(PV == DWF_F64 ? (void*)c->links64[1] : (void*)c->links32[1]), g, d)
+    if (prec == DWF_F64) {
+      switch (g.Ls) {
+        case 4: DWF_FACE(DWF_F64, 4); break;
+        case 8: DWF_FACE(DWF_F64, 8); break;
+        case 16: DWF_FACE(DWF_F64, 16); break;
+        default: DWF_FACE(DWF_F64, 24); break;
+      }
+    } else {
+      switch (g.Ls) {
+        case 4: DWF_FACE(DWF_F32, 4); break;
+        case 8: DWF_FACE(DWF_F32, 8); break;
+        case 16: DWF_FACE(DWF_F32, 16); break;
+        default: DWF_FACE(DWF_F32, 24); break;
+      }
+    }
+#undef DWF_FACE
+    rc = block_inner(c, g, basis, nb, W, nb, prec, C->A64 + (size_t)d * nb * nb, bstride, nb, d, 0, st);
+    if (rc) break;
+    rc = blas_axpby(c, -1.0, W, prec, 1.0, H, prec, n * nb, st);
+  }
+  if (rc == DWF_OK) rc = block_inner(c, g, basis, nb, H, nb, prec, C->A64, bstride, nb, 0, 0, st);
+  if (rc == DWF_OK) rc = blas_copy(c, C->A32, DWF_F32, C->A64, DWF_F64, (int64_t)na, st);
+  if (rc == DWF_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = dwf_cuda_check(c, e, "coarse_build");
+  }
+  if (rc) {
+    coarse_destroy(C);
+    return rc;
+  }
+  *out = C;
+  return DWF_OK;
+}
+
+extern "C" int coarse_destroy(dwf_coarse* C) {
+  if (!C) return DWF_OK;
+  if (C->A64) cudaFree(C->A64);
+  if (C->A32) cudaFree(C->A32);
+  for (int i = 0; i < 6; i++)
+    if (C->ws[i]) cudaFree(C->ws[i]);
+  delete C;
+  return DWF_OK;
+}
+
+extern "C" int coarse_export(const dwf_coarse* C, void* A, int* dims) {
+  if (!C) return DWF_EINVAL;
+  if (dims) {
+    for (int m = 0; m < 4; m++) dims[m] = C->g.Lc[m];
+    dims[4] = C->nb;
+  }
+  if (A) {
+    const size_t na = (size_t)C->g.nc * 9 * C->nb * C->nb;
+    if (cudaMemcpy(A, C->A64, na * sizeof(double2), cudaMemcpyDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return DWF_ECUDA;
+    }
+  }
+  return DWF_OK;
+}
+
+extern "C" int coarse_apply(dwf_coarse* C, void* out, const void* in, int nrhs, void* stream) {
+  if (!C || !out || !in || nrhs < 1) return DWF_EINVAL;
+  int rc = coarse_apply_dev(C, (float2*)out, (const float2*)in, nrhs, (cudaStream_t)stream);
+  if (rc) return rc;
+  DWF_CUDA(C->ctx, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int coarse_solve(dwf_coarse* C, void* e, const void* r, double tol, int maxiter, int* iters,
+                            void* stream) {
+  if (!C || !e || !r || !(tol > 0) || maxiter < 1) return DWF_EINVAL;
+  int it = 0;
+  int rc = coarse_cg(C, (float2*)e, (const float2*)r, tol, maxiter, &it, (cudaStream_t)stream);
+  if (iters) *iters = it;
+  if (rc) return rc;
+  DWF_CUDA(C->ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  return DWF_OK;
+}
+
+extern "C" int dwf_restrict(dwf_ctx* c, void* out, const void* in, const void* basis, int nb, const int block[4],
+                            int nrhs, int prec, void* stream) {
+  if (!c || !out || !in || !basis || !block) return DWF_EINVAL;
+  BlockGeom g;
+  int rc = make_geom(c, block, &g);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double2* tmp = (double2*)ws(c, MW_T11 + 0, (size_t)g.nc * nb * nrhs * sizeof(double2));
+  if (!tmp) return dwf_fail(c, DWF_ENOMEM, "workspace");
+  rc = block_inner(c, g, basis, nb, in, nrhs, prec, tmp, (long long)nb * nrhs, nrhs, 0, 0, st);
+  if (rc) return rc;
+  rc = blas_copy(c, out, DWF_F32, tmp, DWF_F64, (int64_t)g.nc * nb * nrhs, st);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+extern "C" int dwf_prolong(dwf_ctx* c, void* out, const void* in, const void* basis, int nb, const int block[4],
+                           int nrhs, int prec, int accumulate, void* stream) {
+  if (!c || !out || !in || !basis || !block) return DWF_EINVAL;
+  BlockGeom g;
+  int rc = make_geom(c, block, &g);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double2* tmp = (double2*)ws(c, MW_T11 + 0, (size_t)g.nc * nb * nrhs * sizeof(double2));
+  if (!tmp) return dwf_fail(c, DWF_ENOMEM, "workspace");
+  rc = blas_copy(c, tmp, DWF_F64, in, DWF_F32, (int64_t)g.nc * nb * nrhs, st);
+  if (rc) return rc;
+  rc = block_combine(c, g, out, nrhs, prec, basis, nb, prec, tmp, (long long)nb * nrhs, nrhs, accumulate, st);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+// ---------------------------------------------------------------------- MG setup / solve
+namespace {
+
+// Chebyshev smoother S_cheb([a,b],N) of Eq. (24) with M = M^dag = H_DW:
+// z = [c0/2 + sum_{j=1}^{N-1} c_j T_j(y(H^2))] H r.  FP32 full fields.
+int smoother(dwf_mg* G, void* z, const void* r, cudaStream_t st, double* nH) {
+  dwf_ctx* c = G->ctx;
+  const int64_t n = full_elems(c);
+  const size_t bytes = n * sizeof(float2);
+  void* v = ws(c, MW_T0, bytes);
+  void* tp = ws(c, MW_T1, bytes);
+  void* tc = ws(c, MW_T2, bytes);
+  void* ax = ws(c, MW_T3, bytes);
+  void* tmp = ws(c, MW_T4, bytes);
+  if (!v || !tp || !tc || !ax || !tmp) return dwf_fail(c, DWF_ENOMEM, "smoother workspace");
+  const double a = G->p.smooth_lo, b = G->p.smooth_hi;
+  const int N = G->p.smooth_order;
+  std::vector<double> cf(N + 1);
+  for (int j = 0; j <= N; j++) {
+    double s = 0;
+    for (int k = 0; k < N; k++) {
+      const double th = M_PI * (k + 0.5) / N;
+      const double y = a + (b - a) * (cos(th) + 1) / 2;
+      s += cos(j * th) / y;
+    }
+    cf[j] = 2.0 * s / N;
+  }
+  const double mf[1] = {G->p.mf};
+  int rc = ddw_apply(c, v, r, mf, 0, 1, DWF_F32, 1, st);  // v = H r
+  if (rc) return rc;
+  *nH += 1;
+  rc = blas_axpby(c, 0.5 * cf[0], v, DWF_F32, 0.0, z, DWF_F32, n, st);
+  if (rc) return rc;
+  if (N < 2) return DWF_OK;
+  const double xa = 2.0 / (b - a), xb = -(b + a) / (b - a);
+  rc = blas_copy(c, tp, DWF_F32, v, DWF_F32, n, st);
+  if (rc) return rc;
+  rc = hsq(c, ax, tp, tmp, G->p.mf, DWF_F32, 1, st);
+  if (rc) return rc;
+  *nH += 2;
+  rc = blas_axpbypcz(c, xa, ax, xb, tp, 0.0, tc, n, DWF_F32, st);  // T1
+  if (rc) return rc;
+  rc = blas_axpby(c, cf[1], tc, DWF_F32, 1.0, z, DWF_F32, n, st);
+  if (rc) return rc;
+  for (int j = 2; j < N; j++) {
+    rc = hsq(c, ax, tc, tmp, G->p.mf, DWF_F32, 1, st);
+    if (rc) return rc;
+    *nH += 2;
+    rc = blas_cheb_step(c, tp, ax, tc, 2 * xa, 2 * xb, z, cf[j], n, DWF_F32, st);
+    if (rc) return rc;
+    void* t = tp;
+    tp = tc;
+    tc = t;
+  }
+  return DWF_OK;
+}
+
+// V(1,1) of Eqs. (26)-(28) on residual r0 with x0 = 0: x1 = S r0, r1 = r0 - H x1,
+// x2 = x1 + P A^-1 P^dag r1, r2 = r0 - H x2, x3 = x2 + S r2.  FP32.
+int vcycle(dwf_mg* G, void* x, const void* r0, cudaStream_t st, double* nH, int* ncoarse) {
+  dwf_ctx* c = G->ctx;
+  dwf_coarse* C = G->coarse;
+  const int64_t n = full_elems(c);
+  const size_t bytes = n * sizeof(float2);
+  void* rr = ws(c, MW_T5, bytes);
+  void* s2 = ws(c, MW_T6, bytes);
+  if (!rr || !s2) return dwf_fail(c, DWF_ENOMEM, "vcycle workspace");
+  const double mf[1] = {G->p.mf};
+  int rc = smoother(G, x, r0, st, nH);
+  if (rc) return rc;
+  rc = ddw_apply(c, rr, x, mf, 0, 1, DWF_F32, 1, st);
+  if (rc) return rc;
+  *nH += 1;
+  rc = blas_axpby(c, 1.0, r0, DWF_F32, -1.0, rr, DWF_F32, n, st);  // r1
+  if (rc) return rc;
+  const int64_t ncv = (int64_t)C->g.nc * C->nb;
+  double2* t64 = (double2*)ws(c, MW_T7, ncv * sizeof(double2));
+  void *rc32, *ec32;
+  if (!t64 || (rc = coarse_ws(C, 5, 2 * ncv * sizeof(float2), &rc32))) return rc ? rc : dwf_fail(c, DWF_ENOMEM, "ws");
+  ec32 = (float2*)rc32 + ncv;
+  rc = block_inner(c, C->g, G->basis, C->nb, rr, 1, DWF_F32, t64, C->nb, 1, 0, 0, st);  // P^dag r1
+  if (rc) return rc;
+  rc = blas_copy(c, rc32, DWF_F32, t64, DWF_F64, ncv, st);
+  if (rc) return rc;
+  int it = 0;
+  rc = coarse_cg(C, (float2*)ec32, (const float2*)rc32, G->p.coarse_tol, G->p.coarse_maxiter, &it, st);
+  if (rc) return rc;
+  *ncoarse += it;
+  rc = blas_copy(c, t64, DWF_F64, ec32, DWF_F32, ncv, st);
+  if (rc) return rc;
+  rc = block_combine(c, C->g, x, 1, DWF_F32, G->basis, C->nb, DWF_F32, t64, C->nb, 1, 1, st);  // x2 = x1 + P e
+  if (rc) return rc;
+  rc = ddw_apply(c, rr, x, mf, 0, 1, DWF_F32, 1, st);
+  if (rc) return rc;
+  *nH += 1;
+  rc = blas_axpby(c, 1.0, r0, DWF_F32, -1.0, rr, DWF_F32, n, st);  // r2
+  if (rc) return rc;
+  rc = smoother(G, s2, rr, st, nH);
+  if (rc) return rc;
+  return blas_axpby(c, 1.0, s2, DWF_F32, 1.0, x, DWF_F32, n, st);  // x3
+}
+
+}  // namespace
+
+extern "C" int mg_setup(dwf_ctx* c, const dwf_mg_params* p, const void* eta, dwf_mg** out, void* stream) {
+  Timer timer;
+  if (!c || !p || !eta || !out) return DWF_EINVAL;
+  *out = nullptr;
+  const int nb = p->nbasis;
+  if (nb < 2 || (nb & 1) || nb > 64 || nb / 2 > 32) return dwf_fail(c, DWF_EINVAL, "nbasis must be even, <= 64");
+  if (p->subspace_mode != DWF_SUBSPACE_BATCH && p->subspace_mode != DWF_SUBSPACE_RECURSIVE)
+    return dwf_fail(c, DWF_EINVAL, "bad subspace mode");
+  dwf_mg* G = new (std::nothrow) dwf_mg();
+  if (!G) return DWF_ENOMEM;
+  G->ctx = c;
+  G->p = *p;
+  int rc = make_geom(c, p->block, &G->g);
+  if (rc) {
+    delete G;
+    return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = full_elems(c);
+  const int nplus = nb / 2;
+  void* f32 = nullptr;
+  double2* b64 = nullptr;
+  if (cudaMalloc(&G->basis, (size_t)n * nb * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&f32, (size_t)n * nplus * 2 * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&b64, (size_t)n * nb * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    if (f32) cudaFree(f32);
+    if (b64) cudaFree(b64);
+    mg_destroy(G);
+    return dwf_fail(c, DWF_ENOMEM, "mg basis");
+  }
+  auto cleanup = [&]() {
+    cudaFree(f32);
+    cudaFree(b64);
+  };
+  // 1. filtered vectors (FP32): batch mode filters nb Gaussians; recursive mode
+  //    builds nb/2 vectors from one Gaussian.
+  double lmax = p->lambda_max;
+  if (p->subspace_mode == DWF_SUBSPACE_BATCH) {
+    void* e32 = ws(c, MW_T10, (size_t)n * nb * sizeof(float2));
+    if (!e32) {
+      cleanup();
+      mg_destroy(G);
+      return dwf_fail(c, DWF_ENOMEM, "ws");
+    }
+    rc = blas_copy(c, e32, DWF_F32, eta, DWF_F64, n * nb, st);
+    for (int r0 = 0; r0 < nb && rc == DWF_OK; r0 += DWF_MAX_RHS) {
+      const int nr = nb - r0 < DWF_MAX_RHS ? nb - r0 : DWF_MAX_RHS;
+      rc = filter_core(c, (float2*)f32 + (size_t)r0 * n, (float2*)e32 + (size_t)r0 * n, nr, p->lambda_lo, lmax,
+                       p->filter_order, p->mf, DWF_F32, true, st);
+    }
+    if (rc == DWF_OK) rc = normalise_fields(c, f32, nb, n, DWF_F32, st);
+  } else {
+    void* e32 = ws(c, MW_T10, (size_t)n * sizeof(float2));
+    rc = e32 ? blas_copy(c, e32, DWF_F32, eta, DWF_F64, n, st) : DWF_ENOMEM;
+    if (rc == DWF_OK)
+      rc = cheby_recursive_basis(c, f32, e32, p->lambda_lo, lmax, p->filter_order, p->delta, nplus, p->mf, DWF_F32,
+                                 stream);
+  }
+  // 2. chirality projection into FP64: first nb/2 basis vectors take +, the rest -
+  if (rc == DWF_OK) rc = blas_copy(c, b64, DWF_F64, f32, DWF_F32, n * (p->subspace_mode == DWF_SUBSPACE_BATCH ? nb : nplus), st);
+  if (rc == DWF_OK) {
+    if (p->subspace_mode == DWF_SUBSPACE_BATCH) {
+      rc = chiral(c, b64, b64, +1, DWF_F64, nplus, st);
+      if (rc == DWF_OK) rc = chiral(c, b64 + (size_t)nplus * n, b64 + (size_t)nplus * n, -1, DWF_F64, nplus, st);
+    } else {
+      rc = chiral(c, b64 + (size_t)nplus * n, b64, -1, DWF_F64, nplus, st);
+      if (rc == DWF_OK) rc = chiral(c, b64, b64, +1, DWF_F64, nplus, st);
+    }
+  }
+  // 3. FP64 block orthonormalisation (Cholesky-QR twice per block and chirality)
+  if (rc == DWF_OK) rc = block_orthonormalise(c, b64, nb, nplus, p->block, stream);
+  if (rc == DWF_OK) rc = blas_copy(c, G->basis, DWF_F32, b64, DWF_F64, n * nb, st);
+  if (rc == DWF_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = dwf_cuda_check(c, e, "mg_setup");
+  }
+  G->setup_seconds = timer.sec();
+  // 4. little Dirac operator of H_DW from the FP32 basis
+  Timer t2;
+  if (rc == DWF_OK) rc = coarse_build(c, G->basis, nb, nplus, p->block, p->mf, DWF_F32, &G->coarse, stream);
+  G->coarse_op_seconds = t2.sec();
+  G->lambda_max_used = lmax;
+  cleanup();
+  if (rc) {
+    mg_destroy(G);
+    return rc;
+  }
+  *out = G;
+  return DWF_OK;
+}
+
+extern "C" int mg_destroy(dwf_mg* G) {
+  if (!G) return DWF_OK;
+  if (G->basis) cudaFree(G->basis);
+  if (G->coarse) coarse_destroy(G->coarse);
+  delete G;
+  return DWF_OK;
+}
+
+extern "C" int mg_export_basis(const dwf_mg* G, void* out) {
+  if (!G || !out) return DWF_EINVAL;
+  const size_t bytes = (size_t)full_elems(G->ctx) * G->p.nbasis * sizeof(float2);
+  if (cudaMemcpy(out, G->basis, bytes, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return DWF_ECUDA;
+  }
+  return DWF_OK;
+}
+
+extern "C" dwf_coarse* mg_coarse(dwf_mg* G) { return G ? G->coarse : nullptr; }
+
+extern "C" int mg_precondition(dwf_mg* G, void* out, const void* in, void* stream) {
+  if (!G || !out || !in) return DWF_EINVAL;
+  double nH = 0;
+  int nc = 0;
+  int rc = vcycle(G, out, in, (cudaStream_t)stream, &nH, &nc);
+  if (rc) return rc;
+  DWF_CUDA(G->ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  return DWF_OK;
+}
+
+extern "C" int mg_smooth(dwf_mg* G, void* out, const void* in, void* stream) {
+  if (!G || !out || !in) return DWF_EINVAL;
+  double nH = 0;
+  int rc = smoother(G, out, in, (cudaStream_t)stream, &nH);
+  if (rc) return rc;
+  DWF_CUDA(G->ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  return DWF_OK;
+}
+
+// Flexible GCR(nkrylov) on H_DW x = Gamma_5 b with the V(1,1) preconditioner;
+// x and the true residual in FP64, directions in FP32.
+extern "C" int mg_solve(dwf_mg* G, void* x, const void* b, double tol, dwf_solve_stats* stats, void* stream) {
+  Timer timer;
+  if (!G || !x || !b || !(tol > 0)) return DWF_EINVAL;
+  dwf_ctx* c = G->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = full_elems(c);
+  const int nk = G->p.nkrylov > 0 ? G->p.nkrylov : 8;
+  dwf_solve_stats S;
+  memset(&S, 0, sizeof(S));
+  const bool host_b = !dwf_is_device_ptr(b), host_x = !dwf_is_device_ptr(x);
+  void* db = (void*)b;
+  void* dx = x;
+  if (host_b) {
+    db = ws(c, 2, n * 16);  // solver slot WS_B
+    if (!db) return dwf_fail(c, DWF_ENOMEM, "ws");
+    DWF_CUDA(c, cudaMemcpyAsync(db, b, n * 16, cudaMemcpyHostToDevice, st));
+  }
+  if (host_x) {
+    dx = ws(c, 3, n * 16);  // WS_X
+    if (!dx) return dwf_fail(c, DWF_ENOMEM, "ws");
+  }
+  void* rhs = ws(c, 15, n * 16);                     // Gamma_5 b (FP64)
+  void* r64 = ws(c, 4, n * 16);                      // FP64 residual
+  void* t64 = ws(c, 5, n * 16);                      // FP64 temporary
+  void* r32 = ws(c, 9, n * 8);                       // FP32 residual
+  void* zs = ws(c, 10, (size_t)n * 8 * nk);          // directions
+  void* wsv = ws(c, 11, (size_t)n * 8 * nk);         // H directions
+  if (!rhs || !r64 || !t64 || !r32 || !zs || !wsv) return dwf_fail(c, DWF_ENOMEM, "mg_solve workspace");
+  const double mf[1] = {G->p.mf};
+  int rc = chiral(c, rhs, db, 1, DWF_F64, 1, st);  // placeholder overwritten below
+  if (rc) return rc;
+  // rhs = Gamma_5 b = (P_+ - P_-) b: 2 * (1+G5)/2 b - b
+  rc = blas_axpby(c, 2.0, rhs, DWF_F64, 0.0, rhs, DWF_F64, n, st);
+  if (rc) return rc;
+  rc = blas_axpby(c, -1.0, db, DWF_F64, 1.0, rhs, DWF_F64, n, st);
+  if (rc) return rc;
+  rc = norm2_dev(c, rhs, n, DWF_F64, S_TMP0, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP0, 1, st);
+  if (rc) return rc;
+  const double bnorm = sqrt(c->hscal[S_TMP0]);
+  DWF_CUDA(c, cudaMemsetAsync(dx, 0, n * 16, st));
+  double nH = 0;
+  int ncoarse = 0;
+  if (!(bnorm > 0)) {
+    if (host_x) DWF_CUDA(c, cudaMemcpyAsync(x, dx, n * 16, cudaMemcpyDeviceToHost, st));
+    DWF_CUDA(c, cudaStreamSynchronize(st));
+    if (stats) *stats = S;
+    return bnorm == 0 ? DWF_OK : dwf_fail(c, DWF_ENAN, "source is not finite");
+  }
+  rc = blas_copy(c, r64, DWF_F64, rhs, DWF_F64, n, st);
+  if (rc) return rc;
+  double res = 1.0;
+  int it = 0;
+  const int maxit = G->p.maxiter > 0 ? G->p.maxiter : 1000;
+  bool done = false;
+  std::vector<double> wnorm(nk);
+  while (!done && it < maxit) {
+    rc = blas_copy(c, r32, DWF_F32, r64, DWF_F64, n, st);
+    if (rc) return rc;
+    int k = 0;
+    for (; k < nk && it < maxit; k++) {
+      float2* z = (float2*)zs + (size_t)k * n;
+      float2* w = (float2*)wsv + (size_t)k * n;
+      rc = vcycle(G, z, r32, st, &nH, &ncoarse);
+      if (rc) return rc;
+      rc = ddw_apply(c, w, z, mf, 0, 1, DWF_F32, 1, st);
+      if (rc) return rc;
+      nH += 1;
+      for (int j = 0; j < k; j++) {  // orthogonalise against earlier H-directions
+        const float2* wj = (const float2*)wsv + (size_t)j * n;
+        const float2* zj = (const float2*)zs + (size_t)j * n;
+        int np = 0;
+        rc = blas_cdot_partials(c, wj, w, n, DWF_F32, st, &np);
+        if (rc) return rc;
+        rc = blas_finalize(c, np, 2, S_TMP0, st);
+        if (rc) return rc;
+        rc = read_scalars(c, S_TMP0, 2, st);
+        if (rc) return rc;
+        const double br = c->hscal[S_TMP0] / wnorm[j], bi = c->hscal[S_TMP0 + 1] / wnorm[j];
+        rc = blas_caxpy(c, -br, -bi, wj, DWF_F32, w, DWF_F32, n, st);
+        if (rc) return rc;
+        rc = blas_caxpy(c, -br, -bi, zj, DWF_F32, z, DWF_F32, n, st);
+        if (rc) return rc;
+      }
+      int np = 0;
+      rc = blas_cdot_partials(c, w, r32, n, DWF_F32, st, &np);
+      if (rc) return rc;
+      rc = blas_finalize(c, np, 2, S_TMP0, st);
+      if (rc) return rc;
+      rc = norm2_dev(c, w, n, DWF_F32, S_TMP2, st);
+      if (rc) return rc;
+      rc = read_scalars(c, S_TMP0, 3, st);
+      if (rc) return rc;
+      const double ww = c->hscal[S_TMP2];
+      if (!(ww > 0) || !isfinite(ww)) return dwf_fail(c, DWF_ENAN, "GCR breakdown");
+      wnorm[k] = ww;
+      const double ar = c->hscal[S_TMP0] / ww, ai = c->hscal[S_TMP0 + 1] / ww;
+      rc = blas_caxpy(c, ar, ai, z, DWF_F32, dx, DWF_F64, n, st);
+      if (rc) return rc;
+      rc = blas_caxpy(c, -ar, -ai, w, DWF_F32, r32, DWF_F32, n, st);
+      if (rc) return rc;
+      rc = norm2_dev(c, r32, n, DWF_F32, S_TMP2, st);
+      if (rc) return rc;
+      rc = read_scalars(c, S_TMP2, 1, st);
+      if (rc) return rc;
+      it++;
+      if (sqrt(c->hscal[S_TMP2]) / bnorm <= tol) {
+        k++;
+        break;
+      }
+    }
+    // restart: true residual in FP64
+    rc = ddw_apply(c, t64, dx, mf, 0, 1, DWF_F64, 1, st);
+    if (rc) return rc;
+    nH += 1;
+    rc = blas_copy(c, r64, DWF_F64, rhs, DWF_F64, n, st);
+    if (rc) return rc;
+    rc = blas_axpby(c, -1.0, t64, DWF_F64, 1.0, r64, DWF_F64, n, st);
+    if (rc) return rc;
+    rc = norm2_dev(c, r64, n, DWF_F64, S_TMP2, st);
+    if (rc) return rc;
+    rc = read_scalars(c, S_TMP2, 1, st);
+    if (rc) return rc;
+    res = sqrt(c->hscal[S_TMP2]) / bnorm;
+    if (!isfinite(res)) return dwf_fail(c, DWF_ENAN, "NaN in MG solve");
+    done = res <= tol;
+  }
+  if (host_x) DWF_CUDA(c, cudaMemcpyAsync(x, dx, n * 16, cudaMemcpyDeviceToHost, st));
+  DWF_CUDA(c, cudaStreamSynchronize(st));
+  S.iterations = it;
+  S.coarse_iterations = ncoarse;
+  S.fine_matmuls = nH;
+  S.true_residual = res;
+  S.seconds = timer.sec();
+  S.setup_seconds = G->setup_seconds;
+  S.coarse_op_seconds = G->coarse_op_seconds;
+  S.status = done ? DWF_OK : DWF_ENOCONV;
+  if (stats) *stats = S;
+  if (!done) return dwf_fail(c, DWF_ENOCONV, "mg_solve: maxiter reached before tol");
+  return DWF_OK;
+}

@@ -80,6 +80,18 @@ class Context:
         return torch.zeros(2 * nrhs * self.half_numel(), dtype=_DTYPE[prec], device=device)
 
 
+def dwf_counters(ctx):
+    """(kernel launches, algorithmic hopping-term bytes) since the last reset."""
+    n = C.c_int64()
+    b = C.c_double()
+    check(lib().dwf_counters(ctx.h, C.byref(n), C.byref(b)))
+    return n.value, b.value
+
+
+def dwf_reset_counters(ctx):
+    check(lib().dwf_reset_counters(ctx.h))
+
+
 def dwf_dhop(ctx, out, inp, out_parity, dagger=0, nrhs=1):
     check(lib().dwf_dhop(ctx.h, _ptr(out), _ptr(inp), out_parity, dagger, _prec_of(inp), nrhs,
                          _stream()), ctx.h)
@@ -147,3 +159,166 @@ def dwf_power_max(ctx, v0, mf, iters):
     r = C.c_double()
     check(lib().dwf_power_max(ctx.h, C.byref(r), _ptr(v0), mf, iters, _stream()), ctx.h)
     return r.value
+
+
+# ---------------------------------------------------------------------- subspace and multigrid
+def _ivec(v):
+    return (C.c_int * 4)(*v)
+
+
+def cheby_filter(ctx, out, inp, nrhs, lo, hi, order, mf):
+    check(lib().cheby_filter(ctx.h, _ptr(out), _ptr(inp), nrhs, lo, hi, order, mf, _prec_of(inp),
+                             _stream()), ctx.h)
+    return out
+
+
+def cheby_recursive_basis(ctx, phi, eta, lam_lo, lam_max, m, delta, nvec, mf):
+    check(lib().cheby_recursive_basis(ctx.h, _ptr(phi), _ptr(eta), lam_lo, lam_max, m, delta, nvec,
+                                      mf, _prec_of(eta), _stream()), ctx.h)
+    return phi
+
+
+def dwf_chiral_project(ctx, out, inp, sign, nrhs=1):
+    check(lib().dwf_chiral_project(ctx.h, _ptr(out), _ptr(inp), sign, _prec_of(inp), nrhs,
+                                   _stream()), ctx.h)
+    return out
+
+
+def block_orthonormalise(ctx, basis, nb, nplus, block):
+    check(lib().block_orthonormalise(ctx.h, _ptr(basis), nb, nplus, _ivec(block), _stream()), ctx.h)
+    return basis
+
+
+class Coarse:
+    """A dwf_coarse: the 9-point little Dirac operator of H_DW."""
+
+    def __init__(self, handle, ctx, owned=True):
+        self.h = handle
+        self.ctx = ctx
+        self.owned = owned
+        dims = (C.c_int * 5)()
+        check(lib().coarse_export(self.h, None, dims))
+        self.Lc = tuple(dims[:4])
+        self.nb = dims[4]
+        self.nc = int(np.prod(self.Lc))
+
+    def export(self):
+        """FP64 operator as complex128 numpy (nc, 9, nb, nb)."""
+        A = np.zeros((self.nc, 9, self.nb, self.nb), np.complex128)
+        check(lib().coarse_export(self.h, _ptr(A), None))
+        return A
+
+    def close(self):
+        if self.owned and self.h:
+            lib().coarse_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def coarse_build(ctx, basis, nb, nplus, block, mf):
+    h = C.c_void_p()
+    check(lib().coarse_build(ctx.h, _ptr(basis), nb, nplus, _ivec(block), mf, _prec_of(basis),
+                             C.byref(h), _stream()), ctx.h)
+    return Coarse(h, ctx)
+
+
+def coarse_apply(coarse, out, inp, nrhs=1):
+    check(lib().coarse_apply(coarse.h, _ptr(out), _ptr(inp), nrhs, _stream()), coarse.ctx.h)
+    return out
+
+
+def coarse_solve(coarse, e, r, tol, maxiter=1000):
+    it = C.c_int()
+    check(lib().coarse_solve(coarse.h, _ptr(e), _ptr(r), tol, maxiter, C.byref(it), _stream()),
+          coarse.ctx.h)
+    return it.value
+
+
+def dwf_restrict(ctx, out, inp, basis, nb, block, nrhs=1):
+    check(lib().dwf_restrict(ctx.h, _ptr(out), _ptr(inp), _ptr(basis), nb, _ivec(block), nrhs,
+                             _prec_of(basis), _stream()), ctx.h)
+    return out
+
+
+def dwf_prolong(ctx, out, inp, basis, nb, block, nrhs=1, accumulate=0):
+    check(lib().dwf_prolong(ctx.h, _ptr(out), _ptr(inp), _ptr(basis), nb, _ivec(block), nrhs,
+                            _prec_of(basis), accumulate, _stream()), ctx.h)
+    return out
+
+
+def mg_params(block, nbasis, mf, *, subspace_mode=_lib.SUBSPACE_BATCH, lambda_lo=0.02,
+              lambda_max=60.0, filter_order=60, delta=100, smooth=(0.5, 60.0, 12),
+              coarse_tol=0.02, coarse_maxiter=500, nkrylov=8, maxiter=1000):
+    p = _lib.MGParams()
+    p.block = (C.c_int * 4)(*block)
+    p.nbasis, p.subspace_mode, p.mf = nbasis, subspace_mode, mf
+    p.lambda_lo, p.lambda_max, p.filter_order, p.delta = lambda_lo, lambda_max, filter_order, delta
+    p.smooth_lo, p.smooth_hi, p.smooth_order = smooth
+    p.coarse_tol, p.coarse_maxiter, p.nkrylov, p.maxiter = coarse_tol, coarse_maxiter, nkrylov, maxiter
+    return p
+
+
+class MG:
+    """A dwf_mg: HDCR multigrid setup (basis + little Dirac operator)."""
+
+    def __init__(self, ctx, params, eta):
+        h = C.c_void_p()
+        check(lib().mg_setup(ctx.h, C.byref(params), _ptr(eta), C.byref(h), _stream()), ctx.h)
+        self.h = h
+        self.ctx = ctx
+        self.params = params
+        self.coarse = Coarse(C.c_void_p(lib().mg_coarse(h)), ctx, owned=False)
+
+    def basis(self):
+        nb = self.params.nbasis
+        out = torch.zeros(nb * 2 * self.ctx.half_numel(), dtype=torch.float32, device="cuda")
+        check(lib().mg_export_basis(self.h, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mg_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_smooth(mg, out, inp):
+    check(lib().mg_smooth(mg.h, _ptr(out), _ptr(inp), _stream()), mg.ctx.h)
+    return out
+
+
+def mg_precondition(mg, out, inp):
+    check(lib().mg_precondition(mg.h, _ptr(out), _ptr(inp), _stream()), mg.ctx.h)
+    return out
+
+
+def mg_solve(mg, x, b, tol):
+    st = SolveStats()
+    check(lib().mg_solve(mg.h, _ptr(x), _ptr(b), tol, C.byref(st), _stream()), mg.ctx.h)
+    return st.as_dict()
+
+
+def dwf_force(ctx, force, X, masses):
+    """force (complex128 device tensor, gauge layout) += sum_i G_i for the even
+    solutions X (npf half fields back to back, FP64 or FP32)."""
+    m = (C.c_double * len(masses))(*masses)
+    check(lib().dwf_force(ctx.h, _ptr(force), _ptr(X), m, len(masses), _prec_of(X), _stream()), ctx.h)
+    return force
+
+
+def rbcg_normal_solve(ctx, x, phi, mf, tol, maxiter=100000, policy=_lib.SOLVE_MIXED_F32):
+    """x = (M_pc^dag M_pc)^-1 phi on the even parity (FP64 device half fields)."""
+    st = SolveStats()
+    check(lib().rbcg_normal_solve(ctx.h, _ptr(x), _ptr(phi), mf, tol, maxiter, policy, C.byref(st),
+                                  _stream()), ctx.h)
+    return st.as_dict()

@@ -1,0 +1,283 @@
+"""GPU parity of the HDCR multigrid path through the C ABI against the FP64
+oracle (Secs. 3.1-3.4 of arXiv:2103.05034).
+
+Tolerances: FP64 kernels 1e-11 relative (norm-wise); FP32 kernels 1e-5
+relative (a few hundred FP32 roundings of O(1) numbers, 6e-8 each, with
+Chebyshev recurrences of order <= 12 amplifying by at most ~10); iterative
+results are compared as stated per test."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import cheby, coarse, dwf, krylov, mg
+from paper_2103_05034_gb300 import layout, ops
+from paper_2103_05034_gb300._lib import F32, F64, SUBSPACE_BATCH, SUBSPACE_RECURSIVE
+
+from gpu_helpers import dev_to_full_canon, full_dev, rel
+
+pytestmark = pytest.mark.gpu
+M5 = 1.8
+
+
+def fulls_dev(vecs, L, prec):
+    return torch.cat([full_dev(v, L, prec).reshape(-1) for v in vecs])
+
+
+def fulls_canon(t, L, Ls, n):
+    a = layout.real_to_complex(t.double().cpu().numpy()).reshape(n, 2, -1, 4, 3, Ls)
+    return [layout.from_full(a[i], L) for i in range(n)]
+
+
+@pytest.fixture(scope="module")
+def small():
+    L, Ls, mf = (4, 4, 4, 4), 4, 0.05
+    U = synth.random_gauge(L, 0.5, 41)
+    ctx = ops.Context(L, Ls, M5, U)
+    appA = lambda v: dwf.mdagm(U, v, M5, mf)
+    lmax = krylov.power_max(appA, synth.gaussian_spinor(L, Ls, 1), 200) * 1.1
+    yield L, Ls, mf, U, ctx, lmax
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-11), (F32, 2e-5)])
+def test_cheby_filter_batched(small, prec, tol):
+    L, Ls, mf, U, ctx, lmax = small
+    vs = [synth.gaussian_spinor(L, Ls, 50 + i) for i in range(3)]
+    inp = fulls_dev(vs, L, prec)
+    out = torch.zeros_like(inp)
+    order, lo = 9, 0.5
+    ops.cheby_filter(ctx, out, inp, 3, lo, lmax, order, mf)
+    got = fulls_canon(out, L, Ls, 3)
+    appA = lambda v: dwf.mdagm(U, v, M5, mf)
+    for g, v in zip(got, vs):
+        assert rel(g, cheby.cheby_filter(appA, v, order, lo, lmax)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-10), (F32, 1e-4)])
+def test_recursive_basis(small, prec, tol):
+    L, Ls, mf, U, ctx, lmax = small
+    eta = synth.gaussian_spinor(L, Ls, 60)
+    m, delta, nvec, lo = 7, 3, 4, 0.2
+    phi = torch.zeros(nvec * 2 * ctx.half_numel(), dtype=torch.float64 if prec == F64 else torch.float32,
+                      device="cuda")
+    ops.cheby_recursive_basis(ctx, phi, full_dev(eta, L, prec), lo, lmax, m, delta, nvec, mf)
+    got = fulls_canon(phi, L, Ls, nvec)
+    want = cheby.recursive_basis(lambda v: dwf.mdagm(U, v, M5, mf), eta, m, delta, nvec, lo, lmax)
+    for g, w in zip(got, want):
+        assert rel(g, w) < tol
+
+
+def test_chiral_projection(small):
+    L, Ls, mf, U, ctx, lmax = small
+    v = synth.gaussian_spinor(L, Ls, 61)
+    for sign in (1, -1):
+        d = full_dev(v, L, F64)
+        ops.dwf_chiral_project(ctx, d, d, sign)
+        assert rel(dev_to_full_canon(d, L, Ls), coarse.chiral_project(v, sign)) < 1e-15
+
+
+def oracle_basis(U, L, Ls, block, nvec, seed, mf):
+    appA = lambda w: dwf.mdagm(U, w, M5, mf)
+    raw = [cheby.cheby_filter(appA, synth.gaussian_spinor(L, Ls, seed + i), 4, 0.5, 70.0)
+           for i in range(nvec)]
+    half = nvec // 2
+    pre = [coarse.chiral_project(v, +1) for v in raw[:half]] + \
+          [coarse.chiral_project(v, -1) for v in raw[half:]]
+    return pre, coarse.block_orthonormalise(pre, block, [list(range(half)), list(range(half, nvec))])
+
+
+@pytest.mark.parametrize("L,block,nb", [((4, 4, 4, 4), (2, 2, 2, 2), 4), ((4, 4, 2, 8), (2, 2, 2, 4), 6),
+                                        ((8, 4, 4, 4), (4, 4, 2, 2), 8)])
+def test_block_orthonormalise_matches_mgs(L, block, nb):
+    Ls, mf = 4, 0.1
+    U = synth.random_gauge(L, 0.5, 42)
+    ctx = ops.Context(L, Ls, M5, U)
+    pre, want = oracle_basis(U, L, Ls, block, nb, 100, mf)
+    d = fulls_dev(pre, L, F64)
+    ops.block_orthonormalise(ctx, d, nb, nb // 2, block)
+    got = fulls_canon(d, L, Ls, nb)
+    for g, w in zip(got, want):
+        assert rel(g, w) < 1e-10
+    ctx.close()
+
+
+@pytest.fixture(scope="module", params=[((4, 4, 4, 4), (2, 2, 2, 2), 4), ((4, 4, 2, 8), (2, 2, 2, 2), 4),
+                                        ((8, 4, 4, 4), (4, 2, 2, 2), 6)],
+                ids=["4444_b2222", "4428_b2222", "8444_b4222"])
+def coarse_case(request):
+    L, block, nb = request.param
+    Ls, mf = 4, 0.1
+    U = synth.random_gauge(L, 0.5, 43)
+    ctx = ops.Context(L, Ls, M5, U)
+    _, basis = oracle_basis(U, L, Ls, block, nb, 200, mf)
+    A = coarse.coarse_build(U, basis, block, M5, mf)  # (9, Tc, Zc, Yc, Xc, nb, nb)
+    Aflat = np.moveaxis(A.reshape(9, -1, nb, nb), 0, 1)  # (nc, 9, nb, nb)
+    yield L, Ls, block, nb, mf, U, ctx, basis, A, Aflat
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-12), (F32, 2e-6)])
+def test_coarse_build(coarse_case, prec, tol):
+    L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
+    C = ops.coarse_build(ctx, fulls_dev(basis, L, prec), nb, nb // 2, block, mf)
+    got = C.export()
+    assert rel(got, Aflat) < tol
+    C.close()
+
+
+def coarse_vec(A, nb, nrhs, seed):
+    nc = A.shape[0]
+    return synth.complex_gaussian(seed, (nc, nb, nrhs))
+
+
+def oracle_coarse_apply(A, v, Lc):
+    """v (nc, nb, nrhs) -> stencil apply with the oracle per rhs."""
+    nb = v.shape[1]
+    Ast = np.moveaxis(A, 1, 0).reshape((9, Lc[3], Lc[2], Lc[1], Lc[0], nb, nb))
+    out = np.zeros_like(v)
+    for r in range(v.shape[2]):
+        vc = v[:, :, r].reshape(Lc[3], Lc[2], Lc[1], Lc[0], nb)
+        out[:, :, r] = coarse.coarse_apply(Ast, vc).reshape(-1, nb)
+    return out
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 32])
+def test_coarse_apply(coarse_case, nrhs):
+    L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
+    C = ops.coarse_build(ctx, fulls_dev(basis, L, F64), nb, nb // 2, block, mf)
+    v = coarse_vec(Aflat, nb, nrhs, 7)
+    vd = torch.from_numpy(layout.complex_to_real(v, F32).reshape(-1)).cuda()
+    out = torch.zeros_like(vd)
+    ops.coarse_apply(C, out, vd, nrhs)
+    got = layout.real_to_complex(out.double().cpu().numpy()).reshape(v.shape)
+    want = oracle_coarse_apply(C.export(), v, C.Lc)
+    assert rel(got, want) < 1e-6
+    C.close()
+
+
+def test_coarse_solve(coarse_case):
+    L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
+    C = ops.coarse_build(ctx, fulls_dev(basis, L, F64), nb, nb // 2, block, mf)
+    r = coarse_vec(Aflat, nb, 1, 8)[:, :, 0]
+    rd = torch.from_numpy(layout.complex_to_real(r, F32).reshape(-1)).cuda()
+    e = torch.zeros_like(rd)
+    it = ops.coarse_solve(C, e, rd, 1e-5, 2000)
+    assert it > 0
+    eg = layout.real_to_complex(e.double().cpu().numpy()).reshape(r.shape)
+    dense = coarse.coarse_dense_from_stencil(np.moveaxis(C.export(), 1, 0).reshape(
+        (9,) + tuple(C.Lc[::-1]) + (nb, nb)))
+    # the stopping rule bounds the normal residual |A^2 e - A r| <= 1e-5 |A r|
+    Ar = dense @ r.ravel()
+    assert np.linalg.norm(dense @ (dense @ eg.ravel()) - Ar) <= 2e-5 * np.linalg.norm(Ar)
+    # and the oracle's CG on A^2 with the same rule reaches the same solution
+    e_or, it_or = coarse.coarse_cgnr(np.moveaxis(C.export(), 1, 0).reshape((9,) + tuple(C.Lc[::-1]) + (nb, nb)),
+                                     r.reshape(tuple(C.Lc[::-1]) + (nb,)), 1e-5, 2000)
+    assert abs(it - it_or) <= 4
+    want = np.linalg.solve(dense, r.ravel())
+    assert rel(eg.ravel(), want) < 10 * rel(e_or.ravel(), want) + 1e-5
+    C.close()
+
+
+def test_restrict_prolong(coarse_case):
+    L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
+    bd = fulls_dev(basis, L, F32)
+    psi = synth.gaussian_spinor(L, Ls, 9)
+    out = torch.zeros(2 * Aflat.shape[0] * nb, dtype=torch.float32, device="cuda")
+    ops.dwf_restrict(ctx, out, full_dev(psi, L, F32), bd, nb, block)
+    got = layout.real_to_complex(out.double().cpu().numpy()).reshape(-1, nb)
+    want = coarse.restrict(basis, psi, block).reshape(-1, nb)
+    assert rel(got, want) < 1e-6
+    ec = synth.complex_gaussian(10, want.shape)
+    ed = torch.from_numpy(layout.complex_to_real(ec, F32).reshape(-1)).cuda()
+    fine = ctx.new_full(F32)
+    ops.dwf_prolong(ctx, fine, ed, bd, nb, block)
+    Lc = [L[m] // block[m] for m in range(4)]
+    wantf = coarse.prolong(basis, ec.reshape(Lc[3], Lc[2], Lc[1], Lc[0], nb), block)
+    assert rel(dev_to_full_canon(fine, L, Ls), wantf) < 1e-6
+
+
+# ---------------------------------------------------------------- full setup, smoother, V-cycle, solve
+@pytest.fixture(scope="module")
+def mg_case():
+    L, Ls, mf = (4, 4, 4, 4), 4, 0.05
+    block, nb = (2, 2, 2, 2), 8
+    U = synth.random_gauge(L, 0.5, 51)
+    ctx = ops.Context(L, Ls, M5, U)
+    etas = [synth.gaussian_spinor(L, Ls, 600 + i) for i in range(nb)]
+    p = ops.mg_params(block, nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=0.5, lambda_max=70.0,
+                      filter_order=4, smooth=(0.5, 60.0, 6), coarse_tol=0.02, coarse_maxiter=500,
+                      nkrylov=8, maxiter=200)
+    G = ops.MG(ctx, p, fulls_dev(etas, L, F64))
+    yield L, Ls, mf, block, nb, U, ctx, etas, p, G
+    G.close()
+    ctx.close()
+
+
+def test_mg_setup_basis_matches_oracle(mg_case):
+    L, Ls, mf, block, nb, U, ctx, etas, p, G = mg_case
+    appA = lambda w: dwf.mdagm(U, w, M5, mf)
+    raw = [cheby.cheby_filter(appA, e, 4, 0.5, 70.0) for e in etas]
+    raw = [v / np.sqrt(dwf.norm2(v)) for v in raw]
+    pre = [coarse.chiral_project(v, +1) for v in raw[:nb // 2]] + \
+          [coarse.chiral_project(v, -1) for v in raw[nb // 2:]]
+    want = coarse.block_orthonormalise(pre, block, [list(range(nb // 2)), list(range(nb // 2, nb))])
+    got = fulls_canon(G.basis(), L, Ls, nb)
+    for g, w in zip(got, want):
+        assert rel(g, w) < 1e-5
+
+
+def test_mg_smoother(mg_case):
+    L, Ls, mf, block, nb, U, ctx, etas, p, G = mg_case
+    r = synth.gaussian_spinor(L, Ls, 70)
+    out = ctx.new_full(F32)
+    ops.mg_smooth(G, out, full_dev(r, L, F32))
+    appH = lambda w: dwf.hdw(U, w, M5, mf)
+    want, nA = cheby.smoother_apply(appH, appH, r, 0.5, 60.0, 6)
+    assert rel(dev_to_full_canon(out, L, Ls), want) < 2e-5
+
+
+def test_mg_vcycle(mg_case):
+    """V(1,1) against the oracle's sequence on the GPU's own (exported) basis.
+    Both coarse solves run the same CG on A^2 to a relative normal residual of
+    1e-6 (FP32 on the GPU, FP64 in the oracle), so the two corrections differ
+    by about 1e-6 times the coarse condition number."""
+    L, Ls, mf, block, nb, U, ctx, etas, p, G = mg_case
+    p2 = ops.mg_params(block, nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=0.5, lambda_max=70.0,
+                       filter_order=4, smooth=(0.5, 60.0, 6), coarse_tol=1e-6, coarse_maxiter=2000)
+    G2 = ops.MG(ctx, p2, fulls_dev(etas, L, F64))
+    basis = fulls_canon(G2.basis(), L, Ls, nb)
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    r = synth.gaussian_spinor(L, Ls, 71)
+    out = ctx.new_full(F32)
+    ops.mg_precondition(G2, out, full_dev(r, L, F32))
+    appH = lambda w: dwf.hdw(U, w, M5, mf)
+    want = mg.vcycle(appH, r, basis, A, block, (0.5, 60.0, 6), 1e-6, 5000, mg.MGCounter())
+    got = dev_to_full_canon(out, L, Ls)
+    assert rel(got, want) < 1e-3
+    # the preconditioned residual is smaller than the residual itself
+    assert np.sqrt(dwf.norm2(r - appH(got))) < np.sqrt(dwf.norm2(r))
+    G2.close()
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_mg_solve(mg_case, host):
+    L, Ls, mf, block, nb, U, ctx, etas, p, G = mg_case
+    b = synth.gaussian_spinor(L, Ls, 72)
+    tol = 1e-8
+    if host:
+        bh = layout.complex_to_real(layout.to_full(b, L), F64)
+        xh = np.zeros_like(bh)
+        st = ops.mg_solve(G, xh, bh, tol)
+        x = layout.from_full(layout.real_to_complex(xh).reshape(2, -1, 4, 3, Ls), L)
+    else:
+        bd = full_dev(b, L, F64)
+        xd = torch.zeros_like(bd)
+        st = ops.mg_solve(G, xd, bd, tol)
+        x = dev_to_full_canon(xd, L, Ls)
+    res = krylov.true_residual(U, x, b, M5, mf)
+    assert res <= tol * 1.01, st
+    assert st["true_residual"] == pytest.approx(res, rel=1e-3, abs=1e-14)
+    xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert rel(x, xr) < 1e-6
+    assert st["coarse_iterations"] > 0 and st["fine_matmuls"] > 0
