@@ -180,6 +180,73 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------- MG vs FP64 RB-CG
+# HDCR parameters for the 16^3x32, Ls=16 workload: the batched-subspace reading
+# (32 Gaussians, T_60 on [0.02, lambda_max], 4^4 x Ls blocks, 32 basis vectors)
+# with the paper's smoother S_cheb([0.5, 60], 12), coarse CG to 0.02 and pGCR.
+MG_PARAMS = dict(block=(4, 4, 4, 4), nbasis=32, filter_order=60, lambda_lo=0.02,
+                 smooth=(0.5, 60.0, 12), coarse_tol=0.02, coarse_maxiter=500, nkrylov=8,
+                 maxiter=500)
+
+
+def mg_vs_fp64(ctx, w, b, bd, tol):
+    """Time to a true residual of `tol` on the same GPU and source: plain FP64
+    red-black CG against HDCR setup + solve (mixed precision).  One run each,
+    outside the timed steps; CUDA-event and host-clock times agree because
+    both calls synchronise."""
+    import torch
+
+    from paper_2103_05034_gb300 import ops
+    from paper_2103_05034_gb300._lib import F64, SOLVE_F64, SUBSPACE_BATCH
+
+    L, Ls, mf = w["L"], w["Ls"], w["mf"]
+    out = {}
+    x = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ops.rbcg_solve(ctx, x, bd, mf, tol, 100000, SOLVE_F64)
+    out["fp64_rbcg_s"] = time.perf_counter() - t0
+    out["fp64_rbcg_iterations"] = st["iterations"]
+    out["fp64_rbcg_true_residual"] = st["true_residual"]
+    from paper_2103_05034_gb300 import layout
+    p = dict(MG_PARAMS)
+    nb = p["nbasis"]
+    t0 = time.perf_counter()
+    v0 = torch.from_numpy(layout.complex_to_real(layout.to_full(synth.gaussian_spinor(L, Ls, 77), L), F64)).cuda()
+    eta = torch.cat([torch.from_numpy(layout.complex_to_real(
+        layout.to_full(synth.gaussian_spinor(L, Ls, synth.SEED_BASIS + i), L), F64).reshape(-1))
+        for i in range(nb)]).cuda()
+    torch.cuda.synchronize()
+    t_in = time.perf_counter() - t0  # host-side input generation, not counted
+    t0 = time.perf_counter()
+    # lambda_max of D^dag D bounds the filter interval (power method, FP64, 5 % margin)
+    lmax = ops.dwf_power_max(ctx, v0, mf, 30) * 1.05
+    prm = ops.mg_params(p["block"], nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=p["lambda_lo"],
+                        lambda_max=lmax, filter_order=p["filter_order"],
+                        smooth=p["smooth"], coarse_tol=p["coarse_tol"],
+                        coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"], maxiter=p["maxiter"])
+    G = ops.MG(ctx, prm, eta)
+    torch.cuda.synchronize()
+    out["mg_setup_s"] = time.perf_counter() - t0
+    x.zero_()
+    t0 = time.perf_counter()
+    sm = ops.mg_solve(G, x, bd, tol)
+    out["mg_solve_s"] = time.perf_counter() - t0
+    out["mg_outer_iterations"] = sm["iterations"]
+    out["mg_coarse_iterations"] = sm["coarse_iterations"]
+    out["mg_fine_matmuls"] = sm["fine_matmuls"]
+    out["mg_true_residual"] = sm["true_residual"]
+    out["mg_subspace_s"] = sm["setup_seconds"]
+    out["mg_coarse_op_s"] = sm["coarse_op_seconds"]
+    out["mg_total_s"] = out["mg_setup_s"] + out["mg_solve_s"]
+    out["speedup_fp64_over_mg"] = out["fp64_rbcg_s"] / out["mg_total_s"]
+    out["lambda_max"] = lmax
+    out["params"] = {k: v for k, v in p.items()}
+    out["input_generation_s_not_counted"] = t_in
+    G.close()
+    return out
+
+
 # ---------------------------------------------------------------------- GPU leg
 def run_ours(args):
     import torch
@@ -199,6 +266,7 @@ def run_ours(args):
     w, U, b = build_workload(args.workload, rank)
     L, Ls, M5, mf = w["L"], w["Ls"], w["M5"], w["mf"]
     ctx = ops.Context(L, Ls, M5, U)
+    hop_variant, hop_tuned_ms = ops.dwf_autotune(ctx, F32, 20)  # setup, not timed
     bfull = layout.complex_to_real(layout.to_full(b, L), F64)
     bd = torch.from_numpy(bfull).to(dev)
     xd = torch.zeros_like(bd)
@@ -307,7 +375,8 @@ def run_ours(args):
             "config": {"workload": args.workload, "lattice": list(L), "Ls": Ls, "M5": M5, "mf": mf,
                        "solver": "red-black CGNR, FP32 inner, FP64 reliable updates",
                        "tol_true_residual": args.tol, "l2": "flushed (512 MB write) before each step",
-                       "parallelism": f"replicas{world}"},
+                       "parallelism": f"replicas{world}",
+                       "hop_variant_f32": hop_variant, "hop_autotune_ms": hop_tuned_ms},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "roofline": roofline,
@@ -316,6 +385,11 @@ def run_ours(args):
                       "true_residual": s0["true_residual"], "fine_matmuls": s0["fine_matmuls"],
                       "seconds": t_max / args.steps, "wall_seconds_all_steps": t_wall},
         }
+        if args.mg_compare:
+            try:
+                line["mg_vs_fp64"] = mg_vs_fp64(ctx, w, b, bd, args.tol)
+            except Exception as e:  # reported, not hidden: the line says what failed
+                line["mg_vs_fp64"] = {"error": str(e)}
         if args.cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline_leg(w, U, b)
     ctx.close()
@@ -340,6 +414,7 @@ def run_kernel(args):
     ctx = ops.Context(L, Ls, w["M5"], U)
     kind, prec_name = args.kernel.split("_")
     prec = {"f64": F64, "f32": F32, "f16": F16S}[prec_name]
+    variant, tuned_ms = ops.dwf_autotune(ctx, prec, 10)
     inp = torch.from_numpy(layout.complex_to_real(layout.to_half(b, L, 1), prec)).cuda()
     out = torch.zeros_like(inp)
     fn = {"dhop": lambda: ops.dwf_dhop(ctx, out, inp, 0),
@@ -354,7 +429,8 @@ def run_kernel(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "ms_per_call": ms}))
+    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "ms_per_call": ms,
+                      "hop_variant": variant, "autotune_ms": tuned_ms}))
     ctx.close()
     return 0
 
@@ -368,6 +444,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="dwf_16x16x16x32_ls16", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-mg-compare", dest="mg_compare", action="store_false",
+                    help="skip the one-off FP64 RB-CG vs HDCR time-to-solution comparison")
     ap.add_argument("--kernel", default=None,
                     help="profile mode: dhop_f32, dhop_f64, dhop_f16 or mpcdagmpc_f32 alone")
     args = ap.parse_args(argv)

@@ -122,6 +122,17 @@ int64_t dwf_half_bytes(const dwf_ctx* ctx, int prec);
 int dwf_counters(const dwf_ctx* ctx, int64_t* launches, double* hop_bytes);
 int dwf_reset_counters(dwf_ctx* ctx);
 
+/* Autotuner of the hopping kernel: times every tuning variant (register cap x
+ * neighbour prefetch; 6 variants for FP32 and FP16 storage at Ls >= 16, one
+ * otherwise) on this context's lattice, `reps` launches each, keeps the
+ * fastest for precision `prec` and returns its time per launch in *best_ms
+ * (may be NULL).  Uses context workspace; tuning launches are not counted.
+ * Synchronises.  dwf_set_hop_variant / dwf_get_hop_variant pin or read the
+ * choice (0 = untuned default). */
+int dwf_autotune(dwf_ctx* ctx, int prec, int reps, double* best_ms, void* stream);
+int dwf_set_hop_variant(dwf_ctx* ctx, int prec, int variant);
+int dwf_get_hop_variant(const dwf_ctx* ctx, int prec);
+
 /* ------------------------------------------------------------------ operators */
 
 /* Wilson hopping term, Eq. (2), between parities: out (parity out_parity) =
@@ -254,8 +265,15 @@ int coarse_destroy(dwf_coarse* coarse);
  * row j, column k) and/or its shape to dims = {Lc_x, Lc_y, Lc_z, Lc_t, nb}. */
 int coarse_export(const dwf_coarse* coarse, void* A, int* dims);
 /* out(x) = sum_d A_d(x) in(x+d) for nrhs coarse vectors, FP32 complex, layout
- * [nc][nb][nrhs] (coarse site lexicographic in Lc, basis index, rhs). */
-int coarse_apply(dwf_coarse* coarse, void* out, const void* in, int nrhs, void* stream);
+ * [nc][nb][nrhs] (coarse site lexicographic in Lc, basis index, rhs).
+ * prec DWF_F32: CUDA cores, FP32 arithmetic (any nb, nrhs).  prec DWF_TF32:
+ * 5th-generation tensor cores (tcgen05.mma kind::tf32, inputs rounded to TF32,
+ * FP32 accumulation in tensor memory) for nb = 32, an even number of coarse
+ * sites and nrhs in {16, 32, 64}; other shapes return DWF_EINVAL.  The TF32
+ * path synchronises `stream` (it checks the kernel's bounded-wait flag and
+ * returns DWF_ETIMEOUT if a wait gave up). */
+#define DWF_TF32 3
+int coarse_apply(dwf_coarse* coarse, void* out, const void* in, int nrhs, int prec, void* stream);
 /* Coarse solve of Table 1 ("Coarse solver: CGNR"): CG on A^2 e = A r for one
  * FP32 coarse vector, stopping when the normal residual is below tol times its
  * initial value or after maxiter iterations (*iters receives the count). */

@@ -16,7 +16,7 @@ _lib = None
 
 DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ENOCONV, DWF_ENAN, DWF_ECUDA, DWF_ETIMEOUT, DWF_ERANGE = \
     0, -1, -2, -3, -4, -5, -6, -7
-F64, F32, F16S = 0, 1, 2
+F64, F32, F16S, TF32 = 0, 1, 2, 3
 SOLVE_F64, SOLVE_MIXED_F32, SOLVE_MIXED_F16 = 0, 1, 2
 STATUS_NAMES = {0: "DWF_OK", -1: "DWF_EINVAL", -2: "DWF_ENOMEM", -3: "DWF_ENOCONV",
                 -4: "DWF_ENAN", -5: "DWF_ECUDA", -6: "DWF_ETIMEOUT", -7: "DWF_ERANGE"}
@@ -92,6 +92,9 @@ _SIGS = {
     "dwf_half_bytes": (I64, [P, I]),
     "dwf_counters": (I, [P, C.POINTER(I64), C.POINTER(D)]),
     "dwf_reset_counters": (I, [P]),
+    "dwf_autotune": (I, [P, I, I, C.POINTER(D), P]),
+    "dwf_set_hop_variant": (I, [P, I, I]),
+    "dwf_get_hop_variant": (I, [P, I]),
     "dwf_dhop": (I, [P, P, P, I, I, I, I, P]),
     "dwf_mooee": (I, [P, P, P, D, I, I, I, P]),
     "dwf_mooee_inv": (I, [P, P, P, D, I, I, I, P]),
@@ -112,7 +115,7 @@ _SIGS = {
     "coarse_build": (I, [P, P, I, I, C.POINTER(C.c_int), D, I, C.POINTER(P), P]),
     "coarse_destroy": (I, [P]),
     "coarse_export": (I, [P, P, C.POINTER(C.c_int)]),
-    "coarse_apply": (I, [P, P, P, I, P]),
+    "coarse_apply": (I, [P, P, P, I, I, P]),
     "coarse_solve": (I, [P, P, P, D, I, C.POINTER(C.c_int), P]),
     "dwf_restrict": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, P]),
     "dwf_prolong": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, I, P]),

@@ -233,16 +233,23 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
     if (rc) return rc;
   }
   hp.partials = c->partials;
+  if (h.cg_x) {
+    hp.cg_mode = 1;
+    hp.cg_x = h.cg_x;
+    hp.cg_r = h.cg_r;
+    hp.cg_p = h.cg_p;
+    hp.cg_alpha = h.cg_alpha;
+  }
   int rc;
   switch (prec) {
     case DWF_F64:
-      rc = dwf_launch_hop_f64(hp, c->g.Ls, h.nrhs, st, nblocks);
+      rc = dwf_launch_hop_f64(hp, c->g.Ls, h.nrhs, c->hop_variant[0], st, nblocks);
       break;
     case DWF_F32:
-      rc = dwf_launch_hop_f32(hp, c->g.Ls, h.nrhs, st, nblocks);
+      rc = dwf_launch_hop_f32(hp, c->g.Ls, h.nrhs, c->hop_variant[1], st, nblocks);
       break;
     case DWF_F16S:
-      rc = dwf_launch_hop_f16(hp, c->g.Ls, h.nrhs, st, nblocks);
+      rc = dwf_launch_hop_f16(hp, c->g.Ls, h.nrhs, c->hop_variant[2], st, nblocks);
       break;
     default:
       return dwf_fail(c, DWF_EINVAL, "bad precision");
@@ -252,6 +259,67 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
   const double w = (double)dwf_complex_bytes(prec), wl = prec == DWF_F64 ? 16.0 : 8.0;
   c->hop_bytes += (double)c->g.Vh * ((double)c->g.Ls * h.nrhs * (24.0 + (h.aux_mode ? 12.0 : 0.0)) * w +
                                      72.0 * wl);
+  return DWF_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+extern "C" int dwf_set_hop_variant(dwf_ctx* c, int prec, int variant) {
+  if (!c || prec < DWF_F64 || prec > DWF_F16S || variant < 0 || variant >= DWF_HOP_VARIANTS) return DWF_EINVAL;
+  c->hop_variant[prec] = variant;
+  return DWF_OK;
+}
+
+extern "C" int dwf_get_hop_variant(const dwf_ctx* c, int prec) {
+  if (!c || prec < DWF_F64 || prec > DWF_F16S) return DWF_EINVAL;
+  return c->hop_variant[prec];
+}
+
+extern "C" int dwf_autotune(dwf_ctx* c, int prec, int reps, double* best_ms, void* stream) {
+  if (!c || prec < DWF_F64 || prec > DWF_F16S || reps < 1) return DWF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)dwf_half_bytes(c, prec);
+  void* a = dwf_workspace(c, 30, bytes);
+  void* b = dwf_workspace(c, 31, bytes);
+  if (!a || !b) return dwf_fail(c, DWF_ENOMEM, "autotune workspace");
+  DWF_CUDA(c, cudaMemsetAsync(a, 0, bytes, st));
+  cudaEvent_t e0, e1;
+  DWF_CUDA(c, cudaEventCreate(&e0));
+  DWF_CUDA(c, cudaEventCreate(&e1));
+  const int nv = (prec == DWF_F64 || c->g.Ls < 16) ? 1 : DWF_HOP_VARIANTS;
+  int best = 0;
+  float best_t = 1e30f;
+  const int64_t launches0 = c->launches;
+  const double bytes0 = c->hop_bytes;
+  for (int v = 0; v < nv; v++) {
+    c->hop_variant[prec] = v;
+    HopLaunch h;
+    memset(&h, 0, sizeof(h));
+    h.out = b;
+    h.in = a;
+    h.out_parity = 0;
+    h.nrhs = 1;
+    h.alpha = 1.0;
+    int rc = launch_hop(c, h, prec, st, nullptr);  // warm-up
+    if (rc) return rc;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; r++) launch_hop(c, h, prec, st, nullptr);
+    cudaEventRecord(e1, st);
+    DWF_CUDA(c, cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_t) {
+      best_t = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->hop_variant[prec] = best;
+  c->launches = launches0;  // tuning launches are not counted
+  c->hop_bytes = bytes0;
+  if (best_ms) *best_ms = best_t;
+  DWF_CUDA(c, cudaGetLastError());
   return DWF_OK;
 }
 
@@ -538,6 +606,33 @@ static int cg_apply(dwf_ctx* c, void* Ap, const void* p, void* y, void* todd, co
   return mpc_apply(c, Ap, y, todd, mf, 1, prec, 1, 0, st, nullptr);
 }
 
+// One fused CG step: y = M_pc p (|y|^2 = <p, A p> -> alpha), then
+// A p = M_pc^dag y whose last hopping launch updates x += alpha p,
+// r -= alpha A p and reduces |r|^2 (A p is never stored); *nparts partials.
+static int cg_step_fused(dwf_ctx* c, void* x, void* r, const void* p, void* y, void* todd, const double* mf,
+                         int prec, cudaStream_t st, int* nparts) {
+  int np = 0;
+  int rc = mpc_apply(c, y, p, todd, mf, 0, prec, 1, 1, st, &np);
+  if (rc) return rc;
+  rc = blas_finalize_mode(c, np, 1, S_PAP, 1, st);
+  if (rc) return rc;
+  HopLaunch h1 = hop_base(todd, y, 1, 1, 1, -0.5);
+  h1.inv_mode = 2;
+  h1.mf = mf;
+  rc = launch_hop(c, h1, prec, st, nullptr);
+  if (rc) return rc;
+  HopLaunch h2 = hop_base(nullptr, todd, 0, 1, 1, 0.5);
+  h2.aux = y;
+  h2.aux_mode = 3;
+  h2.mf = mf;
+  h2.reduce = 1;
+  h2.cg_x = x;
+  h2.cg_r = r;
+  h2.cg_p = p;
+  h2.cg_alpha = c->dscal + S_ALPHA;
+  return launch_hop(c, h2, prec, st, nparts);
+}
+
 // CG on M_pc^dag M_pc x_e = rhs with FP64 reliable updates.  With bp set (the
 // red-black solve) the stopping residual is the Schur residual |b'_e - M_pc x|
 // / bnorm, which equals the full true residual after reconstruction; without
@@ -569,12 +664,22 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
     if (have_x) {
       r = mpc_apply(c, yhi, x_e, ohi, mfa, 0, DWF_F64, 1, 0, st, nullptr);
       if (r) return r;
-      if (B.bp) {  // y = b'_e - M_pc x; r = M_pc^dag y
+      if (B.bp) {
+        // y = b'_e - M_pc x in FP64 (the true residual); r = M_pc^dag y only
+        // steers the inner CG, so it is applied in the inner precision.
         r = blas_axpby(c, 1.0, B.bp, DWF_F64, -1.0, yhi, DWF_F64, he, st);
         if (r) return r;
-        r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
-        if (r) return r;
         r = norm2_dev(c, yhi, he, DWF_F64, S_TMP2, st);
+        if (r) return r;
+        if (plo == DWF_F64) {
+          r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+        } else {
+          r = blas_copy(c, B.ylo, plo, yhi, DWF_F64, he, st);
+          if (r) return r;
+          r = mpc_apply(c, rlo, B.ylo, B.olo, mfa, 1, plo, 1, 0, st, nullptr);
+          if (r) return r;
+          r = blas_copy(c, rhi, DWF_F64, rlo, plo, he, st);
+        }
       } else {  // r = rhs - M^dag M x
         r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
         if (r) return r;
@@ -618,10 +723,8 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
   const int check_every = 8;
   bool converged = true_res <= tol;
   while (!converged && it < maxiter) {
-    rc = cg_apply(c, Ap, p, B.ylo, B.olo, mfa, plo, st);
-    if (rc) return rc;
     int np = 0;
-    rc = blas_cg_xr(c, xin, rlo, p, Ap, he, plo, S_ALPHA, st, &np);
+    rc = cg_step_fused(c, xin, rlo, p, B.ylo, B.olo, mfa, plo, st, &np);
     if (rc) return rc;
     rc = blas_finalize_mode(c, np, 1, S_RRNEW, 2, st);
     if (rc) return rc;

@@ -143,10 +143,14 @@ __global__ void __launch_bounds__(BT) k_axpbypcz(double a, const typename Prec<P
   for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
     const auto xv = ld_c(x + i);
     const auto yv = ld_c(y + i);
-    const auto zv = ld_c(z + i);
     cpx<R> o;
-    o.re = (R)a * xv.re + (R)b * yv.re + (R)cz * zv.re;
-    o.im = (R)a * xv.im + (R)b * yv.im + (R)cz * zv.im;
+    o.re = (R)a * xv.re + (R)b * yv.re;
+    o.im = (R)a * xv.im + (R)b * yv.im;
+    if (cz != 0.0) {  // z is not read when its coefficient is zero (it may be uninitialised)
+      const auto zv = ld_c(z + i);
+      o.re += (R)cz * zv.re;
+      o.im += (R)cz * zv.im;
+    }
     st_c(z + i, o);
   }
 }

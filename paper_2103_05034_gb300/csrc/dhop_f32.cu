@@ -1,8 +1,9 @@
 // Hopping-term and site-local fifth-dimension kernels instantiated for DWF_F32.
 #include "dhop_impl.cuh"
 
-int dwf_launch_hop_f32(const dwfk::HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nb) {
-  return dwfk::launch_hop_prec<DWF_F32>(hp, Ls, nrhs, st, nb);
+int dwf_launch_hop_f32(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st,
+                       int* nb) {
+  return dwfk::launch_hop_prec<DWF_F32>(hp, Ls, nrhs, variant, st, nb);
 }
 
 int dwf_launch_mooee_f32(void* out, const void* in, const dwfk::HopParams& hp, int dagger,

@@ -43,6 +43,13 @@ struct HopParams {
   int aux_mode, inv_mode, g5r5, reduce;
   long long rhs_stride;
   double d;
+  // fused CG update (cg_mode = 1): with v = the operator output A p,
+  // x += alpha p, r -= alpha v, |r|^2 reduced; v itself is not stored.
+  int cg_mode;
+  void* cg_x;
+  void* cg_r;
+  const void* cg_p;
+  const double* cg_alpha;  // device scalar
   double m[DWF_MAX_RHS];
   double kappa[DWF_MAX_RHS];
   double dls1[DWF_MAX_RHS];
@@ -152,8 +159,43 @@ __device__ __forceinline__ void minv_row(cpx<R>* row, bool fwd, R d, R m, R kapp
   }
 }
 
-template <int P, int LS, int SB>
-__global__ void __launch_bounds__(LS* SB) hop_kernel(const HopParams p) {
+// The same inverse in place with O(1) registers (shared-memory rows): a
+// forward pass leaves F_q in the row, the backward pass recovers
+// v_q = F_q - F_{q-1}/d, accumulates G and writes x_q = kappa/d (F_q - m G_q).
+template <class R, int LS>
+__device__ __forceinline__ void minv_row_inplace(cpx<R>* row, bool fwd, R d, R m, R kappa, R dls1) {
+  const R dinv = R(1) / d;
+  const R kd = kappa * dinv;
+  cpx<R> f = cmake<R>(0, 0);
+#pragma unroll 4
+  for (int q = 0; q < LS; q++) {
+    cpx<R>& e = row[fwd ? q : LS - 1 - q];
+    f.re = fma(f.re, dinv, e.re);
+    f.im = fma(f.im, dinv, e.im);
+    e = f;
+  }
+  cpx<R> g = cmake<R>(0, 0);
+  cpx<R> Fq = row[fwd ? LS - 1 : 0];
+#pragma unroll 4
+  for (int q = LS - 1; q >= 0; q--) {
+    const cpx<R> Fm = q > 0 ? row[fwd ? q - 1 : LS - q] : cmake<R>(0, 0);
+    const cpx<R> vq = cmake<R>(fma(-dinv, Fm.re, Fq.re), fma(-dinv, Fm.im, Fq.im));
+    row[fwd ? q : LS - 1 - q] = cmake<R>(kd * fma(-m, g.re, Fq.re), kd * fma(-m, g.im, Fq.im));
+    g.re = fma(d, g.re, dls1 * vq.re);
+    g.im = fma(d, g.im, dls1 * vq.im);
+    Fq = Fm;
+  }
+}
+
+// Register cap: REGS registers per thread give at least 65536/(LS*SB*REGS)
+// resident CTAs per SM (REGS = 0: no cap).  PF: prefetch the next neighbour.
+template <int LS, int SB, int REGS>
+struct HopMinBlocks {
+  static constexpr int v = REGS == 0 ? 1 : (65536 / (LS * SB * REGS) > 0 ? 65536 / (LS * SB * REGS) : 1);
+};
+
+template <int P, int LS, int SB, int REGS, int PF>
+__global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_kernel(const HopParams p) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
   typedef typename Prec<P>::LS LT;
@@ -201,23 +243,60 @@ __global__ void __launch_bounds__(LS* SB) hop_kernel(const HopParams p) {
     const int tp = (t + 1 == p.L3) ? 0 : t + 1, tm = (t == 0) ? p.L3 - 1 : t - 1;
     const R sf = (R)p.sg;
     const cpx<R>* U = sU + sl * 72;
-    cpx<R> ps[12];
-    load_spinor<P, LS>(ps, in + (size_t)cbi(xp, y, z, t) * 12 * LS, s);
-    hop_dir<R, 0>(v, ps, U + 0 * 9, sf);
-    load_spinor<P, LS>(ps, in + (size_t)cbi(xm, y, z, t) * 12 * LS, s);
-    hop_dir<R, 0>(v, ps, U + 1 * 9, -sf);
-    load_spinor<P, LS>(ps, in + (size_t)cbi(x, yp, z, t) * 12 * LS, s);
-    hop_dir<R, 1>(v, ps, U + 2 * 9, sf);
-    load_spinor<P, LS>(ps, in + (size_t)cbi(x, ym, z, t) * 12 * LS, s);
-    hop_dir<R, 1>(v, ps, U + 3 * 9, -sf);
-    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, zp, t) * 12 * LS, s);
-    hop_dir<R, 2>(v, ps, U + 4 * 9, sf);
-    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, zm, t) * 12 * LS, s);
-    hop_dir<R, 2>(v, ps, U + 5 * 9, -sf);
-    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, z, tp) * 12 * LS, s);
-    hop_dir<R, 3>(v, ps, U + 6 * 9, sf);
-    load_spinor<P, LS>(ps, in + (size_t)cbi(x, y, z, tm) * 12 * LS, s);
-    hop_dir<R, 3>(v, ps, U + 7 * 9, -sf);
+    in += s;
+    auto nbp = [&](int d) -> const S* {
+      int X = x, Y = y, Z = z, T = t;
+      switch (d) {
+        case 0: X = xp; break;
+        case 1: X = xm; break;
+        case 2: Y = yp; break;
+        case 3: Y = ym; break;
+        case 4: Z = zp; break;
+        case 5: Z = zm; break;
+        case 6: T = tp; break;
+        default: T = tm; break;
+      }
+      return in + (size_t)cbi(X, Y, Z, T) * (12 * LS);
+    };
+    if (PF) {
+      // register double buffer: the loads of neighbour d+1 are in flight while
+      // neighbour d is projected and multiplied
+      cpx<R> pa[12], pb[12];
+      load_spinor<P, LS>(pa, nbp(0), 0);
+      load_spinor<P, LS>(pb, nbp(1), 0);
+      hop_dir<R, 0>(v, pa, U + 0 * 9, sf);
+      load_spinor<P, LS>(pa, nbp(2), 0);
+      hop_dir<R, 0>(v, pb, U + 1 * 9, -sf);
+      load_spinor<P, LS>(pb, nbp(3), 0);
+      hop_dir<R, 1>(v, pa, U + 2 * 9, sf);
+      load_spinor<P, LS>(pa, nbp(4), 0);
+      hop_dir<R, 1>(v, pb, U + 3 * 9, -sf);
+      load_spinor<P, LS>(pb, nbp(5), 0);
+      hop_dir<R, 2>(v, pa, U + 4 * 9, sf);
+      load_spinor<P, LS>(pa, nbp(6), 0);
+      hop_dir<R, 2>(v, pb, U + 5 * 9, -sf);
+      load_spinor<P, LS>(pb, nbp(7), 0);
+      hop_dir<R, 3>(v, pa, U + 6 * 9, sf);
+      hop_dir<R, 3>(v, pb, U + 7 * 9, -sf);
+    } else {
+      cpx<R> ps[12];
+      load_spinor<P, LS>(ps, nbp(0), 0);
+      hop_dir<R, 0>(v, ps, U + 0 * 9, sf);
+      load_spinor<P, LS>(ps, nbp(1), 0);
+      hop_dir<R, 0>(v, ps, U + 1 * 9, -sf);
+      load_spinor<P, LS>(ps, nbp(2), 0);
+      hop_dir<R, 1>(v, ps, U + 2 * 9, sf);
+      load_spinor<P, LS>(ps, nbp(3), 0);
+      hop_dir<R, 1>(v, ps, U + 3 * 9, -sf);
+      load_spinor<P, LS>(ps, nbp(4), 0);
+      hop_dir<R, 2>(v, ps, U + 4 * 9, sf);
+      load_spinor<P, LS>(ps, nbp(5), 0);
+      hop_dir<R, 2>(v, ps, U + 5 * 9, -sf);
+      load_spinor<P, LS>(ps, nbp(6), 0);
+      hop_dir<R, 3>(v, ps, U + 6 * 9, sf);
+      load_spinor<P, LS>(ps, nbp(7), 0);
+      hop_dir<R, 3>(v, ps, U + 7 * 9, -sf);
+    }
 
     const R alpha = (R)p.alpha;
 #pragma unroll
@@ -261,7 +340,7 @@ __global__ void __launch_bounds__(LS* SB) hop_kernel(const HopParams p) {
       const int sl2 = w / 12, c2 = w - sl2 * 12;
       if (site0 + sl2 < p.Vh) {
         const bool fwd = (c2 < 6) != (p.inv_mode == 2);
-        minv_row<R, LS>(stage + (sl2 * 12 + c2) * (LS + 1), fwd, (R)p.d, (R)p.m[rhs],
+        minv_row_inplace<R, LS>(stage + (sl2 * 12 + c2) * (LS + 1), fwd, (R)p.d, (R)p.m[rhs],
                         (R)p.kappa[rhs], (R)p.dls1[rhs]);
       }
     }
@@ -272,7 +351,29 @@ __global__ void __launch_bounds__(LS* SB) hop_kernel(const HopParams p) {
     }
   }
 
-  if (active) {
+  if (p.cg_mode) {
+    // CG update on the operator output v = A p: x += alpha p, r -= alpha v;
+    // v becomes the new residual for the reduction below
+    if (active) {
+      const size_t off = (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS + s;
+      S* xs = (S*)p.cg_x + off;
+      S* rs = (S*)p.cg_r + off;
+      const S* ps = (const S*)p.cg_p + off;
+      const R alpha = (R)(*p.cg_alpha);
+#pragma unroll
+      for (int c = 0; c < 12; c++) {
+        cpx<R> xv = ld_c(xs + c * LS), rv = ld_c(rs + c * LS);
+        const cpx<R> pv = ld_c(ps + c * LS);
+        xv.re = fma(alpha, pv.re, xv.re);
+        xv.im = fma(alpha, pv.im, xv.im);
+        rv.re = fma(-alpha, v[c].re, rv.re);
+        rv.im = fma(-alpha, v[c].im, rv.im);
+        st_c(xs + c * LS, xv);
+        st_c(rs + c * LS, rv);
+        v[c] = rv;
+      }
+    }
+  } else if (active) {
     S* out = (S*)p.out + (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS;
     if (p.g5r5) {
       const int so = LS - 1 - s;
@@ -357,8 +458,41 @@ struct HopShape {
   static constexpr int SB = (LS >= 16) ? 8 : (128 / LS);
 };
 
+// Tuning variants of the hopping kernel: (register cap, prefetch).  Variant 0
+// is the uncapped kernel; the autotuner (dwf_autotune) times the rest on the
+// context's lattice and keeps the fastest per precision.
+#define DWF_HOP_VARIANTS 6
+__host__ __device__ constexpr int hop_variant_regs(int v) {
+  return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : 96;
+}
+__host__ __device__ constexpr int hop_variant_pf(int v) { return v >= 4 ? 1 : 0; }
+
+template <int P, int LSV, int V>
+inline void launch_hop_v(const HopParams& hp, dim3 grid, cudaStream_t st) {
+  constexpr int SB = HopShape<LSV>::SB;
+  hop_kernel<P, LSV, SB, hop_variant_regs(V), hop_variant_pf(V)><<<grid, LSV * SB, 0, st>>>(hp);
+}
+
+template <int P, int LSV>
+inline int launch_hop_ls(const HopParams& hp, dim3 grid, int variant, cudaStream_t st) {
+  // FP64 is ALU-bound and the small-Ls cases are test sizes: one variant.
+  if constexpr (P == DWF_F64 || LSV < 16) {
+    launch_hop_v<P, LSV, 0>(hp, grid, st);
+  } else {
+    switch (variant) {
+      case 1: launch_hop_v<P, LSV, 1>(hp, grid, st); break;
+      case 2: launch_hop_v<P, LSV, 2>(hp, grid, st); break;
+      case 3: launch_hop_v<P, LSV, 3>(hp, grid, st); break;
+      case 4: launch_hop_v<P, LSV, 4>(hp, grid, st); break;
+      case 5: launch_hop_v<P, LSV, 5>(hp, grid, st); break;
+      default: launch_hop_v<P, LSV, 0>(hp, grid, st); break;
+    }
+  }
+  return DWF_OK;
+}
+
 template <int P>
-int launch_hop_prec(const HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nblocks) {
+int launch_hop_prec(const HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nblocks) {
   dim3 grid;
   grid.y = nrhs;
   grid.z = 1;
@@ -366,9 +500,8 @@ int launch_hop_prec(const HopParams& hp, int Ls, int nrhs, cudaStream_t st, int*
   case LSV: {                                                                    \
     constexpr int SB = HopShape<LSV>::SB;                                        \
     grid.x = (hp.Vh + SB - 1) / SB;                                              \
-    hop_kernel<P, LSV, SB><<<grid, LSV * SB, 0, st>>>(hp);                       \
     if (nblocks) *nblocks = grid.x * grid.y;                                     \
-    return DWF_OK;                                                               \
+    return launch_hop_ls<P, LSV>(hp, grid, variant, st);                         \
   }
   switch (Ls) {
     DWF_HOP_CASE(4)
@@ -405,9 +538,9 @@ int launch_mooee_prec(void* out, const void* in, const HopParams& hp, int dagger
 }  // namespace dwfk
 
 // Per-precision entry points (defined in dhop_f64.cu, dhop_f32.cu, dhop_f16.cu).
-int dwf_launch_hop_f64(const dwfk::HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nb);
-int dwf_launch_hop_f32(const dwfk::HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nb);
-int dwf_launch_hop_f16(const dwfk::HopParams& hp, int Ls, int nrhs, cudaStream_t st, int* nb);
+int dwf_launch_hop_f64(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nb);
+int dwf_launch_hop_f32(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nb);
+int dwf_launch_hop_f16(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nb);
 int dwf_launch_mooee_f64(void* out, const void* in, const dwfk::HopParams& hp, int dagger,
                          int inverse, int Ls, int nrhs, long long rs, cudaStream_t st);
 int dwf_launch_mooee_f32(void* out, const void* in, const dwfk::HopParams& hp, int dagger,

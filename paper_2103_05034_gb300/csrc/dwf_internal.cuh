@@ -98,6 +98,7 @@ struct dwf_ctx {
   size_t partials_n;
   double* dscal;      // device scalars for solvers
   double* hscal;      // pinned host mirror
+  int hop_variant[3]; // tuned hopping-kernel variant per precision
   int64_t launches;   // kernel launches since the last counter reset
   double hop_bytes;   // algorithmic bytes of hopping-term launches
   std::string err;
@@ -137,6 +138,12 @@ struct HopLaunch {
   int g5r5;
   int reduce;          // 1: |out|^2 partials into ctx->partials
   const double* mf;    // host array [nrhs] of masses (aux_mode>=2 or inv_mode>0)
+  // fused CG update instead of storing out: x += alpha p, r -= alpha out,
+  // |r|^2 reduced (alpha = device scalar); requires reduce = 1
+  void* cg_x;
+  void* cg_r;
+  const void* cg_p;
+  const double* cg_alpha;
 };
 
 int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* nblocks);

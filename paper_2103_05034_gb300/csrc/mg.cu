@@ -19,9 +19,14 @@ struct dwf_coarse {
   int nb, nplus;
   double2* A64;  // [nc][9][nb][nb]
   float2* A32;   // same layout, FP32
+  float* At;     // tensor-core copy (real form, TF32, K-major), built on first use
+  int* err;      // device error flag of the tensor-core kernel
   void* ws[6];
   size_t ws_bytes[6];
 };
+
+int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, int nb, int nc,
+                    const int Lc[4], int nrhs, int* err_dev, cudaStream_t st);
 
 struct dwf_mg {
   dwf_ctx* ctx;
@@ -489,6 +494,8 @@ extern "C" int coarse_destroy(dwf_coarse* C) {
   if (!C) return DWF_OK;
   if (C->A64) cudaFree(C->A64);
   if (C->A32) cudaFree(C->A32);
+  if (C->At) cudaFree(C->At);
+  if (C->err) cudaFree(C->err);
   for (int i = 0; i < 6; i++)
     if (C->ws[i]) cudaFree(C->ws[i]);
   delete C;
@@ -511,11 +518,35 @@ extern "C" int coarse_export(const dwf_coarse* C, void* A, int* dims) {
   return DWF_OK;
 }
 
-extern "C" int coarse_apply(dwf_coarse* C, void* out, const void* in, int nrhs, void* stream) {
+extern "C" int coarse_apply(dwf_coarse* C, void* out, const void* in, int nrhs, int prec, void* stream) {
   if (!C || !out || !in || nrhs < 1) return DWF_EINVAL;
-  int rc = coarse_apply_dev(C, (float2*)out, (const float2*)in, nrhs, (cudaStream_t)stream);
-  if (rc) return rc;
-  DWF_CUDA(C->ctx, cudaGetLastError());
+  cudaStream_t st = (cudaStream_t)stream;
+  dwf_ctx* c = C->ctx;
+  if (prec == DWF_F32) {
+    int rc = coarse_apply_dev(C, (float2*)out, (const float2*)in, nrhs, st);
+    if (rc) return rc;
+    DWF_CUDA(c, cudaGetLastError());
+    return DWF_OK;
+  }
+  if (prec != DWF_TF32) return dwf_fail(c, DWF_EINVAL, "coarse_apply precision: DWF_F32 or DWF_TF32");
+  if (((uintptr_t)out & 15) || ((uintptr_t)in & 15)) return dwf_fail(c, DWF_EINVAL, "alignment");
+  if (!C->err) {
+    if (cudaMalloc(&C->err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return dwf_fail(c, DWF_ENOMEM, "coarse error flag");
+    }
+  }
+  DWF_CUDA(c, cudaMemsetAsync(C->err, 0, sizeof(int), st));
+  int rc = coarse_apply_tc(c, (float2*)out, (const float2*)in, C->A32, &C->At, C->nb, C->g.nc, C->g.Lc, nrhs,
+                           C->err, st);
+  if (rc == DWF_EINVAL)
+    return dwf_fail(c, rc, "tensor-core coarse apply needs nb = 32, an even number of coarse sites, nrhs 16/32/64");
+  if (rc) return dwf_fail(c, rc, "tensor-core coarse apply");
+  DWF_CUDA(c, cudaGetLastError());
+  int herr = 0;
+  DWF_CUDA(c, cudaMemcpyAsync(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DWF_CUDA(c, cudaStreamSynchronize(st));
+  if (herr) return dwf_fail(c, DWF_ETIMEOUT, "tensor-core coarse apply: a bounded barrier wait gave up");
   return DWF_OK;
 }
 

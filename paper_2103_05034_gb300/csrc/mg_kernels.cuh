@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) k_block_combine(typename Prec<PY>::S* Y, 
 // group); thread 0 factorises in shared memory (groups of at most 32 vectors).
 // Sets *fail if a pivot is not positive (the vectors are linearly dependent on
 // that block).
-__global__ void k_block_cholinv(const double2* G, double2* Rinv, int nb, int nplus, int* fail) {
+static __global__ void k_block_cholinv(const double2* G, double2* Rinv, int nb, int nplus, int* fail) {
   __shared__ double2 R[32][33];
   __shared__ double2 Ri[32][33];
   const int xc = blockIdx.x, grp = blockIdx.y;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(128) k_face_hop(typename Prec<P>::S* out, cons
 
 // Coarse 9-point stencil on CUDA cores: out[x][j][r] = sum_d sum_k
 // A[x][d][j][k] in[x+d][k][r]; vectors [nc][nb][nrhs] complex FP32.
-__global__ void __launch_bounds__(256) k_coarse_apply(float2* out, const float2* in, const float2* A,
+static __global__ void __launch_bounds__(256) k_coarse_apply(float2* out, const float2* in, const float2* A,
                                                       int Lc0, int Lc1, int Lc2, int Lc3, int nb, int nrhs) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int nc = Lc0 * Lc1 * Lc2 * Lc3;

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import F16S, F32, F64, SolveStats, check, lib
+from ._lib import F16S, F32, F64, TF32, SolveStats, check, lib
 
 _DTYPE = {F64: torch.float64, F32: torch.float32, F16S: torch.float16}
 
@@ -227,8 +227,9 @@ def coarse_build(ctx, basis, nb, nplus, block, mf):
     return Coarse(h, ctx)
 
 
-def coarse_apply(coarse, out, inp, nrhs=1):
-    check(lib().coarse_apply(coarse.h, _ptr(out), _ptr(inp), nrhs, _stream()), coarse.ctx.h)
+def coarse_apply(coarse, out, inp, nrhs=1, prec=F32):
+    """prec F32 (CUDA cores) or TF32 (tcgen05 tensor cores, nb = 32, nrhs 16/32/64)."""
+    check(lib().coarse_apply(coarse.h, _ptr(out), _ptr(inp), nrhs, prec, _stream()), coarse.ctx.h)
     return out
 
 
@@ -322,3 +323,15 @@ def rbcg_normal_solve(ctx, x, phi, mf, tol, maxiter=100000, policy=_lib.SOLVE_MI
     check(lib().rbcg_normal_solve(ctx.h, _ptr(x), _ptr(phi), mf, tol, maxiter, policy, C.byref(st),
                                   _stream()), ctx.h)
     return st.as_dict()
+
+
+def dwf_autotune(ctx, prec=F32, reps=20):
+    """Pick the fastest hopping-kernel variant for this lattice; returns
+    (variant, ms per launch)."""
+    ms = C.c_double()
+    check(lib().dwf_autotune(ctx.h, prec, reps, C.byref(ms), _stream()), ctx.h)
+    return lib().dwf_get_hop_variant(ctx.h, prec), ms.value
+
+
+def dwf_set_hop_variant(ctx, prec, variant):
+    check(lib().dwf_set_hop_variant(ctx.h, prec, variant))

@@ -281,3 +281,48 @@ def test_mg_solve(mg_case, host):
     xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
     assert rel(x, xr) < 1e-6
     assert st["coarse_iterations"] > 0 and st["fine_matmuls"] > 0
+
+
+@pytest.mark.parametrize("nrhs", [16, 32, 64])
+def test_coarse_apply_tensor_cores(nrhs):
+    """tcgen05 TF32 coarse stencil (nb = 32) against the oracle apply of the
+    exported FP64 operator.  TF32 rounds each input to 11 significant bits
+    (relative error <= 2^-11 = 4.9e-4); with FP32 accumulation of 576 terms of
+    random sign the norm-wise error is ~1e-3, so the bound is 3e-3."""
+    from paper_2103_05034_gb300._lib import TF32
+    L, Ls, mf, block, nb = (4, 4, 4, 8), 4, 0.1, (2, 2, 2, 2), 32
+    U = synth.random_gauge(L, 0.5, 44)
+    ctx = ops.Context(L, Ls, M5, U)
+    vecs = [coarse.chiral_project(synth.gaussian_spinor(L, Ls, 300 + i), 1 if i < nb // 2 else -1)
+            for i in range(nb)]
+    d = fulls_dev(vecs, L, F64)
+    ops.block_orthonormalise(ctx, d, nb, nb // 2, block)
+    C = ops.coarse_build(ctx, d, nb, nb // 2, block, mf)
+    v = synth.complex_gaussian(9, (C.nc, nb, nrhs))
+    vd = torch.from_numpy(layout.complex_to_real(v, F32).reshape(-1)).cuda()
+    out = torch.zeros_like(vd)
+    ops.coarse_apply(C, out, vd, nrhs, prec=TF32)
+    got = layout.real_to_complex(out.double().cpu().numpy()).reshape(v.shape)
+    want = oracle_coarse_apply(C.export(), v, C.Lc)
+    assert rel(got, want) < 3e-3
+    # and the FP32 CUDA-core path on the same operator
+    out32 = torch.zeros_like(vd)
+    ops.coarse_apply(C, out32, vd, nrhs)
+    got32 = layout.real_to_complex(out32.double().cpu().numpy()).reshape(v.shape)
+    assert rel(got32, want) < 1e-6
+    # a second call reuses the arranged operator
+    out.zero_()
+    ops.coarse_apply(C, out, vd, nrhs, prec=TF32)
+    assert rel(layout.real_to_complex(out.double().cpu().numpy()).reshape(v.shape), want) < 3e-3
+    C.close()
+    ctx.close()
+
+
+def test_coarse_apply_tensor_cores_rejects_unsupported_shapes(coarse_case):
+    from paper_2103_05034_gb300._lib import DWFError, TF32
+    L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
+    C = ops.coarse_build(ctx, fulls_dev(basis, L, F64), nb, nb // 2, block, mf)
+    v = torch.zeros(2 * C.nc * nb * 32, dtype=torch.float32, device="cuda")
+    with pytest.raises(DWFError):  # nb != 32 here
+        ops.coarse_apply(C, v.clone(), v, 32, prec=TF32)
+    C.close()
