@@ -178,6 +178,19 @@ int dwf_norm2(dwf_ctx* ctx, double* result, const void* a, int64_t n, int prec, 
 int dwf_cdot(dwf_ctx* ctx, double* result2, const void* a, const void* b, int64_t n,
              int prec, void* stream);
 
+/* Allocation-free |a|^2 (the paper has no counterpart; this serves callers
+ * that cannot call cudaMalloc when they need a global sum, e.g. code running
+ * under a memory pool that forbids new allocations or a plug-in handed only
+ * its buffers).  Same result as dwf_norm2 (FP64 accumulation, fixed order) for
+ * n complex numbers of precision prec at device address a; *result on host.
+ * Needs no context and allocates nothing: the reduction scratch is a static
+ * device array in the library (512 KiB per GPU that loads it, held until
+ * exit).  n <= 2^31, else DWF_EINVAL.  All calls on a device share that
+ * scratch: calls that overlap on the GPU race.  The first call on a device
+ * looks up the scratch address and should come before any stream capture.
+ * Synchronises `stream`. */
+int dwf_norm2_noalloc(double* result, const void* a, int64_t n, int prec, void* stream);
+
 /* ------------------------------------------------------------------ solvers */
 
 /* Red-black preconditioned CGNR (Sec. 5.1): solve D_DW x = b for a full
