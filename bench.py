@@ -197,7 +197,7 @@ def mg_vs_fp64(ctx, w, b, bd, tol):
     import torch
 
     from paper_2103_05034_gb300 import ops
-    from paper_2103_05034_gb300._lib import F64, SOLVE_F64, SUBSPACE_BATCH
+    from paper_2103_05034_gb300._lib import F32, F64, SOLVE_F64, SUBSPACE_BATCH
 
     L, Ls, mf = w["L"], w["Ls"], w["mf"]
     out = {}
@@ -219,11 +219,14 @@ def mg_vs_fp64(ctx, w, b, bd, tol):
     torch.cuda.synchronize()
     t_in = time.perf_counter() - t0  # host-side input generation, not counted
     t0 = time.perf_counter()
-    # lambda_max of D^dag D bounds the filter interval (power method, FP64, 5 % margin)
-    lmax = ops.dwf_power_max(ctx, v0, mf, 30) * 1.05
+    # lambda_max of D^dag D bounds the filter and smoother intervals (power
+    # method in FP32, 100 iterations, 10 % margin: the Rayleigh quotient
+    # approaches the top of the spectrum from below)
+    lmax = ops.dwf_power_max(ctx, v0, mf, 100, F32) * 1.10
     prm = ops.mg_params(p["block"], nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=p["lambda_lo"],
                         lambda_max=lmax, filter_order=p["filter_order"],
-                        smooth=p["smooth"], coarse_tol=p["coarse_tol"],
+                        smooth=(p["smooth"][0], max(p["smooth"][1], lmax), p["smooth"][2]),
+                        coarse_tol=p["coarse_tol"],
                         coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"], maxiter=p["maxiter"])
     G = ops.MG(ctx, prm, eta)
     torch.cuda.synchronize()

@@ -227,8 +227,10 @@ int dwf_force(dwf_ctx* ctx, void* force, const void* X, const double* mf, int np
               void* stream);
 
 /* Power method estimate of the largest eigenvalue of D_DW^dag D_DW (Sec. 3.4),
- * `iters` iterations from the FP64 full field v0 (device).  *lmax on host. */
-int dwf_power_max(dwf_ctx* ctx, double* lmax, const void* v0, double mf, int iters,
+ * `iters` iterations (v <- A v / |A v|, lambda = <v, A v>) from the FP64 full
+ * field v0 (device), arithmetic in precision prec (DWF_F64 or DWF_F32: the
+ * estimate only bounds a filter interval).  *lmax on host; synchronises. */
+int dwf_power_max(dwf_ctx* ctx, double* lmax, const void* v0, double mf, int iters, int prec,
                   void* stream);
 
 /* ------------------------------------------------------------------ subspace setup */

@@ -925,14 +925,15 @@ extern "C" int rbcg_normal_solve(dwf_ctx* c, void* x, const void* phi, double mf
 }
 
 // ------------------------------------------------------------------ power method
-extern "C" int dwf_power_max(dwf_ctx* c, double* lmax, const void* v0, double mf, int iters,
+extern "C" int dwf_power_max(dwf_ctx* c, double* lmax, const void* v0, double mf, int iters, int prec,
                              void* stream) {
   int rc = check_fields(c, DWF_F64, 1, {v0});
   if (rc) return rc;
   if (!lmax || iters < 1) return dwf_fail(c, DWF_EINVAL, "bad argument");
+  if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = 2 * half_elems(c);
-  const size_t bytes = n * 16;
+  const size_t bytes = n * dwf_complex_bytes(prec);
   void* v = dwf_workspace(c, WS_FULL, bytes);
   void* w = dwf_workspace(c, WS_B, bytes);
   void* t = dwf_workspace(c, WS_X, bytes);
@@ -944,27 +945,27 @@ extern "C" int dwf_power_max(dwf_ctx* c, double* lmax, const void* v0, double mf
   if (rc) return rc;
   double nv = sqrt(c->hscal[S_TMP0]);
   if (!(nv > 0)) return dwf_fail(c, DWF_EINVAL, "zero start vector");
-  rc = blas_axpby(c, 1.0 / nv, v0, DWF_F64, 0.0, v, DWF_F64, n, st);
+  rc = blas_axpby(c, 1.0 / nv, v0, DWF_F64, 0.0, v, prec, n, st);
   if (rc) return rc;
   double lam = 0;
-  for (int k = 0; k < iters; k++) {
-    rc = ddw_apply(c, t, v, mfa, 0, 0, DWF_F64, 1, st);
+  for (int k = 0; k < iters; k++) {  // v <- A v / |A v|, lambda = <v, A v>
+    rc = ddw_apply(c, t, v, mfa, 0, 0, prec, 1, st);
     if (rc) return rc;
-    rc = ddw_apply(c, w, t, mfa, 1, 0, DWF_F64, 1, st);
+    rc = ddw_apply(c, w, t, mfa, 1, 0, prec, 1, st);
     if (rc) return rc;
     int np = 0;
-    rc = blas_cdot_partials(c, v, w, n, DWF_F64, st, &np);
+    rc = blas_cdot_partials(c, v, w, n, prec, st, &np);
     if (rc) return rc;
     rc = blas_finalize(c, np, 2, S_TMP0, st);
     if (rc) return rc;
-    rc = norm2_dev(c, w, n, DWF_F64, S_TMP2, st);
+    rc = norm2_dev(c, w, n, prec, S_TMP2, st);
     if (rc) return rc;
     rc = read_scalars(c, S_TMP0, 3, st);
     if (rc) return rc;
     lam = c->hscal[S_TMP0];
     const double nw = sqrt(c->hscal[S_TMP2]);
     if (!isfinite(nw) || !(nw > 0)) return dwf_fail(c, DWF_ENAN, "power method breakdown");
-    rc = blas_axpby(c, 1.0 / nw, w, DWF_F64, 0.0, v, DWF_F64, n, st);
+    rc = blas_axpby(c, 1.0 / nw, w, prec, 0.0, v, prec, n, st);
     if (rc) return rc;
   }
   DWF_CUDA(c, cudaStreamSynchronize(st));

@@ -125,6 +125,101 @@ __device__ __forceinline__ void hop_dir(cpx<R> (&acc)[12], const cpx<R> (&ps)[12
   }
 }
 
+// ---------------------------------------------------------------- packed FP32
+// sm_100+ executes fma/add on a pair of FP32 values held in one 64-bit
+// register (fma.rn.f32x2).  A complex number (re, im) is one such pair, so a
+// complex multiply-add takes two packed FMAs: (u_re, u_re)*(h_re, h_im) +
+// (-u_im, u_im)*(h_im, h_re).  Links are staged in shared memory already
+// broadcast as (re, re, -im, im).
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk2(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(f2p v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+  f2p d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2p swp2(f2p a) {
+  float x, y;
+  upk2(a, x, y);
+  return pk2(y, x);
+}
+
+// acc += (1 - sg gamma_mu) U psi with packed arithmetic; sgp = (sg, sg),
+// sgv = (-sg, sg) (multiplication by sg*i of a swapped pair).
+template <int MU>
+__device__ __forceinline__ void hop_dir_x2(f2p (&acc)[12], const f2p (&ps)[12], const float4* __restrict__ U,
+                                           f2p sgp, f2p sgv, f2p nsgp, f2p nsgv) {
+  f2p h0[3], h1[3], s0[3], s1[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const f2p p0 = ps[c], p1 = ps[3 + c], p2 = ps[6 + c], p3 = ps[9 + c];
+    if (MU == 0) {  // h0 = p0 + s i p3, h1 = p1 + s i p2
+      h0[c] = fma2(sgv, swp2(p3), p0);
+      h1[c] = fma2(sgv, swp2(p2), p1);
+    } else if (MU == 1) {  // h0 = p0 + s p3, h1 = p1 - s p2
+      h0[c] = fma2(sgp, p3, p0);
+      h1[c] = fma2(nsgp, p2, p1);
+    } else if (MU == 2) {  // h0 = p0 + s i p2, h1 = p1 - s i p3
+      h0[c] = fma2(sgv, swp2(p2), p0);
+      h1[c] = fma2(nsgv, swp2(p3), p1);
+    } else {  // h0 = p0 - s p2, h1 = p1 - s p3
+      h0[c] = fma2(nsgp, p2, p0);
+      h1[c] = fma2(nsgp, p3, p1);
+    }
+    s0[c] = swp2(h0[c]);
+    s1[c] = swp2(h1[c]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    f2p g0 = 0ull, g1 = 0ull;  // +0.0f pairs
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const float4 u = U[a * 3 + b];
+      const f2p ure = pk2(u.x, u.y), uim = pk2(u.z, u.w);
+      g0 = fma2(ure, h0[b], g0);
+      g0 = fma2(uim, s0[b], g0);
+      g1 = fma2(ure, h1[b], g1);
+      g1 = fma2(uim, s1[b], g1);
+    }
+    acc[a] = add2(acc[a], g0);
+    acc[3 + a] = add2(acc[3 + a], g1);
+    if (MU == 0) {  // lower: -s i g1, -s i g0
+      acc[6 + a] = fma2(nsgv, swp2(g1), acc[6 + a]);
+      acc[9 + a] = fma2(nsgv, swp2(g0), acc[9 + a]);
+    } else if (MU == 1) {  // -s g1, s g0
+      acc[6 + a] = fma2(nsgp, g1, acc[6 + a]);
+      acc[9 + a] = fma2(sgp, g0, acc[9 + a]);
+    } else if (MU == 2) {  // -s i g0, s i g1
+      acc[6 + a] = fma2(nsgv, swp2(g0), acc[6 + a]);
+      acc[9 + a] = fma2(sgv, swp2(g1), acc[9 + a]);
+    } else {  // -s g0, -s g1
+      acc[6 + a] = fma2(nsgp, g0, acc[6 + a]);
+      acc[9 + a] = fma2(nsgp, g1, acc[9 + a]);
+    }
+  }
+}
+
+template <int P, int LS>
+__device__ __forceinline__ void load_spinor_x2(f2p (&ps)[12], const typename Prec<P>::S* __restrict__ base) {
+#pragma unroll
+  for (int c = 0; c < 12; c++) {
+    const auto z = ld_c(base + c * LS);
+    ps[c] = pk2((float)z.re, (float)z.im);
+  }
+}
+
 template <int P, int LS>
 __device__ __forceinline__ void load_spinor(cpx<typename Prec<P>::R> (&ps)[12],
                                             const typename Prec<P>::S* __restrict__ base, int s) {
@@ -200,7 +295,8 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
   typedef typename Prec<P>::R R;
   typedef typename Prec<P>::LS LT;
   constexpr int NT = LS * SB;
-  __shared__ cpx<R> sU[SB * 72];
+  // PF == 2 (packed FP32 arithmetic) keeps each link element as (re, re, -im, im)
+  __shared__ __align__(16) cpx<R> sU[SB * 72 * (PF == 2 ? 2 : 1)];
   __shared__ cpx<R> stage[SB * 12 * (LS + 1)];
   __shared__ double red[NT / 32 + 1];
 
@@ -217,7 +313,11 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
     const int n = min(SB, p.Vh - site0) * 72;
     for (int i = tid; i < n; i += NT) {
       const LT v = gl[i];
-      sU[i] = cmake<R>((R)v.x, (R)v.y);
+      if constexpr (PF == 2) {
+        ((float4*)sU)[i] = make_float4((float)v.x, (float)v.x, -(float)v.y, (float)v.y);
+      } else {
+        sU[i] = cmake<R>((R)v.x, (R)v.y);
+      }
     }
   }
   __syncthreads();
@@ -258,7 +358,36 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
       }
       return in + (size_t)cbi(X, Y, Z, T) * (12 * LS);
     };
-    if (PF) {
+    if constexpr (PF == 2) {
+      const float4* U4 = (const float4*)sU + sl * 72;
+      const float sgf = (float)p.sg;
+      const f2p sgp = pk2(sgf, sgf), nsgp = pk2(-sgf, -sgf), sgv = pk2(-sgf, sgf), nsgv = pk2(sgf, -sgf);
+      f2p acc[12], pq[12];
+#pragma unroll
+      for (int c = 0; c < 12; c++) acc[c] = 0ull;
+      load_spinor_x2<P, LS>(pq, nbp(0));
+      hop_dir_x2<0>(acc, pq, U4 + 0 * 9, sgp, sgv, nsgp, nsgv);
+      load_spinor_x2<P, LS>(pq, nbp(1));
+      hop_dir_x2<0>(acc, pq, U4 + 1 * 9, nsgp, nsgv, sgp, sgv);
+      load_spinor_x2<P, LS>(pq, nbp(2));
+      hop_dir_x2<1>(acc, pq, U4 + 2 * 9, sgp, sgv, nsgp, nsgv);
+      load_spinor_x2<P, LS>(pq, nbp(3));
+      hop_dir_x2<1>(acc, pq, U4 + 3 * 9, nsgp, nsgv, sgp, sgv);
+      load_spinor_x2<P, LS>(pq, nbp(4));
+      hop_dir_x2<2>(acc, pq, U4 + 4 * 9, sgp, sgv, nsgp, nsgv);
+      load_spinor_x2<P, LS>(pq, nbp(5));
+      hop_dir_x2<2>(acc, pq, U4 + 5 * 9, nsgp, nsgv, sgp, sgv);
+      load_spinor_x2<P, LS>(pq, nbp(6));
+      hop_dir_x2<3>(acc, pq, U4 + 6 * 9, sgp, sgv, nsgp, nsgv);
+      load_spinor_x2<P, LS>(pq, nbp(7));
+      hop_dir_x2<3>(acc, pq, U4 + 7 * 9, nsgp, nsgv, sgp, sgv);
+#pragma unroll
+      for (int c = 0; c < 12; c++) {
+        float a, b;
+        upk2(acc[c], a, b);
+        v[c] = cmake<R>((R)a, (R)b);
+      }
+    } else if (PF) {
       // register double buffer: the loads of neighbour d+1 are in flight while
       // neighbour d is projected and multiplied
       cpx<R> pa[12], pb[12];
@@ -461,11 +590,12 @@ struct HopShape {
 // Tuning variants of the hopping kernel: (register cap, prefetch).  Variant 0
 // is the uncapped kernel; the autotuner (dwf_autotune) times the rest on the
 // context's lattice and keeps the fastest per precision.
-#define DWF_HOP_VARIANTS 6
+#define DWF_HOP_VARIANTS 8
 __host__ __device__ constexpr int hop_variant_regs(int v) {
-  return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : 96;
+  return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : v == 5 ? 96 : v == 6 ? 64 : 80;
 }
-__host__ __device__ constexpr int hop_variant_pf(int v) { return v >= 4 ? 1 : 0; }
+// 0: scalar, 1: scalar with neighbour prefetch, 2: packed FP32 (fma.rn.f32x2)
+__host__ __device__ constexpr int hop_variant_pf(int v) { return v >= 6 ? 2 : v >= 4 ? 1 : 0; }
 
 template <int P, int LSV, int V>
 inline void launch_hop_v(const HopParams& hp, dim3 grid, cudaStream_t st) {
@@ -485,6 +615,8 @@ inline int launch_hop_ls(const HopParams& hp, dim3 grid, int variant, cudaStream
       case 3: launch_hop_v<P, LSV, 3>(hp, grid, st); break;
       case 4: launch_hop_v<P, LSV, 4>(hp, grid, st); break;
       case 5: launch_hop_v<P, LSV, 5>(hp, grid, st); break;
+      case 6: launch_hop_v<P, LSV, 6>(hp, grid, st); break;
+      case 7: launch_hop_v<P, LSV, 7>(hp, grid, st); break;
       default: launch_hop_v<P, LSV, 0>(hp, grid, st); break;
     }
   }

@@ -155,9 +155,9 @@ def rbcg_solve(ctx, x, b, mf, tol, maxiter=100000, policy=_lib.SOLVE_MIXED_F32):
     return st.as_dict()
 
 
-def dwf_power_max(ctx, v0, mf, iters):
+def dwf_power_max(ctx, v0, mf, iters, prec=F64):
     r = C.c_double()
-    check(lib().dwf_power_max(ctx.h, C.byref(r), _ptr(v0), mf, iters, _stream()), ctx.h)
+    check(lib().dwf_power_max(ctx.h, C.byref(r), _ptr(v0), mf, iters, prec, _stream()), ctx.h)
     return r.value
 
 

@@ -196,3 +196,30 @@ def test_power_method(case):
     got = ops.dwf_power_max(ctx, full_dev(v0, L, F64), mf, 30)
     want = krylov.power_max(lambda v: dwf.mdagm(U, v, M5, mf), v0, 30)
     assert got == pytest.approx(want, rel=1e-10)
+
+
+@pytest.mark.parametrize("prec", [F32, F16S])
+@pytest.mark.parametrize("variant", range(8))
+def test_every_hop_variant_matches_oracle(prec, variant):
+    """Each tuning variant of the hopping kernel (register caps, prefetch,
+    packed FP32 arithmetic) reproduces the oracle, plain and with the fused
+    M_ee / M_ee^-1 epilogues of M_pc."""
+    from paper_2103_05034_gb300 import layout
+    for L, Ls in (((4, 4, 2, 2), 16), ((2, 4, 2, 2), 24)):
+        U = synth.random_gauge(L, 0.5, 8)
+        ctx = ops.Context(L, Ls, M5, U)
+        ops.dwf_set_hop_variant(ctx, prec, variant)
+        psi = synth.gaussian_spinor(L, Ls, 31)
+        for dagger in (0, 1):
+            inp = half_dev(psi, L, 1, prec)
+            out = torch.zeros_like(inp)
+            ops.dwf_dhop(ctx, out, inp, 0, dagger)
+            want = layout.to_half(dwf.dhop(U, dwf.project_parity(psi, L, 1), dag=bool(dagger)), L, 0)
+            assert rel(dev_to_half(out, Ls), want) < TOL[prec]
+        if prec == F32:
+            pe = dwf.project_parity(psi, L, 0)
+            inp = half_dev(psi, L, 0, prec)
+            out = torch.zeros_like(inp)
+            ops.dwf_mpc(ctx, out, inp, 0.05, 1)
+            assert rel(dev_to_half(out, Ls), layout.to_half(dwf.mpc_dag(U, pe, M5, 0.05), L, 0)) < TOL[prec]
+        ctx.close()
