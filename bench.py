@@ -126,10 +126,15 @@ def profile_traffic(kernel_key, shash):
 
 
 def build_workload(name, rank):
+    """Links and (for host-sized lattices) the Gaussian source of a workload.
+    Paper-size lattices (over 2^30 5D sites' worth of host memory) get no host
+    source: their inputs are drawn on the device."""
     w = synth.WORKLOADS[name]
     L, Ls = w["L"], w["Ls"]
-    U = synth.random_gauge(L, w["eps"], synth.SEED_GAUGE, ape_steps=w["ape"])
-    b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE + rank)
+    U = synth.workload_gauge(name)
+    b = None
+    if int(np.prod(L)) * Ls <= (1 << 27):
+        b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE + rank)
     return w, U, b
 
 
@@ -418,10 +423,38 @@ def run_kernel(args):
     kind, prec_name = args.kernel.split("_")
     prec = {"f64": F64, "f32": F32, "f16": F16S}[prec_name]
     variant, tuned_ms = ops.dwf_autotune(ctx, prec, 10)
-    inp = torch.from_numpy(layout.complex_to_real(layout.to_half(b, L, 1), prec)).cuda()
+    if b is not None:
+        inp = torch.from_numpy(layout.complex_to_real(layout.to_half(b, L, 1), prec)).cuda()
+    else:  # paper-size lattice: Gaussian input drawn on the device (seeded)
+        gen = torch.Generator(device="cuda").manual_seed(synth.SEED_SOURCE)
+        inp = torch.randn(ctx.half_numel(), generator=gen, device="cuda",
+                          dtype=torch.float32).to({F64: torch.float64, F32: torch.float32,
+                                                   F16S: torch.float16}[prec])
     out = torch.zeros_like(inp)
     fn = {"dhop": lambda: ops.dwf_dhop(ctx, out, inp, 0),
           "mpcdagmpc": lambda: ops.dwf_mpcdag_mpc(ctx, out, inp, w["mf"])}[kind]
+    if args.sweep_variants and kind == "dhop":
+        # every tuning variant, one launch at a time with an L2 flush before each
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        wbytes = {F64: 16, F32: 8, F16S: 4}[prec]
+        nbytes = ctx.Vh * (Ls * 24 * wbytes + 72 * (16 if prec == F64 else 8))
+        for v in range(10 if prec != F64 else 1):
+            ops.dwf_set_hop_variant(ctx, prec, v)
+            for _ in range(3):
+                fn()
+            ts = []
+            for k in range(10):
+                flush.fill_(float(k))
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                z.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(z))
+            ms = float(np.median(ts))
+            print(json.dumps({"kernel": args.kernel, "variant": v, "ms_median": ms,
+                              "GBs_algorithmic": nbytes / ms / 1e6}))
+        ops.dwf_set_hop_variant(ctx, prec, variant)
     for _ in range(args.warmup):
         fn()
     torch.cuda.synchronize()
@@ -451,6 +484,8 @@ def main(argv=None):
                     help="skip the one-off FP64 RB-CG vs HDCR time-to-solution comparison")
     ap.add_argument("--kernel", default=None,
                     help="profile mode: dhop_f32, dhop_f64, dhop_f16 or mpcdagmpc_f32 alone")
+    ap.add_argument("--sweep-variants", action="store_true",
+                    help="with --kernel dhop_*: time every hopping-kernel tuning variant")
     args = ap.parse_args(argv)
     if args.kernel:
         return run_kernel(args)

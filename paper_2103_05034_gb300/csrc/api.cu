@@ -217,6 +217,19 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
   hp.L3 = c->g.L[3];
   hp.Lxh = c->g.Lxh;
   hp.Vh = (int)c->g.Vh;
+  {
+    // z-chunk: the largest even divisor of Lz whose input slab (zc planes of
+    // one time slice, over the t-1, t, t+1 slices plus the output) stays
+    // within ~48 MB of L2; the whole Lz (lexicographic order) when it fits.
+    const double plane = (double)c->g.L[1] * c->g.Lxh * c->g.Ls * h.nrhs * 12.0 * dwf_complex_bytes(prec);
+    int zc = c->g.L[2];
+    if (4.0 * plane * zc > 48e6) {
+      zc = 2;
+      for (int q = 2; q <= c->g.L[2]; q += 2)
+        if (c->g.L[2] % q == 0 && 4.0 * plane * q <= 48e6) zc = q;
+    }
+    hp.zc = zc;
+  }
   hp.out_parity = po;
   hp.sg = h.dagger ? -1.f : 1.f;
   hp.alpha = h.alpha;

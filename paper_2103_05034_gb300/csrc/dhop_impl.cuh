@@ -37,6 +37,7 @@ struct HopParams {
   double* partials;
   int L0, L1, L2, L3, Lxh;
   int Vh;
+  int zc;  // traversal z-chunk (even divisor of L2; L2 = lexicographic order)
   int out_parity;
   float sg;  // +1: D_hop, -1: D_hop^dag
   double alpha;
@@ -303,16 +304,71 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
   const int tid = threadIdx.x;
   const int sl = tid / LS;
   const int s = tid - sl * LS;
-  const int site0 = blockIdx.x * SB;
+  // Traversal order: CTAs walk z-chunks of zc planes outermost and t inside
+  // them, so the t +- 1 neighbour slices of the chunk stay resident in L2 on
+  // lattices whose full time slice does not fit (zc = L2 is the plain
+  // lexicographic order).
+  const int zc = p.zc;
+  int site0;
+  if (!(PF == 3) && zc < p.L2 && (p.Lxh % SB) == 0) {
+    const int nseg = p.Lxh / SB;
+    int r = blockIdx.x;
+    const int seg = r % nseg;
+    r /= nseg;
+    const int yy = r % p.L1;
+    r /= p.L1;
+    const int zl = r % zc;
+    r /= zc;
+    const int tt = r % p.L3;
+    const int zz = (r / p.L3) * zc + zl;
+    site0 = ((tt * p.L2 + zz) * p.L1 + yy) * p.Lxh + seg * SB;
+  } else {
+    site0 = blockIdx.x * SB;
+  }
   const int rhs = blockIdx.y;
-  const int site = site0 + sl;
+  // PF == 3: the CTA handles the 8 output-parity sites of one 2^4 hypercube
+  // (SB = 8), so half of every site's neighbours are the hypercube's other 8
+  // sites, shared through L1 by the CTA.  Otherwise SB consecutive sites.
+  constexpr bool TILE = (PF == 3);
+  auto tile_coords = [&](int l, int& X, int& Y, int& Z, int& T) {
+    // corners (dx dy dz dt as bits 3..0) of each parity, in a fixed order
+    const int even_c[8] = {0x0, 0xC, 0xA, 0x9, 0x6, 0x5, 0x3, 0xF};
+    const int odd_c[8] = {0x8, 0x4, 0x2, 0x1, 0xE, 0xD, 0xB, 0x7};
+    const int code = p.out_parity ? odd_c[l] : even_c[l];
+    const int hx = p.L0 >> 1, hy = p.L1 >> 1, hz = p.L2 >> 1, ht = p.L3 >> 1, zc2 = p.zc >> 1;
+    int r = blockIdx.x;
+    const int cx = r % hx;
+    r /= hx;
+    const int cy = r % hy;
+    r /= hy;
+    int cz, ct;
+    if (zc2 > 0 && zc2 < hz) {  // z-chunked hypercube order
+      const int czl = r % zc2;
+      r /= zc2;
+      ct = r % ht;
+      cz = (r / ht) * zc2 + czl;
+    } else {
+      cz = r % hz;
+      ct = r / hz;
+    }
+    X = 2 * cx + ((code >> 3) & 1);
+    Y = 2 * cy + ((code >> 2) & 1);
+    Z = 2 * cz + ((code >> 1) & 1);
+    T = 2 * ct + (code & 1);
+  };
+  auto tile_site = [&](int l) {
+    int X, Y, Z, T;
+    tile_coords(l, X, Y, Z, T);
+    return ((T * p.L2 + Z) * p.L1 + Y) * p.Lxh + (X >> 1);
+  };
+  const int site = TILE ? tile_site(sl) : site0 + sl;
   const bool active = site < p.Vh;
 
   {
     const LT* gl = (const LT*)p.links + (size_t)site0 * 72;
-    const int n = min(SB, p.Vh - site0) * 72;
+    const int n = TILE ? SB * 72 : min(SB, p.Vh - site0) * 72;
     for (int i = tid; i < n; i += NT) {
-      const LT v = gl[i];
+      const LT v = TILE ? ((const LT*)p.links)[(size_t)tile_site(i / 72) * 72 + (i % 72)] : gl[i];
       if constexpr (PF == 2) {
         ((float4*)sU)[i] = make_float4((float)v.x, (float)v.x, -(float)v.y, (float)v.y);
       } else {
@@ -327,13 +383,18 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
   for (int c = 0; c < 12; c++) v[c] = cmake<R>(0, 0);
 
   if (active) {
-    int rem = site / p.Lxh;
-    const int xh = site - rem * p.Lxh;
-    const int y = rem % p.L1;
-    rem /= p.L1;
-    const int z = rem % p.L2;
-    const int t = rem / p.L2;
-    const int x = 2 * xh + ((y + z + t + p.out_parity) & 1);
+    int x, y, z, t;
+    if (TILE) {
+      tile_coords(sl, x, y, z, t);
+    } else {
+      int rem = site / p.Lxh;
+      const int xh = site - rem * p.Lxh;
+      y = rem % p.L1;
+      rem /= p.L1;
+      z = rem % p.L2;
+      t = rem / p.L2;
+      x = 2 * xh + ((y + z + t + p.out_parity) & 1);
+    }
     const S* in = (const S*)p.in + (size_t)rhs * p.rhs_stride;
     const int Lxh = p.Lxh, L1 = p.L1, L2 = p.L2;
     auto cbi = [&](int X, int Y, int Z, int T) { return ((T * L2 + Z) * L1 + Y) * Lxh + (X >> 1); };
@@ -387,7 +448,7 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
         upk2(acc[c], a, b);
         v[c] = cmake<R>((R)a, (R)b);
       }
-    } else if (PF) {
+    } else if (PF == 1) {
       // register double buffer: the loads of neighbour d+1 are in flight while
       // neighbour d is projected and multiplied
       cpx<R> pa[12], pb[12];
@@ -590,12 +651,14 @@ struct HopShape {
 // Tuning variants of the hopping kernel: (register cap, prefetch).  Variant 0
 // is the uncapped kernel; the autotuner (dwf_autotune) times the rest on the
 // context's lattice and keeps the fastest per precision.
-#define DWF_HOP_VARIANTS 8
+#define DWF_HOP_VARIANTS 10
 __host__ __device__ constexpr int hop_variant_regs(int v) {
-  return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : v == 5 ? 96 : v == 6 ? 64 : 80;
+  return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : v == 5 ? 96 : v == 6 ? 64 : v == 7 ? 80
+         : v == 8 ? 64 : 80;
 }
-// 0: scalar, 1: scalar with neighbour prefetch, 2: packed FP32 (fma.rn.f32x2)
-__host__ __device__ constexpr int hop_variant_pf(int v) { return v >= 6 ? 2 : v >= 4 ? 1 : 0; }
+// 0: scalar, 1: scalar with neighbour prefetch, 2: packed FP32 (fma.rn.f32x2),
+// 3: scalar on 2^4-hypercube tiles (8 output sites per CTA)
+__host__ __device__ constexpr int hop_variant_pf(int v) { return v >= 8 ? 3 : v >= 6 ? 2 : v >= 4 ? 1 : 0; }
 
 template <int P, int LSV, int V>
 inline void launch_hop_v(const HopParams& hp, dim3 grid, cudaStream_t st) {
@@ -617,6 +680,8 @@ inline int launch_hop_ls(const HopParams& hp, dim3 grid, int variant, cudaStream
       case 5: launch_hop_v<P, LSV, 5>(hp, grid, st); break;
       case 6: launch_hop_v<P, LSV, 6>(hp, grid, st); break;
       case 7: launch_hop_v<P, LSV, 7>(hp, grid, st); break;
+      case 8: launch_hop_v<P, LSV, 8>(hp, grid, st); break;
+      case 9: launch_hop_v<P, LSV, 9>(hp, grid, st); break;
       default: launch_hop_v<P, LSV, 0>(hp, grid, st); break;
     }
   }

@@ -400,8 +400,14 @@ extern "C" int block_orthonormalise(dwf_ctx* c, void* basis, int nb, int nplus, 
     DWF_CUDA(c, cudaMemsetAsync(fail, 0, sizeof(int), st));
     c->launches++;
     dwfmg::k_block_cholinv<<<dim3(g.nc, 2), 32, 0, st>>>(G, Ri, nb, nplus, fail);
-    rc = block_combine(c, g, tmp, nb, DWF_F64, basis, nb, DWF_F64, Ri, (long long)nb * nb, nb, 0, st);
-    if (rc) return rc;
+    // R^-1 is block diagonal by chirality group: update each group separately
+    for (int grp = 0; grp < 2; grp++) {
+      const int g0 = grp ? nplus : 0, ng = grp ? nb - nplus : nplus;
+      if (ng <= 0) continue;
+      rc = block_combine(c, g, (double2*)tmp + (size_t)g0 * n, ng, DWF_F64, (const double2*)basis + (size_t)g0 * n,
+                         ng, DWF_F64, Ri + (size_t)g0 * nb + g0, (long long)nb * nb, nb, 0, st);
+      if (rc) return rc;
+    }
     DWF_CUDA(c, cudaMemcpyAsync(basis, tmp, (size_t)n * nb * 16, cudaMemcpyDeviceToDevice, st));
     int hfail = 0;
     DWF_CUDA(c, cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));

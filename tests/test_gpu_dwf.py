@@ -199,7 +199,7 @@ def test_power_method(case):
 
 
 @pytest.mark.parametrize("prec", [F32, F16S])
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(10))
 def test_every_hop_variant_matches_oracle(prec, variant):
     """Each tuning variant of the hopping kernel (register caps, prefetch,
     packed FP32 arithmetic) reproduces the oracle, plain and with the fused
