@@ -123,12 +123,18 @@ int dwf_counters(const dwf_ctx* ctx, int64_t* launches, double* hop_bytes);
 int dwf_reset_counters(dwf_ctx* ctx);
 
 /* Autotuner of the hopping kernel: times every tuning variant (register cap x
- * neighbour prefetch; 6 variants for FP32 and FP16 storage at Ls >= 16, one
- * otherwise) on this context's lattice, `reps` launches each, keeps the
- * fastest for precision `prec` and returns its time per launch in *best_ms
- * (may be NULL).  Uses context workspace; tuning launches are not counted.
- * Synchronises.  dwf_set_hop_variant / dwf_get_hop_variant pin or read the
- * choice (0 = untuned default). */
+ * inner-loop form: scalar, neighbour prefetch, packed FP32 on (re, im) pairs,
+ * 2^4 hypercube tiles, two s-slices per thread with packed FP32 over the
+ * pair, CTAs of 2 or 4 y-rows; DWF_HOP_VARIANTS variants for FP32 and FP16
+ * storage at Ls >= 16, one otherwise) on this context's lattice, `reps`
+ * launches each, keeps the fastest for precision `prec` and returns its time
+ * per launch in *best_ms (may be NULL).  Variants that do not tile the
+ * lattice are skipped.  Uses context workspace; tuning launches are not
+ * counted.  Synchronises.  dwf_set_hop_variant / dwf_get_hop_variant pin or
+ * read the choice (0 = untuned default; valid ids 0 .. DWF_HOP_VARIANTS-1;
+ * dwf_set_hop_variant returns DWF_EINVAL for a variant that does not tile
+ * the lattice). */
+#define DWF_HOP_VARIANTS 18
 int dwf_autotune(dwf_ctx* ctx, int prec, int reps, double* best_ms, void* stream);
 int dwf_set_hop_variant(dwf_ctx* ctx, int prec, int variant);
 int dwf_get_hop_variant(const dwf_ctx* ctx, int prec);

@@ -276,8 +276,18 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
 }
 
 // ------------------------------------------------------------------ autotuner
+// A variant whose CTAs cover several y-rows needs the x segment to divide
+// Lx/2 and the row count to divide Ly.
+static bool hop_variant_fits(const dwf_ctx* c, int prec, int v) {
+  if (prec == DWF_F64 || c->g.Ls < 16) return true;  // always the plain kernel
+  const int ry = dwfk::hop_variant_rows(v);
+  const int sb = c->g.Ls >= 16 ? 8 : 128 / c->g.Ls;
+  return ry == 1 || (c->g.Lxh % sb == 0 && c->g.L[1] % ry == 0);
+}
+
 extern "C" int dwf_set_hop_variant(dwf_ctx* c, int prec, int variant) {
   if (!c || prec < DWF_F64 || prec > DWF_F16S || variant < 0 || variant >= DWF_HOP_VARIANTS) return DWF_EINVAL;
+  if (!hop_variant_fits(c, prec, variant)) return dwf_fail(c, DWF_EINVAL, "hop variant does not tile the lattice");
   c->hop_variant[prec] = variant;
   return DWF_OK;
 }
@@ -304,6 +314,7 @@ extern "C" int dwf_autotune(dwf_ctx* c, int prec, int reps, double* best_ms, voi
   const int64_t launches0 = c->launches;
   const double bytes0 = c->hop_bytes;
   for (int v = 0; v < nv; v++) {
+    if (!hop_variant_fits(c, prec, v)) continue;
     c->hop_variant[prec] = v;
     HopLaunch h;
     memset(&h, 0, sizeof(h));

@@ -283,6 +283,8 @@ __device__ __forceinline__ void minv_row_inplace(cpx<R>* row, bool fwd, R d, R m
   }
 }
 
+extern __shared__ __align__(16) unsigned char hop_dyn_smem[];
+
 // Register cap: REGS registers per thread give at least 65536/(LS*SB*REGS)
 // resident CTAs per SM (REGS = 0: no cap).  PF: prefetch the next neighbour.
 template <int LS, int SB, int REGS>
@@ -290,15 +292,22 @@ struct HopMinBlocks {
   static constexpr int v = REGS == 0 ? 1 : (65536 / (LS * SB * REGS) > 0 ? 65536 / (LS * SB * REGS) : 1);
 };
 
-template <int P, int LS, int SB, int REGS, int PF>
-__global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_kernel(const HopParams p) {
+// RY > 1: the CTA covers RY consecutive y-rows of SB sites each (same x
+// segment), so a row's +-y neighbours and the next row's +-x neighbours are
+// the same input sites and are shared through L1.
+template <int P, int LS, int SB, int REGS, int PF, int RY = 1>
+__global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::v)) hop_kernel(const HopParams p) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::R R;
   typedef typename Prec<P>::LS LT;
-  constexpr int NT = LS * SB;
+  constexpr int SBC = SB * RY;  // sites per CTA
+  constexpr int NT = LS * SBC;
   // PF == 2 (packed FP32 arithmetic) keeps each link element as (re, re, -im, im)
-  __shared__ __align__(16) cpx<R> sU[SB * 72 * (PF == 2 ? 2 : 1)];
-  __shared__ cpx<R> stage[SB * 12 * (LS + 1)];
+  // dynamic shared memory: the links during the hop, then (inv_mode only)
+  // the M_ee^-1 stage in the same bytes; the launcher sizes it per launch so
+  // that plain hops leave most of the SM's L1 to the neighbour re-reads
+  cpx<R>* sU = (cpx<R>*)hop_dyn_smem;
+  cpx<R>* stage = (cpx<R>*)hop_dyn_smem;
   __shared__ double red[NT / 32 + 1];
 
   const int tid = threadIdx.x;
@@ -310,13 +319,15 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
   // lexicographic order).
   const int zc = p.zc;
   int site0;
-  if (!(PF == 3) && zc < p.L2 && (p.Lxh % SB) == 0) {
+  if (RY > 1 || (!(PF == 3) && zc < p.L2 && (p.Lxh % SB) == 0)) {
+    // (RY > 1 needs SB | Lxh and RY | L1; the host launches it only then)
     const int nseg = p.Lxh / SB;
+    const int ny = p.L1 / RY;
     int r = blockIdx.x;
     const int seg = r % nseg;
     r /= nseg;
-    const int yy = r % p.L1;
-    r /= p.L1;
+    const int yy = (r % ny) * RY;
+    r /= ny;
     const int zl = r % zc;
     r /= zc;
     const int tt = r % p.L3;
@@ -325,6 +336,8 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
   } else {
     site0 = blockIdx.x * SB;
   }
+  // site of the l-th CTA slot (rows of SB sites, Lxh apart)
+  auto row_site = [&](int l) { return RY > 1 ? site0 + (l / SB) * p.Lxh + (l % SB) : site0 + l; };
   const int rhs = blockIdx.y;
   // PF == 3: the CTA handles the 8 output-parity sites of one 2^4 hypercube
   // (SB = 8), so half of every site's neighbours are the hypercube's other 8
@@ -361,14 +374,16 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
     tile_coords(l, X, Y, Z, T);
     return ((T * p.L2 + Z) * p.L1 + Y) * p.Lxh + (X >> 1);
   };
-  const int site = TILE ? tile_site(sl) : site0 + sl;
+  const int site = TILE ? tile_site(sl) : row_site(sl);
   const bool active = site < p.Vh;
 
   {
     const LT* gl = (const LT*)p.links + (size_t)site0 * 72;
-    const int n = TILE ? SB * 72 : min(SB, p.Vh - site0) * 72;
+    const int n = (TILE || RY > 1) ? SBC * 72 : min(SB, p.Vh - site0) * 72;
     for (int i = tid; i < n; i += NT) {
-      const LT v = TILE ? ((const LT*)p.links)[(size_t)tile_site(i / 72) * 72 + (i % 72)] : gl[i];
+      const LT v = TILE     ? ((const LT*)p.links)[(size_t)tile_site(i / 72) * 72 + (i % 72)]
+                   : RY > 1 ? ((const LT*)p.links)[(size_t)row_site(i / 72) * 72 + (i % 72)]
+                            : gl[i];
       if constexpr (PF == 2) {
         ((float4*)sU)[i] = make_float4((float)v.x, (float)v.x, -(float)v.y, (float)v.y);
       } else {
@@ -521,14 +536,15 @@ __global__ void __launch_bounds__(LS* SB, (HopMinBlocks<LS, SB, REGS>::v)) hop_k
   }
 
   if (p.inv_mode) {
+    __syncthreads();  // every thread is done with the links
     if (active) {
 #pragma unroll
       for (int c = 0; c < 12; c++) stage[(sl * 12 + c) * (LS + 1) + s] = v[c];
     }
     __syncthreads();
-    for (int w = tid; w < SB * 12; w += NT) {
+    for (int w = tid; w < SBC * 12; w += NT) {
       const int sl2 = w / 12, c2 = w - sl2 * 12;
-      if (site0 + sl2 < p.Vh) {
+      if ((TILE || RY > 1) || site0 + sl2 < p.Vh) {
         const bool fwd = (c2 < 6) != (p.inv_mode == 2);
         minv_row_inplace<R, LS>(stage + (sl2 * 12 + c2) * (LS + 1), fwd, (R)p.d, (R)p.m[rhs],
                         (R)p.kappa[rhs], (R)p.dls1[rhs]);
@@ -643,6 +659,12 @@ __global__ void __launch_bounds__(128) mooee_kernel(typename Prec<P>::S* out,
   for (int q = 0; q < LS; q++) st_c(out + off + q, row[q]);
 }
 
+}  // namespace dwfk
+
+#include "dhop_pair.cuh"
+
+namespace dwfk {
+
 template <int LS>
 struct HopShape {
   static constexpr int SB = (LS >= 16) ? 8 : (128 / LS);
@@ -651,19 +673,49 @@ struct HopShape {
 // Tuning variants of the hopping kernel: (register cap, prefetch).  Variant 0
 // is the uncapped kernel; the autotuner (dwf_autotune) times the rest on the
 // context's lattice and keeps the fastest per precision.
-#define DWF_HOP_VARIANTS 10
+static_assert(DWF_HOP_VARIANTS == 18, "variant table below");
 __host__ __device__ constexpr int hop_variant_regs(int v) {
   return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : v == 5 ? 96 : v == 6 ? 64 : v == 7 ? 80
-         : v == 8 ? 64 : 80;
+         : v == 8 ? 64 : v == 9 ? 80 : v == 10 ? 128 : v == 11 ? 112 : v == 12 ? 96 : v == 13 ? 0
+         : v == 14 ? 64 : v == 15 ? 80 : v == 16 ? 64 : 80;
 }
-// 0: scalar, 1: scalar with neighbour prefetch, 2: packed FP32 (fma.rn.f32x2),
-// 3: scalar on 2^4-hypercube tiles (8 output sites per CTA)
-__host__ __device__ constexpr int hop_variant_pf(int v) { return v >= 8 ? 3 : v >= 6 ? 2 : v >= 4 ? 1 : 0; }
+// rows of sites per CTA (variants 14-17: scalar kernel on 2 or 4 y-rows)
+__host__ __device__ constexpr int hop_variant_rows(int v) { return v >= 16 ? 4 : v >= 14 ? 2 : 1; }
+// 0: scalar, 1: scalar with neighbour prefetch, 2: packed FP32 (fma.rn.f32x2)
+// on (re, im) pairs, 3: scalar on 2^4-hypercube tiles (8 output sites per
+// CTA), 4: two s-slices per thread, packed FP32 over the s-pair
+// (hop_kernel_pair)
+__host__ __device__ constexpr int hop_variant_pf(int v) {
+  return v >= 14 ? 0 : v >= 10 ? 4 : v >= 8 ? 3 : v >= 6 ? 2 : v >= 4 ? 1 : 0;
+}
+
+// Dynamic shared memory of one launch: links (SBC*72 complex, twice for the
+// (re,re,-im,im) packed form), or the M_ee^-1 stage (SBC*12*(LS+1) complex)
+// when the epilogue inverts; opted in above 48 KB once per instantiation.
+template <auto Kern>
+inline void hop_launch_smem(dim3 grid, int threads, size_t bytes, const HopParams& hp, cudaStream_t st) {
+  static size_t opted = 48 * 1024;  // one per kernel instantiation
+  if (bytes > opted) {
+    cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    opted = bytes;
+  }
+  Kern<<<grid, threads, bytes, st>>>(hp);
+}
 
 template <int P, int LSV, int V>
 inline void launch_hop_v(const HopParams& hp, dim3 grid, cudaStream_t st) {
   constexpr int SB = HopShape<LSV>::SB;
-  hop_kernel<P, LSV, SB, hop_variant_regs(V), hop_variant_pf(V)><<<grid, LSV * SB, 0, st>>>(hp);
+  constexpr int PF = hop_variant_pf(V);
+  constexpr int RY = PF == 4 ? 1 : hop_variant_rows(V);
+  constexpr size_t cb = sizeof(cpx<typename Prec<P>::R>);
+  const size_t ub = (size_t)SB * RY * 72 * cb * (PF == 2 || PF == 4 ? 2 : 1);
+  const size_t sb = hp.inv_mode ? (size_t)SB * RY * 12 * (LSV + 1) * cb : 0;
+  const size_t bytes = ub > sb ? ub : sb;
+  if constexpr (PF == 4) {
+    hop_launch_smem<hop_kernel_pair<P, LSV, SB, hop_variant_regs(V)>>(grid, LSV / 2 * SB, bytes, hp, st);
+  } else {
+    hop_launch_smem<hop_kernel<P, LSV, SB, hop_variant_regs(V), PF, RY>>(grid, LSV * SB * RY, bytes, hp, st);
+  }
 }
 
 template <int P, int LSV>
@@ -682,6 +734,14 @@ inline int launch_hop_ls(const HopParams& hp, dim3 grid, int variant, cudaStream
       case 7: launch_hop_v<P, LSV, 7>(hp, grid, st); break;
       case 8: launch_hop_v<P, LSV, 8>(hp, grid, st); break;
       case 9: launch_hop_v<P, LSV, 9>(hp, grid, st); break;
+      case 10: launch_hop_v<P, LSV, 10>(hp, grid, st); break;
+      case 11: launch_hop_v<P, LSV, 11>(hp, grid, st); break;
+      case 12: launch_hop_v<P, LSV, 12>(hp, grid, st); break;
+      case 13: launch_hop_v<P, LSV, 13>(hp, grid, st); break;
+      case 14: launch_hop_v<P, LSV, 14>(hp, grid, st); break;
+      case 15: launch_hop_v<P, LSV, 15>(hp, grid, st); break;
+      case 16: launch_hop_v<P, LSV, 16>(hp, grid, st); break;
+      case 17: launch_hop_v<P, LSV, 17>(hp, grid, st); break;
       default: launch_hop_v<P, LSV, 0>(hp, grid, st); break;
     }
   }
@@ -696,7 +756,9 @@ int launch_hop_prec(const HopParams& hp, int Ls, int nrhs, int variant, cudaStre
 #define DWF_HOP_CASE(LSV)                                                        \
   case LSV: {                                                                    \
     constexpr int SB = HopShape<LSV>::SB;                                        \
-    grid.x = (hp.Vh + SB - 1) / SB;                                              \
+    const int ry = (P == DWF_F64 || LSV < 16) ? 1 : hop_variant_rows(variant);   \
+    if (ry > 1 && (hp.Lxh % SB || hp.L1 % ry)) return DWF_EINVAL;                \
+    grid.x = (hp.Vh + SB * ry - 1) / (SB * ry);                                  \
     if (nblocks) *nblocks = grid.x * grid.y;                                     \
     return launch_hop_ls<P, LSV>(hp, grid, variant, st);                         \
   }

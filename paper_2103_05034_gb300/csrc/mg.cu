@@ -27,6 +27,9 @@ struct dwf_coarse {
 
 int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, int nb, int nc,
                     const int Lc[4], int nrhs, int* err_dev, cudaStream_t st);
+int coarse_cg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float2* A, const int Lc[4], int nc,
+                         int nb, double tol, int maxiter, float2* work, double* part, int part_cap,
+                         int* dev_small, int* iters, cudaStream_t st);
 
 struct dwf_mg {
   dwf_ctx* ctx;
@@ -244,59 +247,18 @@ int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cud
 }
 
 // CG on A^2 e = A r (one right-hand side, FP32 vectors), stopping when the
-// normal-equation residual falls below tol times its initial value.  The
-// scalars live in dscal slots base+S_*.
+// normal-equation residual falls below tol times its initial value: one
+// persistent cooperative launch (coarse_cg.cu).
 int coarse_cg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxiter, int* iters, cudaStream_t st) {
-  dwf_ctx* c = C->ctx;
   const int64_t n = (int64_t)C->g.nc * C->nb;
-  const size_t bytes = n * sizeof(float2);
-  void *b, *r, *p, *t, *Ap;
+  const int part_cap = 3 * 4096;
+  void *work, *part, *small;
   int rc2;
-  if ((rc2 = coarse_ws(C, 0, bytes, &b)) || (rc2 = coarse_ws(C, 1, bytes, &r)) || (rc2 = coarse_ws(C, 2, bytes, &p)) ||
-      (rc2 = coarse_ws(C, 3, bytes, &t)) || (rc2 = coarse_ws(C, 4, bytes, &Ap)))
+  if ((rc2 = coarse_ws(C, 0, 4 * n * sizeof(float2), &work)) || (rc2 = coarse_ws(C, 1, part_cap * sizeof(double), &part)) ||
+      (rc2 = coarse_ws(C, 2, 4 * sizeof(int), &small)))
     return rc2;
-  const int base = 16;
-  int rcd = coarse_apply_dev(C, (float2*)b, rc, 1, st);
-  if (rcd) return rcd;
-  DWF_CUDA(c, cudaMemsetAsync(e, 0, bytes, st));
-  rcd = blas_copy(c, r, DWF_F32, b, DWF_F32, n, st);
-  if (rcd) return rcd;
-  rcd = blas_copy(c, p, DWF_F32, b, DWF_F32, n, st);
-  if (rcd) return rcd;
-  rcd = norm2_dev(c, b, n, DWF_F32, base + S_RR, st);
-  if (rcd) return rcd;
-  rcd = read_scalars(c, base + S_RR, 1, st);
-  if (rcd) return rcd;
-  const double bb = c->hscal[base + S_RR];
-  *iters = 0;
-  if (!(bb > 0)) return isfinite(bb) ? DWF_OK : dwf_fail(c, DWF_ENAN, "NaN in coarse solve");
-  const int check = 4;
-  for (int it = 1; it <= maxiter; it++) {
-    rcd = coarse_apply_dev(C, (float2*)t, (const float2*)p, 1, st);
-    if (rcd) return rcd;
-    int np = 0;
-    rcd = blas_norm2_partials(c, t, n, DWF_F32, st, &np);  // <p, A^2 p> = |A p|^2
-    if (rcd) return rcd;
-    rcd = blas_finalize_mode(c, np, 1, base + S_PAP, 1, st, base);
-    if (rcd) return rcd;
-    rcd = coarse_apply_dev(C, (float2*)Ap, (const float2*)t, 1, st);
-    if (rcd) return rcd;
-    rcd = blas_cg_xr(c, e, r, p, Ap, n, DWF_F32, base + S_ALPHA, st, &np);
-    if (rcd) return rcd;
-    rcd = blas_finalize_mode(c, np, 1, base + S_RRNEW, 2, st, base);
-    if (rcd) return rcd;
-    rcd = blas_cg_p(c, p, r, n, DWF_F32, base + S_BETA, st);
-    if (rcd) return rcd;
-    *iters = it;
-    if (it % check == 0 || it == maxiter) {
-      rcd = read_scalars(c, base + S_RR, 1, st);
-      if (rcd) return rcd;
-      const double rr = c->hscal[base + S_RR];
-      if (!isfinite(rr)) return dwf_fail(c, DWF_ENAN, "NaN in coarse solve");
-      if (rr <= tol * tol * bb) break;
-    }
-  }
-  return DWF_OK;
+  return coarse_cg_persistent(C->ctx, e, rc, C->A32, C->g.Lc, C->g.nc, C->nb, tol, maxiter, (float2*)work,
+                              (double*)part, part_cap, (int*)small, iters, st);
 }
 
 }  // namespace

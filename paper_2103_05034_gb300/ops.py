@@ -334,4 +334,4 @@ def dwf_autotune(ctx, prec=F32, reps=20):
 
 
 def dwf_set_hop_variant(ctx, prec, variant):
-    check(lib().dwf_set_hop_variant(ctx.h, prec, variant))
+    check(lib().dwf_set_hop_variant(ctx.h, prec, variant), ctx.h)

@@ -59,3 +59,12 @@ def test_layout_roundtrip(L):
     assert np.array_equal(lex_even // 2, np.arange(len(lex_even)))
     r = layout.complex_to_real(full, 1)
     assert r.dtype == np.float32 and r.size == 2 * full.size
+
+
+def test_header_constants_match_binding():
+    import re
+    text = open(os.path.join(ROOT, "include", "dwfmg.h")).read()
+    consts = dict((k, int(v)) for k, v in re.findall(r"#define (DWF_\w+) (-?\d+)", text))
+    assert consts["DWF_HOP_VARIANTS"] == _lib.HOP_VARIANTS
+    assert (consts["DWF_F64"], consts["DWF_F32"], consts["DWF_F16S"], consts["DWF_TF32"]) == \
+        (_lib.F64, _lib.F32, _lib.F16S, _lib.TF32)

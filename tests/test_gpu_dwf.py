@@ -11,7 +11,7 @@ import torch
 
 import synth
 from oracle import dwf, krylov
-from paper_2103_05034_gb300 import ops
+from paper_2103_05034_gb300 import _lib, ops
 from paper_2103_05034_gb300._lib import (DWF_EINVAL, F16S, F32, F64, SOLVE_F64, SOLVE_MIXED_F32,
                                          DWFError)
 
@@ -199,13 +199,18 @@ def test_power_method(case):
 
 
 @pytest.mark.parametrize("prec", [F32, F16S])
-@pytest.mark.parametrize("variant", range(10))
+@pytest.mark.parametrize("variant", range(_lib.HOP_VARIANTS))
 def test_every_hop_variant_matches_oracle(prec, variant):
     """Each tuning variant of the hopping kernel (register caps, prefetch,
-    packed FP32 arithmetic) reproduces the oracle, plain and with the fused
-    M_ee / M_ee^-1 epilogues of M_pc."""
+    packed FP32 arithmetic, hypercube tiles, s-pairs, multi-row CTAs)
+    reproduces the oracle, plain and with the fused M_ee / M_ee^-1 epilogues
+    of M_pc."""
     from paper_2103_05034_gb300 import layout
-    for L, Ls in (((4, 4, 2, 2), 16), ((2, 4, 2, 2), 24)):
+    rows = 4 if variant >= 16 else 2 if variant >= 14 else 1  # CTAs over several y-rows
+    cases = [((16, 4, 2, 2), 16), ((16, 4, 2, 2), 24)]  # x segments of 8 sites, 4 rows
+    if rows == 1:
+        cases += [((4, 4, 2, 2), 16), ((2, 4, 2, 2), 24)]
+    for L, Ls in cases:
         U = synth.random_gauge(L, 0.5, 8)
         ctx = ops.Context(L, Ls, M5, U)
         ops.dwf_set_hop_variant(ctx, prec, variant)
@@ -223,3 +228,14 @@ def test_every_hop_variant_matches_oracle(prec, variant):
             ops.dwf_mpc(ctx, out, inp, 0.05, 1)
             assert rel(dev_to_half(out, Ls), layout.to_half(dwf.mpc_dag(U, pe, M5, 0.05), L, 0)) < TOL[prec]
         ctx.close()
+
+
+def test_row_block_variant_rejected_where_it_does_not_tile():
+    """A multi-row variant on a lattice whose x extent is not a multiple of
+    the 8-site segment is refused (DWF_EINVAL), never launched."""
+    L, Ls = (4, 4, 2, 2), 16
+    ctx = ops.Context(L, Ls, M5, synth.random_gauge(L, 0.5, 8))
+    with pytest.raises(DWFError) as e:
+        ops.dwf_set_hop_variant(ctx, F32, 16)
+    assert e.value.code == DWF_EINVAL
+    ctx.close()
