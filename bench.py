@@ -414,6 +414,57 @@ def run_ours(args):
     return 0
 
 
+def run_coarse_kernel(args):
+    """`--kernel coarse_tf32|coarse_f32`: the little Dirac operator of H_DW on
+    the workload's lattice (4^4 x Ls blocks, 32 basis vectors from Gaussians,
+    chirality-projected and block-orthonormalised) applied to 32 right-hand
+    sides, warmup + steps launches, L2 flushed before each timed launch."""
+    import torch
+
+    from paper_2103_05034_gb300 import ops
+    from paper_2103_05034_gb300._lib import F32, F64, TF32
+
+    w, U, _ = build_workload(args.workload, 0)
+    L, Ls, mf = w["L"], w["Ls"], w["mf"]
+    ctx = ops.Context(L, Ls, w["M5"], U)
+    nb, nrhs, block = 32, 32, (4, 4, 4, 4)
+    nfull = 2 * ctx.half_numel()  # reals of one full FP64 field
+    gen = torch.Generator(device="cuda").manual_seed(synth.SEED_BASIS)
+    g = torch.randn(nb * nfull, generator=gen, device="cuda", dtype=torch.float64)
+    basis = torch.empty_like(g)
+    half = nb // 2 * nfull
+    ops.dwf_chiral_project(ctx, basis[:half], g[:half], 1, nb // 2)
+    ops.dwf_chiral_project(ctx, basis[half:], g[half:], -1, nb // 2)
+    del g
+    ops.block_orthonormalise(ctx, basis, nb, nb // 2, block)
+    Cc = ops.coarse_build(ctx, basis, nb, nb // 2, block, mf)
+    del basis
+    prec = {"tf32": TF32, "f32": F32}[args.kernel.split("_")[1]]
+    inp = torch.randn(2 * Cc.nc * nb * nrhs, generator=gen, device="cuda", dtype=torch.float32)
+    out = torch.zeros_like(inp)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        ops.coarse_apply(Cc, out, inp, nrhs, prec)
+    ts = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ops.coarse_apply(Cc, out, inp, nrhs, prec)
+        z.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(z))
+    ms = float(np.median(ts))
+    flop = 8.0 * 9 * nb * nb * nrhs * Cc.nc
+    abytes = Cc.nc * 9 * nb * nb * 8 + 2 * Cc.nc * nb * nrhs * 8  # FP32 operator + in/out vectors
+    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "coarse_sites": Cc.nc, "nbasis": nb,
+                      "nrhs": nrhs, "ms_median": ms, "tflops": flop / ms / 1e9,
+                      "GBs_algorithmic": abytes / ms / 1e6, "flop_per_launch": flop,
+                      "bytes_per_launch": abytes}))
+    Cc.close()
+    ctx.close()
+
+
 def run_kernel(args):
     """Kernel-only loop for profiling: `--kernel dhop_f32|dhop_f64|dhop_f16|mpcdagmpc_f32`
     at the workload's size, warmup + steps launches, no solver."""
@@ -495,13 +546,15 @@ def main(argv=None):
     ap.add_argument("--no-mg-compare", dest="mg_compare", action="store_false",
                     help="skip the one-off FP64 RB-CG vs HDCR time-to-solution comparison")
     ap.add_argument("--kernel", default=None,
-                    help="profile mode: dhop_f32, dhop_f64, dhop_f16 or mpcdagmpc_f32 alone")
+                    help="profile mode: dhop_f32, dhop_f64, dhop_f16, mpcdagmpc_f32, coarse_tf32 or coarse_f32 alone")
     ap.add_argument("--hop-variant", type=int, default=None,
                     help="with --kernel dhop_*: pin this hopping-kernel variant instead of autotuning")
     ap.add_argument("--sweep-variants", action="store_true",
                     help="with --kernel dhop_*: time every hopping-kernel tuning variant")
     args = ap.parse_args(argv)
     if args.kernel:
+        if args.kernel.startswith("coarse_"):
+            return run_coarse_kernel(args)
         return run_kernel(args)
     if args.impl == "reference":
         return run_reference(args)

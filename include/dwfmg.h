@@ -94,6 +94,8 @@ typedef struct dwf_solve_stats {
   double seconds;            /* wall time of the call (host clock) */
   double setup_seconds;      /* mg_setup phases: subspace filter */
   double coarse_op_seconds;  /* mg_setup phases: coarse operator build */
+  int graph_replays;         /* mg_solve: V-cycles replayed from a CUDA graph */
+  int pad_;
 } dwf_solve_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -125,7 +127,9 @@ int dwf_reset_counters(dwf_ctx* ctx);
 /* Autotuner of the hopping kernel: times every tuning variant (register cap x
  * inner-loop form: scalar, neighbour prefetch, packed FP32 on (re, im) pairs,
  * 2^4 hypercube tiles, two s-slices per thread with packed FP32 over the
- * pair, CTAs of 2 or 4 y-rows; DWF_HOP_VARIANTS variants for FP32 and FP16
+ * pair (loads into registers, or staged in shared memory by cp.async with 2,
+ * 4 or 8 neighbours in flight), CTAs of 2 or 4 y-rows; DWF_HOP_VARIANTS
+ * variants for FP32 and FP16
  * storage at Ls >= 16, one otherwise) on this context's lattice, `reps`
  * launches each, keeps the fastest for precision `prec` and returns its time
  * per launch in *best_ms (may be NULL).  Variants that do not tile the
@@ -134,7 +138,7 @@ int dwf_reset_counters(dwf_ctx* ctx);
  * read the choice (0 = untuned default; valid ids 0 .. DWF_HOP_VARIANTS-1;
  * dwf_set_hop_variant returns DWF_EINVAL for a variant that does not tile
  * the lattice). */
-#define DWF_HOP_VARIANTS 18
+#define DWF_HOP_VARIANTS 23
 int dwf_autotune(dwf_ctx* ctx, int prec, int reps, double* best_ms, void* stream);
 int dwf_set_hop_variant(dwf_ctx* ctx, int prec, int variant);
 int dwf_get_hop_variant(const dwf_ctx* ctx, int prec);
@@ -330,6 +334,8 @@ typedef struct dwf_mg_params {
   int coarse_maxiter;
   int nkrylov;           /* GCR restart length */
   int maxiter;           /* outer iterations */
+  int no_graph;          /* 0: mg_solve captures the V-cycle in a CUDA graph
+                            once per solve and replays it; 1: plain launches */
 } dwf_mg_params;
 
 /* Build the multigrid setup: filtered vectors from eta (nbasis FP64 full fields

@@ -18,7 +18,7 @@ DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ENOCONV, DWF_ENAN, DWF_ECUDA, DWF_ETIMEOUT, 
     0, -1, -2, -3, -4, -5, -6, -7
 F64, F32, F16S, TF32 = 0, 1, 2, 3
 SOLVE_F64, SOLVE_MIXED_F32, SOLVE_MIXED_F16 = 0, 1, 2
-HOP_VARIANTS = 18  # DWF_HOP_VARIANTS
+HOP_VARIANTS = 23  # DWF_HOP_VARIANTS
 STATUS_NAMES = {0: "DWF_OK", -1: "DWF_EINVAL", -2: "DWF_ENOMEM", -3: "DWF_ENOCONV",
                 -4: "DWF_ENAN", -5: "DWF_ECUDA", -6: "DWF_ETIMEOUT", -7: "DWF_ERANGE"}
 
@@ -28,7 +28,7 @@ class SolveStats(C.Structure):
                 ("coarse_iterations", C.c_int), ("status", C.c_int),
                 ("fine_matmuls", C.c_double), ("true_residual", C.c_double),
                 ("seconds", C.c_double), ("setup_seconds", C.c_double),
-                ("coarse_op_seconds", C.c_double)]
+                ("coarse_op_seconds", C.c_double), ("graph_replays", C.c_int), ("pad_", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -42,7 +42,8 @@ class MGParams(C.Structure):
                 ("mf", C.c_double), ("lambda_lo", C.c_double), ("lambda_max", C.c_double),
                 ("filter_order", C.c_int), ("delta", C.c_int), ("smooth_lo", C.c_double),
                 ("smooth_hi", C.c_double), ("smooth_order", C.c_int), ("coarse_tol", C.c_double),
-                ("coarse_maxiter", C.c_int), ("nkrylov", C.c_int), ("maxiter", C.c_int)]
+                ("coarse_maxiter", C.c_int), ("nkrylov", C.c_int), ("maxiter", C.c_int),
+                ("no_graph", C.c_int)]
 
 
 def header_functions():

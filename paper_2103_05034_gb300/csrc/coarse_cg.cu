@@ -40,43 +40,25 @@ struct CoarseCGArgs {
   int nc, nb;
   const float2* rhs;
   float2 *e, *r, *p0, *p1, *t;
-  double* part;        // [3][nblk] partial sums
-  unsigned* bar;       // barrier counter, zero at launch
+  double* part;        // [nblk] partial sums of the current reduction
+  double* tot;         // [2] grid totals (alternating)
+  unsigned* bar;       // arrival counter, zero at launch
+  unsigned* rel;       // release counter, zero at launch
   int* status;         // [ST_ITERS], [ST_ERR]
+  int* acc;            // optional: [0] += iterations, [1] |= error (sticky over launches)
   double tol2;
   int maxiter;
 };
+
+__device__ void set_err(const CoarseCGArgs& a, int code) {
+  atomicCAS(&a.status[ST_ERR], 0, code);
+  if (a.acc) atomicOr(&a.acc[1], code);
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// Grid barrier number k (k = 1, 2, ...): returns false when the wait ran out
-// or another CTA has already given up.
-__device__ bool grid_barrier(const CoarseCGArgs& a, unsigned k) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(a.bar, 1u);
-    const unsigned target = k * gridDim.x;
-    int good = 0;
-    for (unsigned i = 0; i < CG_SPIN; i++) {
-      if (ld_acquire(a.bar) >= target) {
-        good = 1;
-        break;
-      }
-      if (*(volatile int*)&a.status[ST_ERR]) break;
-      __nanosleep(32);
-    }
-    if (!good) atomicCAS(&a.status[ST_ERR], 0, ERR_TIMEOUT);
-    __threadfence();
-    ok = good;
-  }
-  __syncthreads();
-  return ok;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -85,31 +67,64 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum of the nblk partials of one slot, same order in every CTA.
-__device__ double total(const CoarseCGArgs& a, int slot) {
-  __shared__ double s;
-  if (threadIdx.x < 32) {
-    double v = 0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) v += __ldcg(a.part + (size_t)slot * gridDim.x + i);
-    v = warp_sum(v);
-    if (threadIdx.x == 0) s = v;
-  }
-  __syncthreads();
-  const double out = s;
-  __syncthreads();
-  return out;
-}
-
-// CTA-wide sum of one double per warp (lane 0 holds it) into part[slot][blockIdx].
-__device__ void store_partial(const CoarseCGArgs& a, int slot, double v) {
+// Grid-wide sum at barrier number k (k = 1, 2, ...).  Every CTA adds its
+// partial (lane 0 of each warp holds the warp's) to part[blockIdx]; the CTA
+// that arrives last sums all partials in block order (fixed order, so the
+// result does not depend on which CTA is last) into tot[k & 1] and releases
+// the others, which wait on rel >= k.  Returns false when a wait ran out or
+// another CTA has given up (the error is recorded).
+__device__ bool reduce_barrier(const CoarseCGArgs& a, unsigned k, double warp_partial, double* total) {
   __shared__ double w[CG_WARPS];
-  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+  __shared__ int flag;
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = warp_partial;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0;
     for (int i = 0; i < CG_WARPS; i++) s += w[i];
-    a.part[(size_t)slot * gridDim.x + blockIdx.x] = s;
+    a.part[blockIdx.x] = s;
+    __threadfence();
+    const unsigned old = atomicAdd(a.bar, 1u);
+    flag = (old == k * gridDim.x - 1) ? 2 : 0;  // 2: this CTA is the last to arrive
   }
+  __syncthreads();
+  if (flag == 2) {
+    __threadfence();
+    double v = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += CG_THREADS) v += __ldcg(a.part + i);
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int i = 0; i < CG_WARPS; i++) s += w[i];
+      a.tot[k & 1] = s;
+      __threadfence();
+      atomicExch(a.rel, k);
+      flag = 1;
+    }
+  } else if (threadIdx.x == 0) {
+    // poll with a growing pause: hundreds of CTAs reading one L2 line at full
+    // rate would queue the arrivals and the release behind the polls
+    int good = 0;
+    unsigned pause = 32;
+    for (unsigned i = 0; i < CG_SPIN; i++) {
+      if (ld_acquire(a.rel) >= k) {
+        good = 1;
+        break;
+      }
+      if (*(volatile int*)&a.status[ST_ERR]) break;
+      __nanosleep(pause);
+      if (pause < 128) pause <<= 1;
+    }
+    if (!good) set_err(a, ERR_TIMEOUT);
+    __threadfence();
+    flag = good;
+  }
+  __syncthreads();
+  const int ok = flag;
+  *total = __ldcg(a.tot + (k & 1));
+  __syncthreads();  // flag and w are reused by the next call
+  return ok;
 }
 
 // Row (x, j) of A v with v = u + beta w gathered at the neighbours (w may be
@@ -153,6 +168,54 @@ __device__ __forceinline__ float2 row_apply(const CoarseCGArgs& a, int x, int j,
   return make_float2(re, im);
 }
 
+// Two rows at once (rows r0 and r0 + stride, the second only when valid):
+// the loads of both are issued before either is reduced, doubling the bytes
+// in flight per warp.
+template <int NB>
+__device__ __forceinline__ void row_apply2(const CoarseCGArgs& a, long long r0, long long r1, bool has1,
+                                           const float2* u, const float2* w, float beta, float2& o0, float2& o1) {
+  const int x0 = (int)(r0 / a.nb), j0 = (int)(r0 % a.nb);
+  const int x1 = has1 ? (int)(r1 / a.nb) : x0, j1 = has1 ? (int)(r1 % a.nb) : j0;
+  if (NB != 32) {  // generic width: one row after the other
+    o0 = row_apply<NB>(a, x0, j0, u, w, beta);
+    o1 = has1 ? row_apply<NB>(a, x1, j1, u, w, beta) : make_float2(0.f, 0.f);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+#pragma unroll
+  for (int d = 0; d < 9; d++) {
+    const int y0 = dwfmg::coarse_nbr(a.Lc, x0, d), y1 = dwfmg::coarse_nbr(a.Lc, x1, d);
+    const float2 m0 = __ldg(a.A + (((size_t)x0 * 9 + d) * 32 + j0) * 32 + lane);
+    const float2 m1 = __ldg(a.A + (((size_t)x1 * 9 + d) * 32 + j1) * 32 + lane);
+    float2 v0 = __ldcg(u + (size_t)y0 * 32 + lane), v1 = __ldcg(u + (size_t)y1 * 32 + lane);
+    if (w) {
+      const float2 q0 = __ldcg(w + (size_t)y0 * 32 + lane), q1 = __ldcg(w + (size_t)y1 * 32 + lane);
+      v0.x = fmaf(beta, q0.x, v0.x);
+      v0.y = fmaf(beta, q0.y, v0.y);
+      v1.x = fmaf(beta, q1.x, v1.x);
+      v1.y = fmaf(beta, q1.y, v1.y);
+    }
+    re0 = fmaf(m0.x, v0.x, re0);
+    re0 = fmaf(-m0.y, v0.y, re0);
+    im0 = fmaf(m0.x, v0.y, im0);
+    im0 = fmaf(m0.y, v0.x, im0);
+    re1 = fmaf(m1.x, v1.x, re1);
+    re1 = fmaf(-m1.y, v1.y, re1);
+    im1 = fmaf(m1.x, v1.y, im1);
+    im1 = fmaf(m1.y, v1.x, im1);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    re0 += __shfl_xor_sync(0xffffffffu, re0, o);
+    im0 += __shfl_xor_sync(0xffffffffu, im0, o);
+    re1 += __shfl_xor_sync(0xffffffffu, re1, o);
+    im1 += __shfl_xor_sync(0xffffffffu, im1, o);
+  }
+  o0 = make_float2(re0, im0);
+  o1 = make_float2(re1, im1);
+}
+
 template <int NB>
 __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(CoarseCGArgs a) {
   const int lane = threadIdx.x & 31;
@@ -160,27 +223,36 @@ __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(CoarseCGArgs a) {
   const long long nwarps = (long long)gridDim.x * CG_WARPS;
   const long long rows = (long long)a.nc * a.nb;
   unsigned nbar = 0;
+  // Each warp owns rows warp, warp + nwarps, warp + 2 nwarps, ... and takes
+  // them two at a time.  body(row, value) is run by lane 0 for each row.
+  auto sweep = [&](const float2* u, const float2* w, float beta, auto&& body) {
+    for (long long r0 = warp; r0 < rows; r0 += 2 * nwarps) {
+      const long long r1 = r0 + nwarps;
+      const bool has1 = r1 < rows;
+      float2 o0, o1;
+      row_apply2<NB>(a, r0, r1, has1, u, w, beta, o0, o1);
+      if (lane == 0) {
+        body(r0, o0);
+        if (has1) body(r1, o1);
+      }
+    }
+  };
 
   // b = A rhs; r = b; both p buffers zero; e = 0.
   double acc = 0;
-  for (long long row = warp; row < rows; row += nwarps) {
-    const int x = (int)(row / a.nb), j = (int)(row % a.nb);
-    const float2 b = row_apply<NB>(a, x, j, a.rhs, nullptr, 0.f);
-    if (lane == 0) {
-      a.r[row] = b;
-      a.p0[row] = make_float2(0.f, 0.f);
-      a.p1[row] = make_float2(0.f, 0.f);
-      a.e[row] = make_float2(0.f, 0.f);
-      acc += (double)b.x * b.x + (double)b.y * b.y;
-    }
-  }
-  store_partial(a, 0, acc);
-  if (!grid_barrier(a, ++nbar)) return;
-  const double bb = total(a, 0);
+  sweep(a.rhs, nullptr, 0.f, [&](long long row, float2 b) {
+    a.r[row] = b;
+    a.p0[row] = make_float2(0.f, 0.f);
+    a.p1[row] = make_float2(0.f, 0.f);
+    a.e[row] = make_float2(0.f, 0.f);
+    acc += (double)b.x * b.x + (double)b.y * b.y;
+  });
+  double bb;
+  if (!reduce_barrier(a, ++nbar, acc, &bb)) return;
   if (!(bb > 0)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       a.status[ST_ITERS] = 0;
-      if (!isfinite(bb)) atomicCAS(&a.status[ST_ERR], 0, ERR_NAN);
+      if (!isfinite(bb)) set_err(a, ERR_NAN);
     }
     return;
   }
@@ -192,63 +264,62 @@ __global__ void __launch_bounds__(CG_THREADS) k_coarse_cg(CoarseCGArgs a) {
     const float2* pprev = (it & 1) ? a.p0 : a.p1;
     // phase A: p_i = r + beta p_{i-1}; t = A p_i
     acc = 0;
-    for (long long row = warp; row < rows; row += nwarps) {
-      const int x = (int)(row / a.nb), j = (int)(row % a.nb);
-      const float2 tv = row_apply<NB>(a, x, j, a.r, pprev, (float)beta);
-      if (lane == 0) {
-        const float2 rv = __ldcg(a.r + row), pv = __ldcg(pprev + row);
-        pcur[row] = make_float2(fmaf((float)beta, pv.x, rv.x), fmaf((float)beta, pv.y, rv.y));
-        a.t[row] = tv;
-        acc += (double)tv.x * tv.x + (double)tv.y * tv.y;
-      }
-    }
-    store_partial(a, 1, acc);
-    if (!grid_barrier(a, ++nbar)) return;
-    const double pap = total(a, 1);
+    sweep(a.r, pprev, (float)beta, [&](long long row, float2 tv) {
+      const float2 rv = __ldcg(a.r + row), pv = __ldcg(pprev + row);
+      pcur[row] = make_float2(fmaf((float)beta, pv.x, rv.x), fmaf((float)beta, pv.y, rv.y));
+      a.t[row] = tv;
+      acc += (double)tv.x * tv.x + (double)tv.y * tv.y;
+    });
+    double pap;
+    if (!reduce_barrier(a, ++nbar, acc, &pap)) return;
     if (!(pap > 0)) {  // A p = 0 with p != 0 cannot happen for a nonsingular A
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.status[ST_ERR], 0, ERR_NAN);
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_err(a, ERR_NAN);
       return;
     }
     const double alpha = rr / pap;
     // phase B: q = A t; e += alpha p_i; r -= alpha q
     acc = 0;
-    for (long long row = warp; row < rows; row += nwarps) {
-      const int x = (int)(row / a.nb), j = (int)(row % a.nb);
-      const float2 q = row_apply<NB>(a, x, j, a.t, nullptr, 0.f);
-      if (lane == 0) {
-        const float2 pv = __ldcg(pcur + row);
-        float2 ev = __ldcg(a.e + row), rv = __ldcg(a.r + row);
-        ev.x = fmaf((float)alpha, pv.x, ev.x);
-        ev.y = fmaf((float)alpha, pv.y, ev.y);
-        rv.x = fmaf(-(float)alpha, q.x, rv.x);
-        rv.y = fmaf(-(float)alpha, q.y, rv.y);
-        a.e[row] = ev;
-        a.r[row] = rv;
-        acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
-      }
-    }
-    store_partial(a, 2, acc);
-    if (!grid_barrier(a, ++nbar)) return;
-    const double rrn = total(a, 2);
+    sweep(a.t, nullptr, 0.f, [&](long long row, float2 q) {
+      const float2 pv = __ldcg(pcur + row);
+      float2 ev = __ldcg(a.e + row), rv = __ldcg(a.r + row);
+      ev.x = fmaf((float)alpha, pv.x, ev.x);
+      ev.y = fmaf((float)alpha, pv.y, ev.y);
+      rv.x = fmaf(-(float)alpha, q.x, rv.x);
+      rv.y = fmaf(-(float)alpha, q.y, rv.y);
+      a.e[row] = ev;
+      a.r[row] = rv;
+      acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+    });
+    double rrn;
+    if (!reduce_barrier(a, ++nbar, acc, &rrn)) return;
     if (!isfinite(rrn)) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.status[ST_ERR], 0, ERR_NAN);
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_err(a, ERR_NAN);
       return;
     }
     beta = rrn / rr;
     rr = rrn;
     if (rr <= a.tol2 * bb) break;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.status[ST_ITERS] = it;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.status[ST_ITERS] = it;
+    if (a.acc) atomicAdd(&a.acc[0], it);
+  }
 }
 
 }  // namespace
 
 // e = (A^2)^-1 A rhs on one right-hand side, FP32 vectors [nc][nb].  Work
-// buffers: r, p0, p1, t (each nc*nb float2), partials (3*grid doubles), and
-// an int[2] status plus an unsigned barrier counter in dev_small (16 bytes).
+// buffers: r, p0, p1, t (each nc*nb float2), part (2 totals + one partial per
+// CTA, doubles), and in dev_small (CG_SMALL_BYTES) the int[2] status and,
+// each in a 128-byte line of its own, the arrival and release counters of
+// the grid barrier.
+// With acc == nullptr the call synchronises and returns the iteration count
+// and any error; with acc set it only enqueues (no host synchronisation, so
+// it can be captured in a CUDA graph) and the kernel adds its iteration count
+// to acc[0] and ORs its error code into acc[1] for the caller to read later.
 int coarse_cg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float2* A, const int Lc[4], int nc,
                          int nb, double tol, int maxiter, float2* work, double* part, int part_cap,
-                         int* dev_small, int* iters, cudaStream_t st) {
+                         int* dev_small, int* acc, int* iters, cudaStream_t st) {
   // NB = 32 and 64 compiled with fixed nb (fully unrolled loads); others generic
   void (*kern)(CoarseCGArgs) = nb == 32 ? k_coarse_cg<32> : nb == 64 ? k_coarse_cg<64> : k_coarse_cg<0>;
   const int ki = nb == 32 ? 0 : nb == 64 ? 1 : 2;
@@ -268,7 +339,7 @@ int coarse_cg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float2*
   const long long need = (rows + CG_WARPS - 1) / CG_WARPS;
   if (grid > need) grid = (int)need;
   if (grid < 1) grid = 1;
-  if (3 * grid > part_cap) return dwf_fail(c, DWF_EINVAL, "coarse CG partial buffer too small");
+  if (grid + 2 > part_cap) return dwf_fail(c, DWF_EINVAL, "coarse CG partial buffer too small");
   CoarseCGArgs a;
   a.A = A;
   for (int m = 0; m < 4; m++) a.Lc[m] = Lc[m];
@@ -280,15 +351,22 @@ int coarse_cg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float2*
   a.p0 = work + rows;
   a.p1 = work + 2 * rows;
   a.t = work + 3 * rows;
-  a.part = part;
+  a.part = part + 2;  // part[0..1]: the two grid totals
+  a.tot = part;
   a.status = dev_small;
-  a.bar = (unsigned*)(dev_small + 2);
+  a.bar = (unsigned*)(dev_small + 32);
+  a.rel = (unsigned*)(dev_small + 64);
+  a.acc = acc;
   a.tol2 = tol * tol;
   a.maxiter = maxiter;
-  DWF_CUDA(c, cudaMemsetAsync(dev_small, 0, 4 * sizeof(int), st));
+  DWF_CUDA(c, cudaMemsetAsync(dev_small, 0, CG_SMALL_BYTES, st));
   void* args[] = {&a};
   c->launches++;
   DWF_CUDA(c, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(CG_THREADS), args, 0, st));
+  if (acc) {
+    *iters = 0;
+    return DWF_OK;
+  }
   int hs[2] = {0, 0};
   DWF_CUDA(c, cudaMemcpyAsync(hs, dev_small, sizeof(hs), cudaMemcpyDeviceToHost, st));
   DWF_CUDA(c, cudaStreamSynchronize(st));

@@ -5,18 +5,19 @@
 //
 // Real form of one complex block product (nb = 32):
 //   [Re out; Im out] (64 x N) = [[Ar, -Ai], [Ai, Ar]] (64 x 64) [Re in; Im in] (64 x N)
-// tcgen05.mma with M = 128 is used with two coarse sites per CTA packed
-// block-diagonally: rows 0-63 / K 0-63 belong to site x1, rows 64-127 /
-// K 64-127 to site x2 (the off-diagonal blocks are zero and stay resident in
-// shared memory), so the accumulator row i is TMEM lane i.  For each of the 9
-// directions one pipeline stage holds
-//   A: [K/4 = 32][M = 128][4] TF32 (64 KB; the two 16 KB site blocks arrive by
-//      cp.async.bulk from a pre-arranged copy of the operator)
-//   B: [K/4 = 32][N][4] TF32 (N*512 B; the neighbours' input vectors, split
-//      into real and imaginary rows by the threads)
+// tcgen05.mma with M = 128 takes two coarse sites at once: the A tile of one
+// direction stacks site x1's 64 rows over site x2's (K = 64, no zero blocks),
+// and two MMA chains multiply it by x1's and by x2's B block into two column
+// ranges of the accumulator; rows 0-63 of the first range and rows 64-127 of
+// the second are the two results (the other quadrants are discarded).  One
+// pipeline stage per direction holds
+//   A: [K/4 = 16][M = 128][4] TF32 (32 KB, one cp.async.bulk from a copy of
+//      the operator pre-arranged per site pair)
+//   B: 2 x [K/4 = 16][N][4] TF32 (2 x N*256 B, the neighbours' blocks of a
+//      pre-arranged copy of the right-hand sides)
 // in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices;
-// K-adjacent cores LBO apart, M/N-adjacent cores 128 B apart).  16 MMAs of
-// K = 8 per stage, two stages in flight, one tcgen05.commit per stage.
+// K-adjacent cores LBO apart, M/N-adjacent cores 128 B apart); 3 to 5 stages
+// in flight, 16 MMAs of K = 8 per stage, one tcgen05.commit per stage.
 #include <string.h>
 
 #include "dwf_internal.cuh"
@@ -27,8 +28,8 @@ namespace {
 constexpr int TC_NB = 32;           // basis vectors per site handled here
 constexpr int TC_ROWS = 2 * TC_NB;  // real rows per site
 constexpr int TC_M = 128;
-constexpr int TC_K = 128;           // per stage: two sites x 64
-constexpr int TC_THREADS = 128;
+constexpr int TC_K = 64;            // per stage and site
+constexpr int TC_THREADS = 128;     // epilogue warps; one more warp issues copies and MMAs
 constexpr unsigned TC_SPIN = 1u << 22;  // bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -63,13 +64,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// Pre-arranged operator: At[x][d][kg = 16][r = 64][4] TF32 (real form, K-major).
+// Pre-arranged operator, per pair of coarse sites (2p, 2p+1) and direction:
+// At[p][d][kg = 16][r = 128][4] TF32 (real form, K-major), rows 0-63 site 2p
+// and rows 64-127 site 2p+1, so that one stage's A tile is one contiguous
+// 32 KB bulk copy.
 __global__ void k_tc_arrange(float* At, const float2* A, int nc) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (x, d, r, k)
   if (e >= (long long)nc * 9 * TC_ROWS * TC_ROWS) return;
   const int k = (int)(e % TC_ROWS);
   const int r = (int)((e / TC_ROWS) % TC_ROWS);
   const long long xd = e / (TC_ROWS * TC_ROWS);
+  const long long x = xd / 9;
+  const int d = (int)(xd % 9);
   const int j = r % TC_NB, kk = k % TC_NB;
   const float2 a = A[(xd * TC_NB + j) * TC_NB + kk];
   float v;
@@ -77,36 +83,97 @@ __global__ void k_tc_arrange(float* At, const float2* A, int nc) {
     v = k < TC_NB ? a.x : -a.y;
   else
     v = k < TC_NB ? a.y : a.x;
-  At[((xd * (TC_ROWS / 4) + k / 4) * TC_ROWS + r) * 4 + (k & 3)] = to_tf32(v);
+  const long long pd = (x >> 1) * 9 + d;
+  const int row = (int)(x & 1) * TC_ROWS + r;
+  At[((pd * (TC_ROWS / 4) + k / 4) * TC_M + row) * 4 + (k & 3)] = to_tf32(v);
 }
 
+// Pre-arranged right-hand sides: Bt[y][kg = 16][n = N][4] TF32, K index
+// k < 32 the real part and k >= 32 the imaginary part of in[y][k mod 32][n]
+// (the K-major no-swizzle layout of one site's 64 x N B block), so that the
+// main kernel fetches a neighbour's block with one bulk copy.
+__global__ void k_tc_arrange_in(float* Bt, const float2* in, int nc, int N) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (y, j, n)
+  if (e >= (long long)nc * TC_NB * N) return;
+  const int n = (int)(e % N);
+  const int j = (int)((e / N) % TC_NB);
+  const long long y = e / ((long long)N * TC_NB);
+  const float2 v = in[e];
+  const int kre = j, kim = TC_NB + j;
+  Bt[((y * (TC_ROWS / 4) + kre / 4) * N + n) * 4 + (kre & 3)] = to_tf32(v.x);
+  Bt[((y * (TC_ROWS / 4) + kim / 4) * N + n) * 4 + (kim & 3)] = to_tf32(v.y);
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Pipeline depth for N right-hand sides: as many 32 KB + N*512 B stages as
+// fit in about 220 KB of shared memory, at most 5.
 template <int N>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_coarse_apply_tc(float2* out, const float2* in, const float* At, int Lc0, int Lc1, int Lc2, int Lc3,
-                      int* err) {
+struct TcStages {
+  static constexpr int bytes = (TC_K / 4) * TC_M * 16 + 2 * (TC_K / 4) * N * 16;
+  static constexpr int v = (220 * 1024 / bytes) < 5 ? (220 * 1024 / bytes) : 5;
+};
+
+// Persistent, warp-specialised coarse stencil.  Each CTA walks pairs of
+// coarse sites (x1, x2) = (2p, 2p+1), p = blockIdx.x, blockIdx.x + gridDim.x,
+// ...; one pair is 9 pipeline stages (one per stencil direction d).
+//   warp 4 (one elected thread): for stage g, waits until the MMAs of stage
+//     g-S have released shared-memory buffer g%S, posts the stage's bytes on
+//     full[g%S] and issues its three bulk copies (A_d of the pair, 32 KB; the
+//     neighbours' B blocks, 2 x N*256 B); then issues the 16 MMAs of stage
+//     g-S+1 once its copies have landed and commits them to done[(g-S+1)%S]
+//     (and, after a pair's last direction, to acc_full[t]).  S-1 stages of
+//     copies are in flight while one stage multiplies.
+//   warps 0-3: per pair, wait acc_full[t], read the accumulator (TMEM lane =
+//     stacked row; rows 0-63 from the first column range, 64-127 from the
+//     second) with tcgen05.ld, store it, and arrive on acc_empty[t]; the
+//     producer waits on acc_empty[t] before the first MMA of the pair two
+//     later, which reuses accumulator t (two accumulators of 2N columns in
+//     TMEM, so a pair's epilogue overlaps the next pair's MMAs).
+// Every wait is bounded; a thread whose wait runs out sets *err and stops
+// issuing work, and the producer waits (bounded) for copies still in flight
+// before the CTA frees its tensor memory.
+template <int N>
+__global__ void __launch_bounds__(TC_THREADS + 32, 1)
+    k_coarse_apply_tc(float2* out, const float* Bt, const float* At, int Lc0, int Lc1, int Lc2, int Lc3,
+                      int npairs, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr int A_BYTES = (TC_K / 4) * TC_M * 16;  // 64 KB
-  constexpr int B_BYTES = (TC_K / 4) * N * 16;
+  constexpr int S = TcStages<N>::v;
+  constexpr int A_BYTES = (TC_K / 4) * TC_M * 16;  // 32 KB
+  constexpr int B_BYTES = (TC_K / 4) * N * 16;     // one site's block
+  constexpr int ST_BYTES = A_BYTES + 2 * B_BYTES;
   constexpr uint32_t LBO_A = TC_M * 16, LBO_B = N * 16, SBO = 128;
-  unsigned char* Abuf[2] = {smem, smem + A_BYTES};
-  unsigned char* Bbuf[2] = {smem + 2 * A_BYTES, smem + 2 * A_BYTES + B_BYTES};
-  uint64_t* bars = (uint64_t*)(smem + 2 * A_BYTES + 2 * B_BYTES);  // full[2], done[2]
-  uint32_t* tslot = (uint32_t*)(bars + 4);
+  constexpr uint32_t NCOL = 2 * N;  // one accumulator: two column ranges of N
+  constexpr uint32_t TCOLS = 2 * NCOL;
+  static_assert(NCOL % 32 == 0 && (TCOLS & (TCOLS - 1)) == 0, "TMEM allocation is a power of two >= 32");
+  uint64_t* bars = (uint64_t*)(smem + S * ST_BYTES);
+  // bars: full[0..S), done[S..2S), acc_full[2S..2S+2), acc_empty[2S+2..2S+4)
+  uint64_t* full = bars;
+  uint64_t* done = bars + S;
+  uint64_t* acc_full = bars + 2 * S;
+  uint64_t* acc_empty = bars + 2 * S + 2;
+  uint32_t* tslot = (uint32_t*)(bars + 2 * S + 4);
+  __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Lc[4] = {Lc0, Lc1, Lc2, Lc3};
-  const int nc = Lc0 * Lc1 * Lc2 * Lc3;
-  const int x1 = 2 * blockIdx.x, x2 = 2 * blockIdx.x + 1;
-  const int xs[2] = {x1, x2};
 
-  // zero both A stages (the off-diagonal blocks stay zero)
-  for (int i = tid; i < 2 * A_BYTES / 16; i += TC_THREADS) ((uint4*)smem)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    for (int i = 0; i < 4; i++) mbar_init(smem_u32(bars + i), 1);
+    for (int i = 0; i < 2 * S + 2; i++) mbar_init(smem_u32(bars + i), 1);
+    for (int i = 0; i < 2; i++) mbar_init(smem_u32(acc_empty + i), TC_THREADS);
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(32 * ((N + 31) / 32)));
+                 "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -115,107 +182,114 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = *tslot;
   constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
                              ((uint32_t)(TC_M >> 4) << 24);
-  bool ok = true;
-
-  for (int d = 0; d < 9; d++) {
-    const int buf = d & 1;
-    const uint32_t use = (uint32_t)(d >> 1) & 1u;
-    if (d >= 2) {  // the MMAs of stage d-2 have finished reading this buffer
-      if (!mbar_wait(smem_u32(bars + 2 + buf), use ^ 1u)) ok = false;
-    }
-    __syncthreads();
-    if (ok && tid == 0) {
-      const uint32_t fb = smem_u32(bars + buf);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * 16 * 1024) : "memory");
-      for (int q = 0; q < 2; q++) {
-        const float* src = At + ((long long)xs[q] * 9 + d) * (TC_ROWS / 4) * TC_ROWS * 4;
-        for (int kg = 0; kg < 16; kg++) {
-          const uint32_t dst = smem_u32(Abuf[buf] + (size_t)(16 * q + kg) * LBO_A + q * TC_ROWS * 16);
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-              "l"(src + kg * TC_ROWS * 4), "r"(TC_ROWS * 16), "r"(fb)
-              : "memory");
-        }
-      }
-    }
-    // B: neighbours' inputs, split into real (k = j) and imaginary (k = 32 + j) rows
-    float* B = (float*)Bbuf[buf];
-    for (int e = tid; e < 2 * TC_NB * N; e += TC_THREADS) {
-      const int n = e % N, j = (e / N) % TC_NB, q = e / (N * TC_NB);
-      const int y = dwfmg::coarse_nbr(Lc, xs[q], d);
-      const float2 v = in[((long long)y * TC_NB + j) * N + n];
-      const int kre = 64 * q + j, kim = 64 * q + 32 + j;
-      B[((kre >> 2) * N + n) * 4 + (kre & 3)] = to_tf32(v.x);
-      B[((kim >> 2) * N + n) * 4 + (kim & 3)] = to_tf32(v.y);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (ok && tid == 0) {
-      if (!mbar_wait(smem_u32(bars + buf), use)) {
-        ok = false;
-      } else {
+  const int mypairs = (int)blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (warp == 4) {
+    if (lane == 0) {
+      bool ok = true;
+      const int nst = mypairs * 9;
+      int issued = 0;  // stages whose copies were issued
+      auto mma_stage = [&](int h) -> bool {
+        const int pl = h / 9, d = h % 9, t = pl & 1, b = h % S;
+        if (d == 0 && pl >= 2 && !mbar_wait(smem_u32(acc_empty + t), ((pl - 2) >> 1) & 1)) return false;
+        if (!mbar_wait(smem_u32(full + b), (h / S) & 1)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(Abuf[buf]), b0 = smem_u32(Bbuf[buf]);
+        const uint32_t a0 = smem_u32(smem + b * ST_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < TC_K / 8; kk++) {
-          const uint64_t ad = smem_desc(a0 + kk * 2 * LBO_A, LBO_A, SBO);
-          const uint64_t bd = smem_desc(b0 + kk * 2 * LBO_B, LBO_B, SBO);
-          const uint32_t acc = (d > 0 || kk > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
+        for (int q = 0; q < 2; q++) {  // site q's B block into column range q
+          const uint32_t b0 = a0 + A_BYTES + q * B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < TC_K / 8; kk++) {
+            const uint64_t ad = smem_desc(a0 + kk * 2 * LBO_A, LBO_A, SBO);
+            const uint64_t bd = smem_desc(b0 + kk * 2 * LBO_B, LBO_B, SBO);
+            const uint32_t acc = (d > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * NCOL + q * N),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(bars + 2 + buf))
-                     : "memory");
+        tc_commit(smem_u32(done + b));
+        if (d == 8) tc_commit(smem_u32(acc_full + t));
+        return true;
+      };
+      for (int g = 0; g < nst && ok; g++) {
+        const int pl = g / 9, d = g % 9, b = g % S;
+        const int p = blockIdx.x + pl * gridDim.x;
+        if (g >= S && !mbar_wait(smem_u32(done + b), ((g - S) / S) & 1)) {
+          ok = false;
+          break;
+        }
+        unsigned char* st = smem + b * ST_BYTES;
+        const uint32_t fb = smem_u32(full + b);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(ST_BYTES) : "memory");
+        bulk_g2s(smem_u32(st), At + ((long long)p * 9 + d) * (TC_ROWS / 4) * TC_M * 4, A_BYTES, fb);
+        for (int q = 0; q < 2; q++) {
+          const int y = dwfmg::coarse_nbr(Lc, 2 * p + q, d);
+          bulk_g2s(smem_u32(st + A_BYTES + q * B_BYTES), Bt + (long long)y * (TC_ROWS / 4) * N * 4, B_BYTES, fb);
+        }
+        issued = g + 1;
+        if (g >= S - 1 && !mma_stage(g - (S - 1))) {
+          ok = false;
+          break;
+        }
+      }
+      for (int h = (nst > S - 1 ? nst - (S - 1) : 0); ok && h < nst; h++)
+        if (!mma_stage(h)) ok = false;
+      if (!ok) {
+        atomicExch(err, 1);
+        atomicExch(&abort_flag, 1);
+        // let copies still in flight land before the CTA exits (bounded)
+        for (int h = (issued >= S ? issued - S : 0); h < issued; h++) mbar_wait(smem_u32(full + h % S), (h / S) & 1);
       }
     }
-    if (tid == 0 && !ok) atomicExch(err, 1);
-    ok = __syncthreads_and(ok);
-  }
-  // the last commit (stage 8, buffer 0, fifth use) covers every earlier MMA
-  if (ok && !mbar_wait(smem_u32(bars + 2), 0u)) ok = false;
-  if (!ok && tid == 0) {
-    atomicExch(err, 1);
-    mbar_wait(smem_u32(bars + 0), 0u);  // bounded: let copies in flight land
-    mbar_wait(smem_u32(bars + 1), 1u);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    // each warp reads its 32 TMEM lanes (= accumulator rows) across N columns
+  } else {
+    // epilogue warps 0-3: warp w owns TMEM lanes 32w..32w+31 = stacked rows;
+    // rows 0-63 are site x1 (column range 0), rows 64-127 site x2 (range 1)
     const int r = warp * 32 + lane;
     const int q = r / TC_ROWS, rr = r % TC_ROWS;
     const int part = rr / TC_NB, j = rr % TC_NB;
-    float* o = (float*)(out + ((long long)xs[q] * TC_NB + j) * N) + part;
+    for (int pl = 0; pl < mypairs; pl++) {
+      const int t = pl & 1;
+      const int p = blockIdx.x + pl * gridDim.x;
+      if (!mbar_wait(smem_u32(acc_full + t), (pl >> 1) & 1)) {
+        atomicExch(err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* o = (float*)(out + ((long long)(2 * p + q) * TC_NB + j) * N) + part;
 #pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + t * NCOL + q * N + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int i = 0; i < 16; i++) o[2 * (c0 + i)] = __uint_as_float(v[i]);
+        for (int i = 0; i < 16; i++) o[2 * (c0 + i)] = __uint_as_float(v[i]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty + t)) : "memory");
+      if (*(volatile int*)&abort_flag) break;
     }
   }
-  (void)nc;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32 * ((N + 31) / 32)));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
   }
 }
 
 }  // namespace
 
 // Tensor-core coarse apply; returns DWF_EINVAL when the shape is not covered
-// (nb != 32, an odd number of coarse sites, nrhs not 16, 32 or 64).
-int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, int nb, int nc,
-                    const int Lc[4], int nrhs, int* err_dev, cudaStream_t st) {
+// (nb != 32, an odd number of coarse sites, nrhs not 16, 32 or 64).  At (the
+// real-form operator) is built on first use; Bt (the arranged right-hand
+// sides) is a buffer the coarse operator keeps, grown on demand.
+int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, float** Bt,
+                    size_t* Bt_bytes, int nb, int nc, const int Lc[4], int nrhs, int* err_dev, cudaStream_t st) {
   if (nb != TC_NB || (nc & 1) || (nrhs != 16 && nrhs != 32 && nrhs != 64)) return DWF_EINVAL;
   if (!*At) {
     if (cudaMalloc(At, (size_t)nc * 9 * TC_ROWS * TC_ROWS * sizeof(float)) != cudaSuccess) {
@@ -226,21 +300,45 @@ int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32
     k_tc_arrange<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(*At, A32, nc);
     c->launches++;
   }
-  const int smem = 2 * (TC_K / 4) * TC_M * 16 + 2 * (TC_K / 4) * nrhs * 16 + 64;
-  c->launches++;
-  switch (nrhs) {
-    case 16:
-      cudaFuncSetAttribute(k_coarse_apply_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      k_coarse_apply_tc<16><<<nc / 2, TC_THREADS, smem, st>>>(out, in, *At, Lc[0], Lc[1], Lc[2], Lc[3], err_dev);
-      break;
-    case 32:
-      cudaFuncSetAttribute(k_coarse_apply_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      k_coarse_apply_tc<32><<<nc / 2, TC_THREADS, smem, st>>>(out, in, *At, Lc[0], Lc[1], Lc[2], Lc[3], err_dev);
-      break;
-    default:
-      cudaFuncSetAttribute(k_coarse_apply_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      k_coarse_apply_tc<64><<<nc / 2, TC_THREADS, smem, st>>>(out, in, *At, Lc[0], Lc[1], Lc[2], Lc[3], err_dev);
-      break;
+  const size_t bbytes = (size_t)nc * TC_ROWS * nrhs * sizeof(float);
+  if (*Bt_bytes < bbytes) {
+    if (*Bt) cudaFree(*Bt);
+    *Bt = nullptr;
+    *Bt_bytes = 0;
+    if (cudaMalloc(Bt, bbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return DWF_ENOMEM;
+    }
+    *Bt_bytes = bbytes;
   }
+  {
+    const long long n = (long long)nc * TC_NB * nrhs;
+    k_tc_arrange_in<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(*Bt, in, nc, nrhs);
+    c->launches++;
+  }
+  static int nsm_cache = 0;
+  if (!nsm_cache) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm_cache, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm_cache < 1) nsm_cache = 1;
+  }
+  const int npairs = nc / 2;
+  const int grid = npairs < nsm_cache ? npairs : nsm_cache;
+  c->launches++;
+#define DWF_TC_CASE(NV)                                                                                      \
+  case NV:                                                                                                   \
+    smem = TcStages<NV>::v * TcStages<NV>::bytes + 256;                                                      \
+    cudaFuncSetAttribute(k_coarse_apply_tc<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);          \
+    k_coarse_apply_tc<NV><<<grid, TC_THREADS + 32, smem, st>>>(out, *Bt, *At, Lc[0], Lc[1], Lc[2], Lc[3],    \
+                                                               npairs, err_dev);                             \
+    break;
+  int smem = 0;
+  switch (nrhs) {
+    DWF_TC_CASE(16)
+    DWF_TC_CASE(32)
+    DWF_TC_CASE(64)
+  }
+#undef DWF_TC_CASE
   return DWF_OK;
 }

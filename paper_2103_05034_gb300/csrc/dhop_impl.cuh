@@ -377,6 +377,47 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
   const int site = TILE ? tile_site(sl) : row_site(sl);
   const bool active = site < p.Vh;
 
+  // coordinates and the first neighbour's spinor are fetched before the
+  // link barrier, so that the two latencies overlap (inactive threads of a
+  // ragged last CTA compute addresses of site 0 and load nothing)
+  int x, y, z, t;
+  if (TILE) {
+    tile_coords(sl, x, y, z, t);
+  } else {
+    int rem = (active ? site : 0) / p.Lxh;
+    const int xh = (active ? site : 0) - rem * p.Lxh;
+    y = rem % p.L1;
+    rem /= p.L1;
+    z = rem % p.L2;
+    t = rem / p.L2;
+    x = 2 * xh + ((y + z + t + p.out_parity) & 1);
+  }
+  const S* in = (const S*)p.in + (size_t)rhs * p.rhs_stride;
+  const int Lxh = p.Lxh, L1 = p.L1, L2 = p.L2;
+  auto cbi = [&](int X, int Y, int Z, int T) { return ((T * L2 + Z) * L1 + Y) * Lxh + (X >> 1); };
+  const int xp = (x + 1 == p.L0) ? 0 : x + 1, xm = (x == 0) ? p.L0 - 1 : x - 1;
+  const int yp = (y + 1 == p.L1) ? 0 : y + 1, ym = (y == 0) ? p.L1 - 1 : y - 1;
+  const int zp = (z + 1 == p.L2) ? 0 : z + 1, zm = (z == 0) ? p.L2 - 1 : z - 1;
+  const int tp = (t + 1 == p.L3) ? 0 : t + 1, tm = (t == 0) ? p.L3 - 1 : t - 1;
+  const R sf = (R)p.sg;
+  const cpx<R>* U = sU + sl * 72;
+  in += s;
+  auto nbp = [&](int d) -> const S* {
+    int X = x, Y = y, Z = z, T = t;
+    switch (d) {
+      case 0: X = xp; break;
+      case 1: X = xm; break;
+      case 2: Y = yp; break;
+      case 3: Y = ym; break;
+      case 4: Z = zp; break;
+      case 5: Z = zm; break;
+      case 6: T = tp; break;
+      default: T = tm; break;
+    }
+    return in + (size_t)cbi(X, Y, Z, T) * (12 * LS);
+  };
+  cpx<R> ps[12];
+  if ((PF == 0 || PF == 3) && active) load_spinor<P, LS>(ps, nbp(0), 0);  // the scalar paths
   {
     const LT* gl = (const LT*)p.links + (size_t)site0 * 72;
     const int n = (TILE || RY > 1) ? SBC * 72 : min(SB, p.Vh - site0) * 72;
@@ -398,42 +439,6 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
   for (int c = 0; c < 12; c++) v[c] = cmake<R>(0, 0);
 
   if (active) {
-    int x, y, z, t;
-    if (TILE) {
-      tile_coords(sl, x, y, z, t);
-    } else {
-      int rem = site / p.Lxh;
-      const int xh = site - rem * p.Lxh;
-      y = rem % p.L1;
-      rem /= p.L1;
-      z = rem % p.L2;
-      t = rem / p.L2;
-      x = 2 * xh + ((y + z + t + p.out_parity) & 1);
-    }
-    const S* in = (const S*)p.in + (size_t)rhs * p.rhs_stride;
-    const int Lxh = p.Lxh, L1 = p.L1, L2 = p.L2;
-    auto cbi = [&](int X, int Y, int Z, int T) { return ((T * L2 + Z) * L1 + Y) * Lxh + (X >> 1); };
-    const int xp = (x + 1 == p.L0) ? 0 : x + 1, xm = (x == 0) ? p.L0 - 1 : x - 1;
-    const int yp = (y + 1 == p.L1) ? 0 : y + 1, ym = (y == 0) ? p.L1 - 1 : y - 1;
-    const int zp = (z + 1 == p.L2) ? 0 : z + 1, zm = (z == 0) ? p.L2 - 1 : z - 1;
-    const int tp = (t + 1 == p.L3) ? 0 : t + 1, tm = (t == 0) ? p.L3 - 1 : t - 1;
-    const R sf = (R)p.sg;
-    const cpx<R>* U = sU + sl * 72;
-    in += s;
-    auto nbp = [&](int d) -> const S* {
-      int X = x, Y = y, Z = z, T = t;
-      switch (d) {
-        case 0: X = xp; break;
-        case 1: X = xm; break;
-        case 2: Y = yp; break;
-        case 3: Y = ym; break;
-        case 4: Z = zp; break;
-        case 5: Z = zm; break;
-        case 6: T = tp; break;
-        default: T = tm; break;
-      }
-      return in + (size_t)cbi(X, Y, Z, T) * (12 * LS);
-    };
     if constexpr (PF == 2) {
       const float4* U4 = (const float4*)sU + sl * 72;
       const float sgf = (float)p.sg;
@@ -484,9 +489,7 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
       hop_dir<R, 3>(v, pa, U + 6 * 9, sf);
       hop_dir<R, 3>(v, pb, U + 7 * 9, -sf);
     } else {
-      cpx<R> ps[12];
-      load_spinor<P, LS>(ps, nbp(0), 0);
-      hop_dir<R, 0>(v, ps, U + 0 * 9, sf);
+      hop_dir<R, 0>(v, ps, U + 0 * 9, sf);  // ps holds neighbour 0 already
       load_spinor<P, LS>(ps, nbp(1), 0);
       hop_dir<R, 0>(v, ps, U + 1 * 9, -sf);
       load_spinor<P, LS>(ps, nbp(2), 0);
@@ -673,21 +676,26 @@ struct HopShape {
 // Tuning variants of the hopping kernel: (register cap, prefetch).  Variant 0
 // is the uncapped kernel; the autotuner (dwf_autotune) times the rest on the
 // context's lattice and keeps the fastest per precision.
-static_assert(DWF_HOP_VARIANTS == 18, "variant table below");
+static_assert(DWF_HOP_VARIANTS == 23, "variant table below");
 __host__ __device__ constexpr int hop_variant_regs(int v) {
   return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : v == 5 ? 96 : v == 6 ? 64 : v == 7 ? 80
          : v == 8 ? 64 : v == 9 ? 80 : v == 10 ? 128 : v == 11 ? 112 : v == 12 ? 96 : v == 13 ? 0
-         : v == 14 ? 64 : v == 15 ? 80 : v == 16 ? 64 : 80;
+         : v == 14 ? 64 : v == 15 ? 80 : v == 16 ? 64 : v == 17 ? 80 : v == 18 ? 56 : v == 19 ? 48 : 0;
 }
+// s-pair kernel with asynchronous shared-memory staging, neighbours in flight
+// per thread (variants 20-22)
+__host__ __device__ constexpr int hop_variant_depth(int v) { return v == 20 ? 8 : v == 21 ? 4 : v == 22 ? 2 : 0; }
 // rows of sites per CTA (variants 14-17: scalar kernel on 2 or 4 y-rows)
-__host__ __device__ constexpr int hop_variant_rows(int v) { return v >= 16 ? 4 : v >= 14 ? 2 : 1; }
+__host__ __device__ constexpr int hop_variant_rows(int v) {
+  return (v == 16 || v == 17) ? 4 : (v == 14 || v == 15) ? 2 : 1;
+}
 // 0: scalar, 1: scalar with neighbour prefetch, 2: packed FP32 (fma.rn.f32x2)
 // on (re, im) pairs, 3: scalar on 2^4-hypercube tiles (8 output sites per
 // CTA), 4: two s-slices per thread, packed FP32 over the s-pair
 // (hop_kernel_pair)
 __host__ __device__ constexpr int hop_variant_pf(int v) {
-  return v >= 14 ? 0 : v >= 10 ? 4 : v >= 8 ? 3 : v >= 6 ? 2 : v >= 4 ? 1 : 0;
-}
+  return v >= 20 ? 4 : v >= 14 ? 0 : v >= 10 ? 4 : v >= 8 ? 3 : v >= 6 ? 2 : v >= 4 ? 1 : 0;
+}  // 18, 19: scalar with 56 / 48 registers
 
 // Dynamic shared memory of one launch: links (SBC*72 complex, twice for the
 // (re,re,-im,im) packed form), or the M_ee^-1 stage (SBC*12*(LS+1) complex)
@@ -711,7 +719,11 @@ inline void launch_hop_v(const HopParams& hp, dim3 grid, cudaStream_t st) {
   const size_t ub = (size_t)SB * RY * 72 * cb * (PF == 2 || PF == 4 ? 2 : 1);
   const size_t sb = hp.inv_mode ? (size_t)SB * RY * 12 * (LSV + 1) * cb : 0;
   const size_t bytes = ub > sb ? ub : sb;
-  if constexpr (PF == 4) {
+  if constexpr (PF == 4 && hop_variant_depth(V) > 0) {
+    constexpr int D = hop_variant_depth(V);
+    hop_launch_smem<hop_kernel_pair<P, LSV, SB, hop_variant_regs(V), D>>(
+        grid, LSV / 2 * SB, pair_smem_bytes<P, LSV, SB, D>(hp.inv_mode != 0), hp, st);
+  } else if constexpr (PF == 4) {
     hop_launch_smem<hop_kernel_pair<P, LSV, SB, hop_variant_regs(V)>>(grid, LSV / 2 * SB, bytes, hp, st);
   } else {
     hop_launch_smem<hop_kernel<P, LSV, SB, hop_variant_regs(V), PF, RY>>(grid, LSV * SB * RY, bytes, hp, st);
@@ -742,6 +754,11 @@ inline int launch_hop_ls(const HopParams& hp, dim3 grid, int variant, cudaStream
       case 15: launch_hop_v<P, LSV, 15>(hp, grid, st); break;
       case 16: launch_hop_v<P, LSV, 16>(hp, grid, st); break;
       case 17: launch_hop_v<P, LSV, 17>(hp, grid, st); break;
+      case 18: launch_hop_v<P, LSV, 18>(hp, grid, st); break;
+      case 19: launch_hop_v<P, LSV, 19>(hp, grid, st); break;
+      case 20: launch_hop_v<P, LSV, 20>(hp, grid, st); break;
+      case 21: launch_hop_v<P, LSV, 21>(hp, grid, st); break;
+      case 22: launch_hop_v<P, LSV, 22>(hp, grid, st); break;
       default: launch_hop_v<P, LSV, 0>(hp, grid, st); break;
     }
   }

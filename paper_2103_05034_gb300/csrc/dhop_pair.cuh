@@ -11,6 +11,8 @@
 // broadcast pairs.  The epilogues are those of hop_kernel (same HopParams).
 #pragma once
 
+#include <type_traits>
+
 namespace dwfk {
 
 template <int P>
@@ -142,8 +144,54 @@ __device__ __forceinline__ void load_pair(f2p (&pr)[12], f2p (&pi)[12], const ty
   for (int c = 0; c < 12; c++) PairIO<P>::ld(base + c * LS, pr[c], pi[c]);
 }
 
+// Asynchronous staging (D > 0): each thread copies its own s-pair of every
+// neighbour component straight from global to shared memory (cp.async, no
+// register staging), up to D neighbours in flight per thread, and reads each
+// back when its copy group has landed.  Shared memory, not the register file,
+// then bounds the bytes in flight.  Slot layout [slot][component][thread] so
+// that a warp's reads are contiguous.
+template <int P>
+struct PairBytes {
+  static constexpr int v = P == DWF_F32 ? 16 : 8;
+};
+template <int B>
+__device__ __forceinline__ void cp_async_bytes(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (B == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+template <int P>
+__device__ __forceinline__ void read_staged(const unsigned char* slot, int nt, int tid, f2p (&pr)[12], f2p (&pi)[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; c++) {
+    const typename Prec<P>::S* e =
+        (const typename Prec<P>::S*)(slot + ((size_t)c * nt + tid) * PairBytes<P>::v);
+    PairIO<P>::ld(e, pr[c], pi[c]);
+  }
+}
+
+// Shared memory of one launch of hop_kernel_pair<.., D> (bytes).
+template <int P, int LS, int SB, int D>
+__host__ __device__ constexpr size_t pair_smem_bytes(bool inv) {
+  return (size_t)SB * 72 * 16 +
+         (D > 0 ? ((size_t)D * 12 * (LS / 2 * SB) * PairBytes<P>::v > (inv ? (size_t)SB * 12 * (LS + 1) * 8 : 0)
+                       ? (size_t)D * 12 * (LS / 2 * SB) * PairBytes<P>::v
+                       : (inv ? (size_t)SB * 12 * (LS + 1) * 8 : 0))
+                 : 0);
+}
+
 // One CTA: SB consecutive checkerboard sites x LS/2 threads (s-pairs).
-template <int P, int LS, int SB, int REGS>
+// D = 0: neighbours loaded into registers one at a time; D > 0: staged
+// asynchronously in shared memory, D neighbours deep.
+template <int P, int LS, int SB, int REGS, int D = 0>
 __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::v)) hop_kernel_pair(const HopParams p) {
   static_assert(P != DWF_F64, "packed FP32 kernel");
   static_assert(LS % 2 == 0, "Ls must be even");
@@ -152,9 +200,12 @@ __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::
   constexpr int TPS = LS / 2;
   constexpr int NT = TPS * SB;
   // dynamic shared memory: links during the hop, then (inv_mode) the
-  // M_ee^-1 stage in the same bytes (sized by the launcher)
+  // M_ee^-1 stage in the same bytes; with D > 0 the staging slots follow the
+  // links and the M_ee^-1 stage reuses the slots (sized by the launcher)
   float4* sU = (float4*)hop_dyn_smem;
-  cpx<float>* stage = (cpx<float>*)hop_dyn_smem;
+  unsigned char* stg = hop_dyn_smem + (D > 0 ? SB * 72 * 16 : 0);
+  cpx<float>* stage = (cpx<float>*)stg;
+  constexpr int SLOT = 12 * NT * PairBytes<P>::v;
   __shared__ double red[NT / 32 + 1];
 
   const int tid = threadIdx.x;
@@ -182,6 +233,52 @@ __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::
   const int site = site0 + sl;
   const bool active = site < p.Vh;
 
+  // coordinates and the first neighbour are fetched before the link barrier
+  int rem = (active ? site : 0) / p.Lxh;
+  const int xh = (active ? site : 0) - rem * p.Lxh;
+  const int y = rem % p.L1;
+  rem /= p.L1;
+  const int z = rem % p.L2;
+  const int t = rem / p.L2;
+  const int x = 2 * xh + ((y + z + t + p.out_parity) & 1);
+  const S* in = (const S*)p.in + (size_t)rhs * p.rhs_stride + s0;
+  const int Lxh = p.Lxh, L1 = p.L1, L2 = p.L2;
+  auto cbi = [&](int X, int Y, int Z, int T) { return ((T * L2 + Z) * L1 + Y) * Lxh + (X >> 1); };
+  const int xp = (x + 1 == p.L0) ? 0 : x + 1, xm = (x == 0) ? p.L0 - 1 : x - 1;
+  const int yp = (y + 1 == p.L1) ? 0 : y + 1, ym = (y == 0) ? p.L1 - 1 : y - 1;
+  const int zp = (z + 1 == p.L2) ? 0 : z + 1, zm = (z == 0) ? p.L2 - 1 : z - 1;
+  const int tp = (t + 1 == p.L3) ? 0 : t + 1, tm = (t == 0) ? p.L3 - 1 : t - 1;
+  auto nbp = [&](int d) -> const S* {
+    int X = x, Y = y, Z = z, T = t;
+    switch (d) {
+      case 0: X = xp; break;
+      case 1: X = xm; break;
+      case 2: Y = yp; break;
+      case 3: Y = ym; break;
+      case 4: Z = zp; break;
+      case 5: Z = zm; break;
+      case 6: T = tp; break;
+      default: T = tm; break;
+    }
+    return in + (size_t)cbi(X, Y, Z, T) * (12 * LS);
+  };
+  f2p pr[12], pi[12];
+  auto issue = [&](int d) {  // D > 0: one copy group per neighbour
+    unsigned char* slot = stg + (d % (D > 0 ? D : 1)) * SLOT;
+    const S* src = nbp(d);
+#pragma unroll
+    for (int c = 0; c < 12; c++)
+      cp_async_bytes<PairBytes<P>::v>(slot + ((size_t)c * NT + tid) * PairBytes<P>::v, src + c * LS);
+    cp_async_commit();
+  };
+  if (active) {
+    if constexpr (D > 0) {
+#pragma unroll
+      for (int d = 0; d < (D < 8 ? D : 8); d++) issue(d);
+    } else {
+      load_pair<P, LS>(pr, pi, nbp(0));
+    }
+  }
   {
     const LT* gl = (const LT*)p.links + (size_t)site0 * 72;
     const int n = min(SB, p.Vh - site0) * 72;
@@ -197,54 +294,48 @@ __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::
   for (int c = 0; c < 12; c++) vr[c] = vi[c] = 0ull;
 
   if (active) {
-    int rem = site / p.Lxh;
-    const int xh = site - rem * p.Lxh;
-    const int y = rem % p.L1;
-    rem /= p.L1;
-    const int z = rem % p.L2;
-    const int t = rem / p.L2;
-    const int x = 2 * xh + ((y + z + t + p.out_parity) & 1);
-    const S* in = (const S*)p.in + (size_t)rhs * p.rhs_stride + s0;
-    const int Lxh = p.Lxh, L1 = p.L1, L2 = p.L2;
-    auto cbi = [&](int X, int Y, int Z, int T) { return ((T * L2 + Z) * L1 + Y) * Lxh + (X >> 1); };
-    const int xp = (x + 1 == p.L0) ? 0 : x + 1, xm = (x == 0) ? p.L0 - 1 : x - 1;
-    const int yp = (y + 1 == p.L1) ? 0 : y + 1, ym = (y == 0) ? p.L1 - 1 : y - 1;
-    const int zp = (z + 1 == p.L2) ? 0 : z + 1, zm = (z == 0) ? p.L2 - 1 : z - 1;
-    const int tp = (t + 1 == p.L3) ? 0 : t + 1, tm = (t == 0) ? p.L3 - 1 : t - 1;
-    auto nbp = [&](int d) -> const S* {
-      int X = x, Y = y, Z = z, T = t;
-      switch (d) {
-        case 0: X = xp; break;
-        case 1: X = xm; break;
-        case 2: Y = yp; break;
-        case 3: Y = ym; break;
-        case 4: Z = zp; break;
-        case 5: Z = zm; break;
-        case 6: T = tp; break;
-        default: T = tm; break;
-      }
-      return in + (size_t)cbi(X, Y, Z, T) * (12 * LS);
-    };
     const float4* U = sU + sl * 72;
     const float sgf = p.sg;
     const f2p SG = pk2(sgf, sgf), NSG = pk2(-sgf, -sgf), NEG = pk2(-1.f, -1.f);
-    f2p pr[12], pi[12];
-    load_pair<P, LS>(pr, pi, nbp(0));
-    hop_dir_pair<0>(vr, vi, pr, pi, U + 0 * 9, SG, NSG, NEG);
-    load_pair<P, LS>(pr, pi, nbp(1));
-    hop_dir_pair<0>(vr, vi, pr, pi, U + 1 * 9, NSG, SG, NEG);
-    load_pair<P, LS>(pr, pi, nbp(2));
-    hop_dir_pair<1>(vr, vi, pr, pi, U + 2 * 9, SG, NSG, NEG);
-    load_pair<P, LS>(pr, pi, nbp(3));
-    hop_dir_pair<1>(vr, vi, pr, pi, U + 3 * 9, NSG, SG, NEG);
-    load_pair<P, LS>(pr, pi, nbp(4));
-    hop_dir_pair<2>(vr, vi, pr, pi, U + 4 * 9, SG, NSG, NEG);
-    load_pair<P, LS>(pr, pi, nbp(5));
-    hop_dir_pair<2>(vr, vi, pr, pi, U + 5 * 9, NSG, SG, NEG);
-    load_pair<P, LS>(pr, pi, nbp(6));
-    hop_dir_pair<3>(vr, vi, pr, pi, U + 6 * 9, SG, NSG, NEG);
-    load_pair<P, LS>(pr, pi, nbp(7));
-    hop_dir_pair<3>(vr, vi, pr, pi, U + 7 * 9, NSG, SG, NEG);
+    if constexpr (D > 0) {
+      // neighbour d is in slot d % D; before reading it, at most
+      // min(7, d + D - 1) - d later groups may still be in flight
+      auto step = [&](auto dc) {
+        constexpr int d = decltype(dc)::value;
+        constexpr int later = (d + D - 1 < 7 ? d + D - 1 : 7) - d;
+        cp_async_wait<later>();
+        read_staged<P>(stg + (d % D) * SLOT, NT, tid, pr, pi);
+        if (d & 1)
+          hop_dir_pair<d / 2>(vr, vi, pr, pi, U + d * 9, NSG, SG, NEG);
+        else
+          hop_dir_pair<d / 2>(vr, vi, pr, pi, U + d * 9, SG, NSG, NEG);
+        if (d + D < 8) issue(d + D);  // the slot's values are consumed
+      };
+      step(std::integral_constant<int, 0>());
+      step(std::integral_constant<int, 1>());
+      step(std::integral_constant<int, 2>());
+      step(std::integral_constant<int, 3>());
+      step(std::integral_constant<int, 4>());
+      step(std::integral_constant<int, 5>());
+      step(std::integral_constant<int, 6>());
+      step(std::integral_constant<int, 7>());
+    } else {
+      hop_dir_pair<0>(vr, vi, pr, pi, U + 0 * 9, SG, NSG, NEG);  // neighbour 0 loaded above
+      load_pair<P, LS>(pr, pi, nbp(1));
+      hop_dir_pair<0>(vr, vi, pr, pi, U + 1 * 9, NSG, SG, NEG);
+      load_pair<P, LS>(pr, pi, nbp(2));
+      hop_dir_pair<1>(vr, vi, pr, pi, U + 2 * 9, SG, NSG, NEG);
+      load_pair<P, LS>(pr, pi, nbp(3));
+      hop_dir_pair<1>(vr, vi, pr, pi, U + 3 * 9, NSG, SG, NEG);
+      load_pair<P, LS>(pr, pi, nbp(4));
+      hop_dir_pair<2>(vr, vi, pr, pi, U + 4 * 9, SG, NSG, NEG);
+      load_pair<P, LS>(pr, pi, nbp(5));
+      hop_dir_pair<2>(vr, vi, pr, pi, U + 5 * 9, NSG, SG, NEG);
+      load_pair<P, LS>(pr, pi, nbp(6));
+      hop_dir_pair<3>(vr, vi, pr, pi, U + 6 * 9, SG, NSG, NEG);
+      load_pair<P, LS>(pr, pi, nbp(7));
+      hop_dir_pair<3>(vr, vi, pr, pi, U + 7 * 9, NSG, SG, NEG);
+    }
 
     const float al = (float)p.alpha;
     const f2p AL = pk2(al, al);

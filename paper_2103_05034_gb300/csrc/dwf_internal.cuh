@@ -12,6 +12,7 @@
 
 #define DWF_MAX_RHS 64
 #define DWF_NWS 32  // workspace slots
+#define CG_SMALL_BYTES 384  // status and barrier counters of the persistent coarse CG
 
 // ------------------------------------------------------------------ complex helpers
 template <class R>

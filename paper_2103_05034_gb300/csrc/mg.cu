@@ -20,16 +20,20 @@ struct dwf_coarse {
   double2* A64;  // [nc][9][nb][nb]
   float2* A32;   // same layout, FP32
   float* At;     // tensor-core copy (real form, TF32, K-major), built on first use
+  float* Bt;     // tensor-core right-hand sides (real form, TF32), per apply
+  size_t Bt_bytes;
   int* err;      // device error flag of the tensor-core kernel
   void* ws[6];
   size_t ws_bytes[6];
+  int* cg_acc;   // when set: coarse CG runs without host synchronisation and
+                 // accumulates [iterations, error] here (graph capture)
 };
 
-int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, int nb, int nc,
-                    const int Lc[4], int nrhs, int* err_dev, cudaStream_t st);
+int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, float** Bt,
+                    size_t* Bt_bytes, int nb, int nc, const int Lc[4], int nrhs, int* err_dev, cudaStream_t st);
 int coarse_cg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float2* A, const int Lc[4], int nc,
                          int nb, double tol, int maxiter, float2* work, double* part, int part_cap,
-                         int* dev_small, int* iters, cudaStream_t st);
+                         int* dev_small, int* acc, int* iters, cudaStream_t st);
 
 struct dwf_mg {
   dwf_ctx* ctx;
@@ -241,8 +245,13 @@ int coarse_ws(dwf_coarse* C, int slot, size_t bytes, void** out) {
 int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cudaStream_t st) {
   const long long n = (long long)C->g.nc * C->nb * nrhs;
   C->ctx->launches++;
-  dwfmg::k_coarse_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1],
-                                                                     C->g.Lc[2], C->g.Lc[3], C->nb, nrhs);
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (C->nb == 32)
+    dwfmg::k_coarse_apply<32><<<blocks, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2],
+                                                      C->g.Lc[3], C->nb, nrhs);
+  else
+    dwfmg::k_coarse_apply<0><<<blocks, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2],
+                                                     C->g.Lc[3], C->nb, nrhs);
   return DWF_OK;
 }
 
@@ -255,10 +264,10 @@ int coarse_cg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxite
   void *work, *part, *small;
   int rc2;
   if ((rc2 = coarse_ws(C, 0, 4 * n * sizeof(float2), &work)) || (rc2 = coarse_ws(C, 1, part_cap * sizeof(double), &part)) ||
-      (rc2 = coarse_ws(C, 2, 4 * sizeof(int), &small)))
+      (rc2 = coarse_ws(C, 2, CG_SMALL_BYTES, &small)))
     return rc2;
   return coarse_cg_persistent(C->ctx, e, rc, C->A32, C->g.Lc, C->g.nc, C->nb, tol, maxiter, (float2*)work,
-                              (double*)part, part_cap, (int*)small, iters, st);
+                              (double*)part, part_cap, (int*)small, C->cg_acc, iters, st);
 }
 
 }  // namespace
@@ -463,6 +472,7 @@ extern "C" int coarse_destroy(dwf_coarse* C) {
   if (C->A64) cudaFree(C->A64);
   if (C->A32) cudaFree(C->A32);
   if (C->At) cudaFree(C->At);
+  if (C->Bt) cudaFree(C->Bt);
   if (C->err) cudaFree(C->err);
   for (int i = 0; i < 6; i++)
     if (C->ws[i]) cudaFree(C->ws[i]);
@@ -505,7 +515,7 @@ extern "C" int coarse_apply(dwf_coarse* C, void* out, const void* in, int nrhs, 
     }
   }
   DWF_CUDA(c, cudaMemsetAsync(C->err, 0, sizeof(int), st));
-  int rc = coarse_apply_tc(c, (float2*)out, (const float2*)in, C->A32, &C->At, C->nb, C->g.nc, C->g.Lc, nrhs,
+  int rc = coarse_apply_tc(c, (float2*)out, (const float2*)in, C->A32, &C->At, &C->Bt, &C->Bt_bytes, C->nb, C->g.nc, C->g.Lc, nrhs,
                            C->err, st);
   if (rc == DWF_EINVAL)
     return dwf_fail(c, rc, "tensor-core coarse apply needs nb = 32, an even number of coarse sites, nrhs 16/32/64");
@@ -663,6 +673,113 @@ int vcycle(dwf_mg* G, void* x, const void* r0, cudaStream_t st, double* nH, int*
   rc = smoother(G, s2, rr, st, nH);
   if (rc) return rc;
   return blas_axpby(c, 1.0, s2, DWF_F32, 1.0, x, DWF_F32, n, st);  // x3
+}
+
+// One V(1,1) application replayed from a CUDA graph.  Its launch sequence
+// (the two smoothers' hopping and Chebyshev launches, the restriction, one
+// cooperative coarse-CG launch, the prolongation) is captured once per solve
+// on a private stream, after a plain warm-up V-cycle has sized every
+// workspace, and replayed for each pGCR direction; the residual is copied
+// into, and the direction out of, two fixed buffers.  The coarse CG then runs
+// without host synchronisation and reports its iteration count and any error
+// through a device accumulator that the solve reads at its next
+// synchronisation.  The graph lives for one mg_solve call, so no workspace
+// can move under it.
+struct VGraph {
+  dwf_ctx* c = nullptr;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* in = nullptr;
+  void* out = nullptr;
+  int* acc = nullptr;    // device [coarse iterations, error bits]
+  int* acc_h = nullptr;  // pinned mirror
+  int64_t launches = 0;  // kernel launches per replay
+  double nH = 0;         // H_DW applications per replay
+  int state = 0;         // 0: not built, 1: ready, -1: not available
+  int replays = 0;
+  ~VGraph() {
+    if (gs) cudaStreamSynchronize(gs);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (gs) cudaStreamDestroy(gs);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+    if (acc) cudaFree(acc);
+    if (acc_h) cudaFreeHost(acc_h);
+  }
+};
+
+int vgraph_build(VGraph& V, dwf_mg* G, cudaStream_t st) {
+  dwf_ctx* c = G->ctx;
+  V.c = c;
+  V.state = -1;
+  const size_t bytes = (size_t)full_elems(c) * sizeof(float2);
+  if (cudaStreamCreateWithFlags(&V.gs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&V.e0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&V.e1, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&V.in, bytes) != cudaSuccess || cudaMalloc(&V.out, bytes) != cudaSuccess ||
+      cudaMalloc(&V.acc, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&V.acc_h, 2 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return DWF_OK;  // plain launches
+  }
+  V.acc_h[0] = V.acc_h[1] = 0;
+  DWF_CUDA(c, cudaMemsetAsync(V.acc, 0, 2 * sizeof(int), st));
+  DWF_CUDA(c, cudaStreamSynchronize(st));
+  const int64_t l0 = c->launches;
+  double nH = 0;
+  int nco = 0;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(V.gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return DWF_OK;
+  }
+  G->coarse->cg_acc = V.acc;
+  const std::string err_before = c->err;
+  const int rc = vcycle(G, V.out, V.in, V.gs, &nH, &nco);
+  G->coarse->cg_acc = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(V.gs, &graph);
+  V.launches = c->launches - l0;
+  c->launches = l0;
+  if (rc || ec != cudaSuccess || !graph || cudaGraphInstantiate(&V.exec, graph, 0) != cudaSuccess) {
+    // capture not possible (e.g. a launch form the driver cannot record):
+    // the solve continues with plain launches
+    if (graph) cudaGraphDestroy(graph);
+    V.exec = nullptr;
+    c->err = err_before;
+    cudaGetLastError();
+    return DWF_OK;
+  }
+  cudaGraphDestroy(graph);
+  V.nH = nH;
+  V.state = 1;
+  return DWF_OK;
+}
+
+int vgraph_run(VGraph& V, void* z, const void* r, cudaStream_t st, double* nH) {
+  dwf_ctx* c = V.c;
+  const size_t bytes = (size_t)full_elems(c) * sizeof(float2);
+  DWF_CUDA(c, cudaMemcpyAsync(V.in, r, bytes, cudaMemcpyDeviceToDevice, st));
+  DWF_CUDA(c, cudaEventRecord(V.e0, st));
+  DWF_CUDA(c, cudaStreamWaitEvent(V.gs, V.e0, 0));
+  DWF_CUDA(c, cudaGraphLaunch(V.exec, V.gs));
+  DWF_CUDA(c, cudaEventRecord(V.e1, V.gs));
+  DWF_CUDA(c, cudaStreamWaitEvent(st, V.e1, 0));
+  DWF_CUDA(c, cudaMemcpyAsync(z, V.out, bytes, cudaMemcpyDeviceToDevice, st));
+  DWF_CUDA(c, cudaMemcpyAsync(V.acc_h, V.acc, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  c->launches += V.launches;
+  *nH += V.nH;
+  V.replays++;
+  return DWF_OK;
+}
+
+// Error bits of the graph's coarse CG, valid after a synchronisation.
+int vgraph_check(const VGraph& V) {
+  if (V.state != 1 || !V.acc_h[1]) return DWF_OK;
+  return dwf_fail(V.c, (V.acc_h[1] & 1) ? DWF_ETIMEOUT : DWF_ENAN,
+                  (V.acc_h[1] & 1) ? "coarse CG grid barrier timed out" : "NaN in coarse solve");
 }
 
 }  // namespace
@@ -857,6 +974,7 @@ extern "C" int mg_solve(dwf_mg* G, void* x, const void* b, double tol, dwf_solve
   const int maxit = G->p.maxiter > 0 ? G->p.maxiter : 1000;
   bool done = false;
   std::vector<double> wnorm(nk);
+  VGraph V;
   while (!done && it < maxit) {
     rc = blas_copy(c, r32, DWF_F32, r64, DWF_F64, n, st);
     if (rc) return rc;
@@ -864,7 +982,12 @@ extern "C" int mg_solve(dwf_mg* G, void* x, const void* b, double tol, dwf_solve
     for (; k < nk && it < maxit; k++) {
       float2* z = (float2*)zs + (size_t)k * n;
       float2* w = (float2*)wsv + (size_t)k * n;
-      rc = vcycle(G, z, r32, st, &nH, &ncoarse);
+      if (V.state == 1) {
+        rc = vgraph_run(V, z, r32, st, &nH);
+      } else {
+        rc = vcycle(G, z, r32, st, &nH, &ncoarse);
+        if (!rc && V.state == 0 && !G->p.no_graph) rc = vgraph_build(V, G, st);
+      }
       if (rc) return rc;
       rc = ddw_apply(c, w, z, mf, 0, 1, DWF_F32, 1, st);
       if (rc) return rc;
@@ -906,6 +1029,8 @@ extern "C" int mg_solve(dwf_mg* G, void* x, const void* b, double tol, dwf_solve
       if (rc) return rc;
       rc = read_scalars(c, S_TMP2, 1, st);
       if (rc) return rc;
+      rc = vgraph_check(V);
+      if (rc) return rc;
       it++;
       if (sqrt(c->hscal[S_TMP2]) / bnorm <= tol) {
         k++;
@@ -930,8 +1055,11 @@ extern "C" int mg_solve(dwf_mg* G, void* x, const void* b, double tol, dwf_solve
   }
   if (host_x) DWF_CUDA(c, cudaMemcpyAsync(x, dx, n * 16, cudaMemcpyDeviceToHost, st));
   DWF_CUDA(c, cudaStreamSynchronize(st));
+  rc = vgraph_check(V);
+  if (rc) return rc;
   S.iterations = it;
-  S.coarse_iterations = ncoarse;
+  S.coarse_iterations = ncoarse + (V.state == 1 ? V.acc_h[0] : 0);
+  S.graph_replays = V.replays;
   S.fine_matmuls = nH;
   S.true_residual = res;
   S.seconds = timer.sec();

@@ -326,8 +326,14 @@ __global__ void __launch_bounds__(128) k_face_hop(typename Prec<P>::S* out, cons
 
 // Coarse 9-point stencil on CUDA cores: out[x][j][r] = sum_d sum_k
 // A[x][d][j][k] in[x+d][k][r]; vectors [nc][nb][nrhs] complex FP32.
-static __global__ void __launch_bounds__(256) k_coarse_apply(float2* out, const float2* in, const float2* A,
-                                                      int Lc0, int Lc1, int Lc2, int Lc3, int nb, int nrhs) {
+// One thread per output (site x, row j, right-hand side r); threads of a warp
+// share x and j (broadcast A element) and read consecutive r (coalesced).
+// NB > 0 fixes nb at compile time so that the k loop unrolls and its loads
+// are all in flight together.
+template <int NB>
+__global__ void __launch_bounds__(256) k_coarse_apply(float2* out, const float2* in, const float2* A, int Lc0,
+                                                      int Lc1, int Lc2, int Lc3, int nb_rt, int nrhs) {
+  const int nb = NB > 0 ? NB : nb_rt;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int nc = Lc0 * Lc1 * Lc2 * Lc3;
   if (e >= (long long)nc * nb * nrhs) return;
@@ -336,21 +342,37 @@ static __global__ void __launch_bounds__(256) k_coarse_apply(float2* out, const 
   const int j = (int)(t % nb);
   const int x = (int)(t / nb);
   const int Lc[4] = {Lc0, Lc1, Lc2, Lc3};
-  float re = 0.f, im = 0.f;
+  float re = 0.f, im = 0.f, re2 = 0.f, im2 = 0.f;
   for (int d = 0; d < 9; d++) {
     const int y = coarse_nbr(Lc, x, d);
     const float2* Ad = A + (((long long)x * 9 + d) * nb + j) * nb;
     const float2* v = in + (long long)y * nb * nrhs + r;
-    for (int k = 0; k < nb; k++) {
-      const float2 a = Ad[k];
-      const float2 b = v[(long long)k * nrhs];
+#pragma unroll
+    for (int k = 0; k < (NB > 0 ? NB : 1); k += 2) {
+      if (NB == 0) break;
+      const float2 a = __ldg(Ad + k), a2 = __ldg(Ad + k + 1);
+      const float2 b = __ldg(v + (long long)k * nrhs), b2 = __ldg(v + (long long)(k + 1) * nrhs);
       re = fmaf(a.x, b.x, re);
       re = fmaf(-a.y, b.y, re);
       im = fmaf(a.x, b.y, im);
       im = fmaf(a.y, b.x, im);
+      re2 = fmaf(a2.x, b2.x, re2);
+      re2 = fmaf(-a2.y, b2.y, re2);
+      im2 = fmaf(a2.x, b2.y, im2);
+      im2 = fmaf(a2.y, b2.x, im2);
+    }
+    if (NB == 0) {
+      for (int k = 0; k < nb; k++) {
+        const float2 a = Ad[k];
+        const float2 b = v[(long long)k * nrhs];
+        re = fmaf(a.x, b.x, re);
+        re = fmaf(-a.y, b.y, re);
+        im = fmaf(a.x, b.y, im);
+        im = fmaf(a.y, b.x, im);
+      }
     }
   }
-  out[e] = make_float2(re, im);
+  out[e] = make_float2(re + re2, im + im2);
 }
 
 }  // namespace dwfmg

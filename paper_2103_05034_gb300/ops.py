@@ -254,13 +254,14 @@ def dwf_prolong(ctx, out, inp, basis, nb, block, nrhs=1, accumulate=0):
 
 def mg_params(block, nbasis, mf, *, subspace_mode=_lib.SUBSPACE_BATCH, lambda_lo=0.02,
               lambda_max=60.0, filter_order=60, delta=100, smooth=(0.5, 60.0, 12),
-              coarse_tol=0.02, coarse_maxiter=500, nkrylov=8, maxiter=1000):
+              coarse_tol=0.02, coarse_maxiter=500, nkrylov=8, maxiter=1000, graph=True):
     p = _lib.MGParams()
     p.block = (C.c_int * 4)(*block)
     p.nbasis, p.subspace_mode, p.mf = nbasis, subspace_mode, mf
     p.lambda_lo, p.lambda_max, p.filter_order, p.delta = lambda_lo, lambda_max, filter_order, delta
     p.smooth_lo, p.smooth_hi, p.smooth_order = smooth
     p.coarse_tol, p.coarse_maxiter, p.nkrylov, p.maxiter = coarse_tol, coarse_maxiter, nkrylov, maxiter
+    p.no_graph = 0 if graph else 1
     return p
 
 

@@ -206,7 +206,7 @@ def test_every_hop_variant_matches_oracle(prec, variant):
     reproduces the oracle, plain and with the fused M_ee / M_ee^-1 epilogues
     of M_pc."""
     from paper_2103_05034_gb300 import layout
-    rows = 4 if variant >= 16 else 2 if variant >= 14 else 1  # CTAs over several y-rows
+    rows = 4 if variant in (16, 17) else 2 if variant in (14, 15) else 1  # CTAs over several y-rows
     cases = [((16, 4, 2, 2), 16), ((16, 4, 2, 2), 24)]  # x segments of 8 sites, 4 rows
     if rows == 1:
         cases += [((4, 4, 2, 2), 16), ((2, 4, 2, 2), 24)]

@@ -283,14 +283,41 @@ def test_mg_solve(mg_case, host):
     assert st["coarse_iterations"] > 0 and st["fine_matmuls"] > 0
 
 
-@pytest.mark.parametrize("nrhs", [16, 32, 64])
-def test_coarse_apply_tensor_cores(nrhs):
+def test_mg_solve_graph_replay_is_identical(mg_case):
+    """The V-cycle replayed from a CUDA graph runs the same kernels on the
+    same data as plain launches: same outer and coarse iteration counts and
+    a bit-identical solution; the graph solve reports its replays."""
+    L, Ls, mf, block, nb, U, ctx, etas, p, G = mg_case
+    b = full_dev(synth.gaussian_spinor(L, Ls, 73), L, F64)
+    runs = []
+    for graph in (True, False):
+        pg = ops.mg_params(block, nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=0.5, lambda_max=70.0,
+                           filter_order=4, smooth=(0.5, 60.0, 6), coarse_tol=0.02, coarse_maxiter=500,
+                           nkrylov=8, maxiter=200, graph=graph)
+        Gg = ops.MG(ctx, pg, fulls_dev(etas, L, F64))
+        x = torch.zeros_like(b)
+        st = ops.mg_solve(Gg, x, b, 1e-8)
+        runs.append((st, x.clone()))
+        Gg.close()
+    (sg, xg), (sp, xp) = runs
+    assert sg["graph_replays"] == sg["iterations"] - 1 and sg["graph_replays"] > 0
+    assert sp["graph_replays"] == 0
+    assert (sg["iterations"], sg["coarse_iterations"]) == (sp["iterations"], sp["coarse_iterations"])
+    assert sg["fine_matmuls"] == sp["fine_matmuls"]
+    assert torch.equal(xg, xp)
+
+
+@pytest.mark.parametrize("nrhs,L", [(16, (4, 4, 4, 8)), (32, (4, 4, 4, 8)), (64, (4, 4, 4, 8)),
+                                     (32, (8, 8, 16, 16))])
+def test_coarse_apply_tensor_cores(nrhs, L):
     """tcgen05 TF32 coarse stencil (nb = 32) against the oracle apply of the
     exported FP64 operator.  TF32 rounds each input to 11 significant bits
     (relative error <= 2^-11 = 4.9e-4); with FP32 accumulation of 576 terms of
-    random sign the norm-wise error is ~1e-3, so the bound is 3e-3."""
+    random sign the norm-wise error is ~1e-3, so the bound is 3e-3.  The
+    8x8x16x16 lattice has 1024 coarse sites = 512 site pairs, more than one
+    pair per CTA of the persistent kernel (both accumulators reused)."""
     from paper_2103_05034_gb300._lib import TF32
-    L, Ls, mf, block, nb = (4, 4, 4, 8), 4, 0.1, (2, 2, 2, 2), 32
+    Ls, mf, block, nb = 4, 0.1, (2, 2, 2, 2), 32
     U = synth.random_gauge(L, 0.5, 44)
     ctx = ops.Context(L, Ls, M5, U)
     vecs = [coarse.chiral_project(synth.gaussian_spinor(L, Ls, 300 + i), 1 if i < nb // 2 else -1)
