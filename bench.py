@@ -398,6 +398,24 @@ def run_ours(args):
                       "true_residual": s0["true_residual"], "fine_matmuls": s0["fine_matmuls"],
                       "seconds": t_max / args.steps, "wall_seconds_all_steps": t_wall},
         }
+        try:  # the same solve with FP16-storage inner vectors (scaled residual)
+            from paper_2103_05034_gb300._lib import SOLVE_MIXED_F16
+            xd.zero_()
+            ops.rbcg_solve(ctx, xd, bd, mf, args.tol, 100000, SOLVE_MIXED_F16)  # warm
+            xd.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s16 = ops.rbcg_solve(ctx, xd, bd, mf, args.tol, 100000, SOLVE_MIXED_F16)
+            torch.cuda.synchronize()
+            line["solve_mixed_f16"] = {"seconds": time.perf_counter() - t0, "iterations": s16["iterations"],
+                                       "reliable_updates": s16["reliable_updates"],
+                                       "true_residual": s16["true_residual"]}
+        except Exception as e:
+            line["solve_mixed_f16"] = {"error": str(e)}
+        try:  # the tensor-core coarse stencil (multi-RHS), measured beside the solve
+            line["coarse_apply_tc"] = coarse_apply_measure(ctx, w, "tf32", 3, 20)
+        except Exception as e:
+            line["coarse_apply_tc"] = {"error": str(e)}
         if args.mg_compare:
             try:
                 line["mg_vs_fp64"] = mg_vs_fp64(ctx, w, b, bd, args.tol)
@@ -414,19 +432,17 @@ def run_ours(args):
     return 0
 
 
-def run_coarse_kernel(args):
-    """`--kernel coarse_tf32|coarse_f32`: the little Dirac operator of H_DW on
-    the workload's lattice (4^4 x Ls blocks, 32 basis vectors from Gaussians,
-    chirality-projected and block-orthonormalised) applied to 32 right-hand
-    sides, warmup + steps launches, L2 flushed before each timed launch."""
+def coarse_apply_measure(ctx, w, prec_name, warmup, steps):
+    """The little Dirac operator of H_DW on the context's lattice (4^4 x Ls
+    blocks, 32 basis vectors from Gaussians, chirality-projected and
+    block-orthonormalised) applied to 32 right-hand sides; median CUDA-event
+    time of `steps` calls with L2 flushed before each."""
     import torch
 
     from paper_2103_05034_gb300 import ops
-    from paper_2103_05034_gb300._lib import F32, F64, TF32
+    from paper_2103_05034_gb300._lib import F32, TF32
 
-    w, U, _ = build_workload(args.workload, 0)
-    L, Ls, mf = w["L"], w["Ls"], w["mf"]
-    ctx = ops.Context(L, Ls, w["M5"], U)
+    mf = w["mf"]
     nb, nrhs, block = 32, 32, (4, 4, 4, 4)
     nfull = 2 * ctx.half_numel()  # reals of one full FP64 field
     gen = torch.Generator(device="cuda").manual_seed(synth.SEED_BASIS)
@@ -439,14 +455,14 @@ def run_coarse_kernel(args):
     ops.block_orthonormalise(ctx, basis, nb, nb // 2, block)
     Cc = ops.coarse_build(ctx, basis, nb, nb // 2, block, mf)
     del basis
-    prec = {"tf32": TF32, "f32": F32}[args.kernel.split("_")[1]]
+    prec = {"tf32": TF32, "f32": F32}[prec_name]
     inp = torch.randn(2 * Cc.nc * nb * nrhs, generator=gen, device="cuda", dtype=torch.float32)
     out = torch.zeros_like(inp)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         ops.coarse_apply(Cc, out, inp, nrhs, prec)
     ts = []
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(float(k))
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -457,11 +473,230 @@ def run_coarse_kernel(args):
     ms = float(np.median(ts))
     flop = 8.0 * 9 * nb * nb * nrhs * Cc.nc
     abytes = Cc.nc * 9 * nb * nb * 8 + 2 * Cc.nc * nb * nrhs * 8  # FP32 operator + in/out vectors
-    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "coarse_sites": Cc.nc, "nbasis": nb,
-                      "nrhs": nrhs, "ms_median": ms, "tflops": flop / ms / 1e9,
-                      "GBs_algorithmic": abytes / ms / 1e6, "flop_per_launch": flop,
-                      "bytes_per_launch": abytes}))
+    res = {"kernel": f"coarse_{prec_name}", "coarse_sites": Cc.nc, "nbasis": nb, "nrhs": nrhs,
+           "ms_median": ms, "tflops": flop / ms / 1e9, "GBs_algorithmic": abytes / ms / 1e6,
+           "flop_per_launch": flop, "bytes_per_launch": abytes}
+    peaks, kind = measured_peaks()
+    if prec_name == "tf32" and "bf16_tflops" in peaks:
+        tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # nominal dense TF32 / BF16 ratio
+        res["frac_of_tf32_peak"] = res["tflops"] / tf32_peak
+        res["tf32_peak_tflops"] = tf32_peak
+        res["peak_source"] = f"{kind} bf16_tflops x 1.1/2.25 (nominal TF32/BF16 dense ratio)"
+    res["frac_of_hbm"] = res["GBs_algorithmic"] / peaks["hbm_gbs"]
     Cc.close()
+    return res
+
+
+def run_coarse_kernel(args):
+    """`--kernel coarse_tf32|coarse_f32`: the coarse stencil alone (see
+    coarse_apply_measure), warmup + steps calls."""
+    from paper_2103_05034_gb300 import ops
+
+    w, U, _ = build_workload(args.workload, 0)
+    ctx = ops.Context(w["L"], w["Ls"], w["M5"], U)
+    res = coarse_apply_measure(ctx, w, args.kernel.split("_")[1], args.warmup, args.steps)
+    res["workload"] = args.workload
+    print(json.dumps(res))
+    ctx.close()
+
+
+def run_rows(args):
+    """`--rows`: every step of the hot path measured alone on the workload
+    (CUDA events, L2 flushed before each timed call, median), with its
+    algorithmic bytes or flops and the fraction of the measured peak, and the
+    oracle's time for the same step on the small 4^4 x 8 lattice beside it.
+    One JSON line per step."""
+    import torch
+
+    from oracle import cheby as o_cheby
+    from oracle import dwf as o_dwf
+    from paper_2103_05034_gb300 import layout, ops
+    from paper_2103_05034_gb300._lib import F16S, F32, F64, SOLVE_MIXED_F32, SUBSPACE_BATCH
+
+    w, U, b = build_workload(args.workload, 0)
+    L, Ls, M5, mf = w["L"], w["Ls"], w["M5"], w["mf"]
+    ctx = ops.Context(L, Ls, M5, U)
+    ops.dwf_autotune(ctx, F32, 10)
+    ops.dwf_autotune(ctx, F16S, 10)
+    peaks, kind = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    fp64_peak = 1.25  # TFLOP/s, nominal dense FP64 of GB300 (no measured figure)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(synth.SEED_SOURCE)
+    nh = ctx.half_numel()  # reals of one half field
+
+    def field(n, dtype):
+        return torch.randn(n, generator=gen, device="cuda", dtype=torch.float32).to(dtype)
+
+    def timed(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            z.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(z))
+        return float(np.median(ts))
+
+    def hop_bytes(fn):
+        ops.dwf_reset_counters(ctx)
+        fn()
+        torch.cuda.synchronize()
+        return ops.dwf_counters(ctx)[1]
+
+    # CPU baseline beside each step: the oracle (FP64 numpy, one process) on the
+    # small 4^4 x 8 lattice, in ns per 5D site
+    sw = synth.WORKLOADS["dwf_4x4x4x4_ls8"]
+    sL, sLs = sw["L"], sw["Ls"]
+    sU = synth.random_gauge(sL, sw["eps"], synth.SEED_GAUGE)
+    spsi = synth.gaussian_spinor(sL, sLs, synth.SEED_SOURCE)
+    s5 = int(np.prod(sL)) * sLs
+
+    def oracle_ns_per_site(fn, reps=3):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return (time.perf_counter() - t0) / reps / s5 * 1e9
+
+    rows = []
+
+    def emit(row, entry, ms, work=None, unit=None, peak=None, bound=None, oracle=None, nrhs=1, **extra):
+        d = {"row": row, "entry": entry, "workload": args.workload, "gpu_ms": ms}
+        if work is not None:
+            rate = work / (ms / 1e3) / (1e9 if unit == "GB/s" else 1e12)
+            d.update({"work_per_call": work, "achieved": rate, "unit": unit, "bound": bound,
+                      "peak": peak, "frac": rate / peak if peak else None})
+        if oracle is not None:
+            d["cpu_baseline_ns_per_5d_site"] = oracle  # the oracle, 4^4 x 8
+            d["gpu_ns_per_5d_site"] = ms * 1e6 / (2 * ctx.Vh * Ls * nrhs)  # per right-hand side
+        d.update(extra)
+        rows.append(d)
+        print(json.dumps(d), flush=True)
+
+    V5h = ctx.Vh * Ls
+    pe = o_dwf.project_parity(spsi, sL, 1)
+    a32 = field(nh, torch.float32)
+    o32 = torch.zeros_like(a32)
+    a64, o64 = a32.double(), torch.zeros(nh, dtype=torch.float64, device="cuda")
+    a16, o16 = a32.half(), torch.zeros(nh, dtype=torch.float16, device="cuda")
+    f = lambda: ops.dwf_dhop(ctx, o32, a32, 0)
+    emit("a1", "dwf_dhop F32", timed(f), hop_bytes(f), "GB/s", hbm, "hbm",
+         oracle_ns_per_site(lambda: o_dwf.dhop(sU, pe)) * 2)
+    f = lambda: ops.dwf_dhop(ctx, o16, a16, 0)
+    emit("a1", "dwf_dhop F16 storage", timed(f), hop_bytes(f), "GB/s", hbm, "hbm")
+    f = lambda: ops.dwf_dhop(ctx, o64, a64, 0)
+    emit("a1", "dwf_dhop F64", timed(f, 5), 1320.0 * V5h, "TFLOP/s", fp64_peak, "fp64 alu (nominal 1.25)")
+    f = lambda: ops.dwf_mooee_inv(ctx, o32, a32, mf)
+    emit("a2", "dwf_mooee_inv F32", timed(f), V5h * 24 * 8.0, "GB/s", hbm, "hbm",
+         oracle_ns_per_site(lambda: o_dwf.mooee_inv(spsi, M5, mf)))
+    f = lambda: ops.dwf_mpcdag_mpc(ctx, o32, a32, mf)
+    emit("a3", "dwf_mpcdag_mpc F32", timed(f), hop_bytes(f), "GB/s", hbm, "hbm",
+         oracle_ns_per_site(lambda: o_dwf.mpc_dag(sU, o_dwf.mpc(sU, o_dwf.project_parity(spsi, sL, 0), M5, mf),
+                                                   M5, mf)) * 2)
+    bd = torch.from_numpy(layout.complex_to_real(layout.to_full(b, L), F64)).cuda()
+    xd = torch.zeros_like(bd)
+    st = {}
+
+    def solve():
+        xd.zero_()
+        st.update(ops.rbcg_solve(ctx, xd, bd, mf, args.tol, 100000, SOLVE_MIXED_F32))
+    ms = timed(solve, 3)
+    emit("a4", "rbcg_solve mixed FP32/FP64", ms, hop_bytes(solve), "GB/s", hbm, "hbm",
+         iterations=st["iterations"], true_residual=st["true_residual"],
+         note="achieved = algorithmic hopping bytes of the whole solve / its time")
+    f = lambda: ops.dwf_norm2(ctx, a32)
+    emit("a5", "dwf_norm2 F32 (half field)", timed(f), nh * 4.0, "GB/s", hbm, "hbm")
+    f = lambda: ops.dwf_cdot(ctx, a64, a64)
+    emit("a5", "dwf_cdot F64 (half field)", timed(f), 2 * nh * 8.0, "GB/s", hbm, "hbm")
+    full32 = field(2 * nh, torch.float32)
+    fo32 = torch.zeros_like(full32)
+    f = lambda: ops.dwf_hdw(ctx, fo32, full32, mf)
+    emit("a6", "dwf_hdw F32 (full field)", timed(f), hop_bytes(f), "GB/s", hbm, "hbm",
+         oracle_ns_per_site(lambda: o_dwf.hdw(sU, spsi, M5, mf)))
+    v0 = torch.from_numpy(layout.complex_to_real(layout.to_full(synth.gaussian_spinor(L, Ls, 77), L), F64)).cuda()
+    f = lambda: ops.dwf_power_max(ctx, v0, mf, 100, F32)
+    emit("a7", "dwf_power_max F32, 100 iterations", timed(f, 3), hop_bytes(f), "GB/s", hbm, "hbm")
+    nr = 8
+    fin = field(2 * nh * nr, torch.float32)
+    fout = torch.zeros_like(fin)
+    f = lambda: ops.cheby_filter(ctx, fout, fin, nr, 0.02, 60.0, 60, mf)
+    emit("a8", f"cheby_filter F32, order 60, {nr} RHS", timed(f, 3), hop_bytes(f), "GB/s", hbm, "hbm",
+         oracle_ns_per_site(lambda: o_cheby.cheby_filter(lambda v: o_dwf.mdagm(sU, v, M5, mf), spsi, 4, 0.02,
+                                                          60.0), 1) * 60 / 4, nrhs=nr)
+    del fin, fout
+    nb, block = 32, (4, 4, 4, 4)
+    g64 = field(nb * 2 * nh, torch.float64)
+    basis = torch.empty_like(g64)
+    half = nb // 2 * 2 * nh
+    ops.dwf_chiral_project(ctx, basis[:half], g64[:half], 1, nb // 2)
+    ops.dwf_chiral_project(ctx, basis[half:], g64[half:], -1, nb // 2)
+    work = basis.clone()
+
+    def ortho():
+        work.copy_(basis)
+        ops.block_orthonormalise(ctx, work, nb, nb // 2, block)
+    ms = timed(ortho, 3)
+    copy_ms = timed(lambda: work.copy_(basis), 3)
+    nfull_c = nh  # complex numbers of one full field (= reals of one half field)
+    emit("a9", "block_orthonormalise FP64, 32 vectors, 4^4 x Ls blocks", ms - copy_ms,
+         2 * 2 * 8.0 * nb * nb * nfull_c, "TFLOP/s", fp64_peak, "fp64 alu (nominal 1.25)",
+         note="work = Cholesky-QR2: two passes of a Gram matrix and an R^-1 application, 8 nb^2 flop per"
+              " complex entry each, all in FP64 as the orthonormalisation requires")
+    del g64, basis
+    Cc = [None]
+
+    work32 = work.float()  # the multigrid setup builds from the FP32 copy of the basis
+    del work
+
+    def build():
+        if Cc[0] is not None:
+            Cc[0].close()
+        Cc[0] = ops.coarse_build(ctx, work32, nb, nb // 2, block, mf)
+    ms = timed(build, 3)
+    emit("a10", "coarse_build (9-point H_DW stencil), nb 32, 4^4 x Ls blocks, FP32 basis", ms, None,
+         note="face hops of the 32 basis fields and block inner products, as in mg_setup")
+    del work32
+    coarse = Cc[0]
+    r = field(2 * coarse.nc * nb, torch.float32)
+    e = torch.zeros_like(r)
+    its = []
+
+    def csolve():
+        its.append(ops.coarse_solve(coarse, e, r, 1e-4, 5000))
+    ms = timed(csolve, 5)
+    emit("a12", "coarse_solve (persistent coarse CG on A^2), Gaussian right-hand side, to 1e-4", ms, None,
+         iterations=its[-1], us_per_iteration=1e3 * ms / max(its[-1], 1))
+    coarse.close()
+    for pn in ("tf32", "f32"):
+        res = coarse_apply_measure(ctx, w, pn, 3, 10)
+        emit("a11", f"coarse_apply {pn.upper()}, nb 32, 32 RHS, 512 coarse sites", res["ms_median"],
+             res["flop_per_launch"], "TFLOP/s",
+             res.get("tf32_peak_tflops") if pn == "tf32" else None, "tensor (TF32)" if pn == "tf32" else "fp32",
+             GBs_algorithmic=res["GBs_algorithmic"], frac_of_hbm=res["frac_of_hbm"])
+    lmax = ops.dwf_power_max(ctx, v0, mf, 100, F32) * 1.1
+    prm = ops.mg_params(block, nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=0.05, lambda_max=lmax,
+                        filter_order=60, smooth=(0.05, lmax, 32), coarse_tol=0.02)
+    eta = field(nb * 2 * nh, torch.float64)
+    G = ops.MG(ctx, prm, eta)
+    del eta
+    f = lambda: ops.mg_smooth(G, fo32, full32)
+    emit("a13", "mg_smooth S_cheb([0.05, lmax], 32), F32 full field", timed(f, 3), hop_bytes(f), "GB/s", hbm,
+         "hbm", note="achieved counts the hopping launches' algorithmic bytes only (the Chebyshev updates add"
+                     " six field passes per order)")
+    G.close()
+    npf = 4
+    X = field(npf * nh, torch.float32)
+    force = torch.zeros(int(np.prod(L)) * 4 * 9 * 2, dtype=torch.float64, device="cuda")
+    f = lambda: ops.dwf_force(ctx, force, X, [0.01, 0.05, 0.2, 1.0])
+    fbytes = npf * 4 * nh * 4.0 + 2 * ctx.Vh * 72 * 8 * 2 + force.numel() * 8 * 2
+    emit("a15", "dwf_force, 4 pseudofermions, FP32 fields", timed(f, 3), fbytes, "GB/s", hbm, "hbm",
+         note="work = X, Y, X', Y' half fields per pseudofermion + links + force read and write; the hops"
+              " forming Y, X', Y' are inside the call")
+    print(json.dumps({"rows_measured": len(rows), "peak_source": kind}), flush=True)
     ctx.close()
 
 
@@ -547,11 +782,15 @@ def main(argv=None):
                     help="skip the one-off FP64 RB-CG vs HDCR time-to-solution comparison")
     ap.add_argument("--kernel", default=None,
                     help="profile mode: dhop_f32, dhop_f64, dhop_f16, mpcdagmpc_f32, coarse_tf32 or coarse_f32 alone")
+    ap.add_argument("--rows", action="store_true",
+                    help="measure every step of the hot path alone (one JSON line per step)")
     ap.add_argument("--hop-variant", type=int, default=None,
                     help="with --kernel dhop_*: pin this hopping-kernel variant instead of autotuning")
     ap.add_argument("--sweep-variants", action="store_true",
                     help="with --kernel dhop_*: time every hopping-kernel tuning variant")
     args = ap.parse_args(argv)
+    if args.rows:
+        return run_rows(args)
     if args.kernel:
         if args.kernel.startswith("coarse_"):
             return run_coarse_kernel(args)

@@ -209,7 +209,10 @@ int dwf_norm2_noalloc(double* result, const void* a, int64_t n, int prec, void* 
  * M_pc^dag M_pc x_e = M_pc^dag b'_e and reconstructs x_o = M_oo^-1 (b_o -
  * M_oe x_e).  Stops when the FP64 true residual ||b - D_DW x|| / ||b|| <= tol
  * (returned in stats->true_residual), or returns DWF_ENOCONV after maxiter
- * CG iterations.  policy is one of DWF_SOLVE_*.  stats may be NULL. */
+ * CG iterations.  policy is one of DWF_SOLVE_*: with DWF_SOLVE_MIXED_F16 the
+ * inner CG stores its vectors in FP16 (FP32 arithmetic) and works on the
+ * residual scaled to unit mean square at every FP64 reliable update.  stats
+ * may be NULL. */
 int rbcg_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int maxiter,
                int policy, dwf_solve_stats* stats, void* stream);
 

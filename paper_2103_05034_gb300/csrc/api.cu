@@ -252,6 +252,7 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
     hp.cg_r = h.cg_r;
     hp.cg_p = h.cg_p;
     hp.cg_alpha = h.cg_alpha;
+    hp.cg_x32 = h.cg_x32;
   }
   int rc;
   switch (prec) {
@@ -654,6 +655,7 @@ static int cg_step_fused(dwf_ctx* c, void* x, void* r, const void* p, void* y, v
   h2.cg_r = r;
   h2.cg_p = p;
   h2.cg_alpha = c->dscal + S_ALPHA;
+  h2.cg_x32 = prec == DWF_F16S;  // the FP16-storage CG accumulates x in FP32
   return launch_hop(c, h2, prec, st, nparts);
 }
 
@@ -676,17 +678,43 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
   const double delta = 0.1;
   double true_res = 0, rr_hi = 0, rho = 1, rr_max = 0, rr_lo = 0;
   bool have_x = false;
+  // FP16 storage keeps the inner system scaled: r_lo = r / sigma with sigma
+  // = |r| / sqrt(n) at every reliable update, so that the stored components
+  // are of order one (unscaled they would fall below FP16's range as the
+  // residual shrinks); the inner correction is scaled back, x += sigma x_lo.
+  // FP32 and FP64 inner precisions keep sigma = 1.
+  const bool scaled = plo == DWF_F16S;
+  double sigma = 1.0;
+  // the inner x accumulates the scaled correction A^-1 r / sigma, whose
+  // entries can exceed FP16's range (the low modes of M_pc^dag M_pc); it is
+  // kept in FP32 when the other inner vectors are FP16
+  const int px = scaled ? DWF_F32 : plo;
   void *rhi = B.rhi, *yhi = B.yhi, *ohi = B.ohi, *xlo = B.xlo, *rlo = B.rlo, *p = B.p, *Ap = B.Ap;
 
   auto reliable = [&]() -> int {
     int r;
+    const double sigma_prev = sigma;
+    const bool had_x = have_x;
     if (have_x && plo != DWF_F64) {
-      r = blas_axpby(c, 1.0, xlo, plo, 1.0, x_e, DWF_F64, he, st);
+      r = blas_axpby(c, sigma, xlo, px, 1.0, x_e, DWF_F64, he, st);
       if (r) return r;
     }
-    if (plo != DWF_F64) DWF_CUDA(c, cudaMemsetAsync(xlo, 0, blo, st));
+    if (plo != DWF_F64) DWF_CUDA(c, cudaMemsetAsync(xlo, 0, he * dwf_complex_bytes(px), st));
     if (have_x) {
-      r = mpc_apply(c, yhi, x_e, ohi, mfa, 0, DWF_F64, 1, 0, st, nullptr);
+      // While the residual is far above FP32 rounding (true residual > 1e-4),
+      // M_pc x is formed by the FP32 operator on x rounded to FP32 (error about
+      // 1e-7 of |b|, three decades below the residual it corrects); below that
+      // in FP64.  FP32 inner policy of the red-black solve only; the stopping
+      // decision (true residual <= tol) is always taken on an FP64 residual.
+      if (plo == DWF_F32 && B.bp && true_res > 1e-4) {
+        r = blas_copy(c, B.ylo, DWF_F32, x_e, DWF_F64, he, st);
+        if (r) return r;
+        r = mpc_apply(c, B.Ap, B.ylo, B.olo, mfa, 0, DWF_F32, 1, 0, st, nullptr);
+        if (r) return r;
+        r = blas_copy(c, yhi, DWF_F64, B.Ap, DWF_F32, he, st);
+      } else {
+        r = mpc_apply(c, yhi, x_e, ohi, mfa, 0, DWF_F64, 1, 0, st, nullptr);
+      }
       if (r) return r;
       if (B.bp) {
         // y = b'_e - M_pc x in FP64 (the true residual); r = M_pc^dag y only
@@ -697,6 +725,16 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
         if (r) return r;
         if (plo == DWF_F64) {
           r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+        } else if (scaled) {  // M_pc^dag on y / sigma_y, scaled back into rhi
+          r = read_scalars(c, S_TMP2, 1, st);
+          if (r) return r;
+          const double sy = sqrt(c->hscal[S_TMP2] / (double)he);
+          if (!(sy > 0) || !isfinite(sy)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
+          r = blas_axpby(c, 1.0 / sy, yhi, DWF_F64, 0.0, B.ylo, plo, he, st);
+          if (r) return r;
+          r = mpc_apply(c, rlo, B.ylo, B.olo, mfa, 1, plo, 1, 0, st, nullptr);
+          if (r) return r;
+          r = blas_axpby(c, sy, rlo, plo, 0.0, rhi, DWF_F64, he, st);
         } else {
           r = blas_copy(c, B.ylo, plo, yhi, DWF_F64, he, st);
           if (r) return r;
@@ -721,7 +759,22 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
     }
     r = norm2_dev(c, rhi, he, DWF_F64, S_TMP3, st);
     if (r) return r;
-    r = blas_copy(c, rlo, plo, rhi, DWF_F64, he, st);
+    if (scaled) {
+      r = read_scalars(c, S_TMP3, 1, st);
+      if (r) return r;
+      sigma = sqrt(c->hscal[S_TMP3] / (double)he);
+      if (!isfinite(sigma)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
+      if (!(sigma > 0)) sigma = 1.0;  // exact solution: the inner solve is not entered
+      r = blas_axpby(c, 1.0 / sigma, rhi, DWF_F64, 0.0, rlo, plo, he, st);
+      if (r) return r;
+      // FP16 vectors: the CG restarts from the new residual (p = r); the
+      // direction carried over in FP16 loses conjugacy and can grow without
+      // bound over many updates
+      if (had_x) r = blas_copy(c, p, plo, rlo, plo, he, st);
+      (void)sigma_prev;
+    } else {
+      r = blas_copy(c, rlo, plo, rhi, DWF_F64, he, st);
+    }
     if (r) return r;
     r = norm2_dev(c, rlo, he, plo, S_RR, st);
     if (r) return r;
@@ -743,7 +796,7 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
   S.reliable_updates = 0;
   rc = blas_copy(c, p, plo, rlo, plo, he, st);
   if (rc) return rc;
-  int it = 0;
+  int it = 0, last_reliable_it = 0;
   const int check_every = 8;
   bool converged = true_res <= tol;
   while (!converged && it < maxiter) {
@@ -759,11 +812,15 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
     if (it % check_every == 0 || it == maxiter) {
       rc = read_scalars(c, S_RR, 1, st);
       if (rc) return rc;
-      rr_lo = c->hscal[S_RR];
+      rr_lo = sigma * sigma * c->hscal[S_RR];  // in the units of rr_hi
       if (!isfinite(rr_lo)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
       if (rr_lo > rr_max) rr_max = rr_lo;
       const double predicted = rho * sqrt(rr_lo) / bnorm;
-      if (rr_lo < delta * delta * rr_max || predicted <= tol || it == maxiter) {
+      // FP16 inner vectors also take a reliable update (a restart) every 64
+      // iterations, in case their recursive residual stalls above delta
+      if (rr_lo < delta * delta * rr_max || predicted <= tol || it == maxiter ||
+          (scaled && it - last_reliable_it >= 64)) {
+        last_reliable_it = it;
         rc = reliable();
         if (rc) return rc;
         converged = true_res <= tol;
@@ -783,9 +840,8 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
   if (!(tol > 0) || maxiter < 1) return dwf_fail(c, DWF_EINVAL, "bad tol or maxiter");
   if (policy < DWF_SOLVE_F64 || policy > DWF_SOLVE_MIXED_F16)
     return dwf_fail(c, DWF_EINVAL, "bad policy");
-  if (policy == DWF_SOLVE_MIXED_F16) return dwf_fail(c, DWF_EINVAL, "FP16 policy not available");
   cudaStream_t st = (cudaStream_t)stream;
-  const int plo = policy == DWF_SOLVE_F64 ? DWF_F64 : DWF_F32;
+  const int plo = policy == DWF_SOLVE_F64 ? DWF_F64 : policy == DWF_SOLVE_MIXED_F16 ? DWF_F16S : DWF_F32;
   const int64_t he = half_elems(c);
   const size_t b64 = he * 16, blo = he * dwf_complex_bytes(plo);
   dwf_solve_stats S;
@@ -812,7 +868,7 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
   void* rhi = dwf_workspace(c, WS_RHI, b64);
   void* yhi = dwf_workspace(c, WS_YHI, b64);
   void* ohi = dwf_workspace(c, WS_OHI, b64);
-  void* xlo = plo == DWF_F64 ? nullptr : dwf_workspace(c, WS_XLO, blo);
+  void* xlo = plo == DWF_F64 ? nullptr : dwf_workspace(c, WS_XLO, plo == DWF_F16S ? he * 8 : blo);
   void* rlo = dwf_workspace(c, WS_RLO, blo);
   void* p = dwf_workspace(c, WS_P, blo);
   void* Ap = dwf_workspace(c, WS_AP, blo);

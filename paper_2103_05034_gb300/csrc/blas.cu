@@ -1,5 +1,7 @@
 // BLAS-1 kernels with FP64 accumulation for global sums (the inner products
-// of every Krylov step, arXiv:2103.05034 Secs. 3 and 5.1).  Reductions are
+// of every Krylov step, arXiv:2103.05034 Secs. 3 and 5.1); single-precision
+// data accumulate per thread in compensated FP32 (PartialSum) and combine in
+// FP64.  Reductions are
 // two-pass and deterministic: a fixed grid writes one partial per CTA (warp
 // shuffles, then shared memory), one CTA sums the partials in order.
 #include "dwf_internal.cuh"
@@ -25,27 +27,30 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 template <int P>
 __global__ void __launch_bounds__(BT) k_norm2(const typename Prec<P>::S* a, long long n, double* part) {
+  typedef typename Prec<P>::R R;
   __shared__ double sh[BT / 32];
-  double acc = 0.0;
+  PartialSum<R> acc;
   for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
     const auto z = ld_c(a + i);
-    acc += (double)z.re * z.re + (double)z.im * z.im;
+    acc.add(fma(z.re, z.re, z.im * z.im));
   }
-  const double t = block_sum(acc, sh);
+  const double t = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 template <int P>
 __global__ void __launch_bounds__(BT) k_cdot(const typename Prec<P>::S* a, const typename Prec<P>::S* b,
                                              long long n, double* part) {
+  typedef typename Prec<P>::R R;
   __shared__ double sh[BT / 32];
-  double re = 0.0, im = 0.0;
+  PartialSum<R> pre, pim;
   for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
     const auto x = ld_c(a + i);
     const auto y = ld_c(b + i);
-    re += (double)x.re * y.re + (double)x.im * y.im;
-    im += (double)x.re * y.im - (double)x.im * y.re;
+    pre.add(fma(x.re, y.re, x.im * y.im));
+    pim.add(fma(x.re, y.im, -(x.im * y.re)));
   }
+  const double re = pre.value(), im = pim.value();
   const double tr = block_sum(re, sh);
   const double ti = block_sum(im, sh);
   if (threadIdx.x == 0) {
@@ -83,7 +88,17 @@ __global__ void __launch_bounds__(BT) k_axpby(double a, const typename Prec<PX>:
   for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
     const auto xv = ld_c(x + i);
     cpx<RY> o;
-    if (b == 0.0) {
+    if (PX != DWF_F64 && PY != DWF_F64) {  // single-precision data: FP32 arithmetic
+      const float af = (float)a, bf = (float)b;
+      if (b == 0.0) {
+        o.re = af * (float)xv.re;
+        o.im = af * (float)xv.im;
+      } else {
+        const auto yv = ld_c(y + i);
+        o.re = fmaf(af, (float)xv.re, bf * (float)yv.re);
+        o.im = fmaf(af, (float)xv.im, bf * (float)yv.im);
+      }
+    } else if (b == 0.0) {
       o.re = (RY)(a * (double)xv.re);
       o.im = (RY)(a * (double)xv.im);
     } else {
@@ -103,7 +118,7 @@ __global__ void __launch_bounds__(BT) k_cg_xr(typename Prec<P>::S* x, typename P
   typedef typename Prec<P>::R R;
   __shared__ double sh[BT / 32];
   const R alpha = (R)dscal[ialpha];
-  double acc = 0.0;
+  PartialSum<R> acc;
   for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
     auto xv = ld_c(x + i);
     auto rv = ld_c(r + i);
@@ -115,9 +130,9 @@ __global__ void __launch_bounds__(BT) k_cg_xr(typename Prec<P>::S* x, typename P
     rv.im = fma(-alpha, av.im, rv.im);
     st_c(x + i, xv);
     st_c(r + i, rv);
-    acc += (double)rv.re * rv.re + (double)rv.im * rv.im;
+    acc.add(fma(rv.re, rv.re, rv.im * rv.im));
   }
-  const double t = block_sum(acc, sh);
+  const double t = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
@@ -187,8 +202,14 @@ __global__ void __launch_bounds__(BT) k_caxpy(double ar, double ai, const typena
     const auto xv = ld_c(x + i);
     const auto yv = ld_c(y + i);
     cpx<RY> o;
-    o.re = (RY)((double)yv.re + ar * xv.re - ai * xv.im);
-    o.im = (RY)((double)yv.im + ar * xv.im + ai * xv.re);
+    if (PX != DWF_F64 && PY != DWF_F64) {  // single-precision data: FP32 arithmetic
+      const float arf = (float)ar, aif = (float)ai;
+      o.re = fmaf(arf, (float)xv.re, fmaf(-aif, (float)xv.im, (float)yv.re));
+      o.im = fmaf(arf, (float)xv.im, fmaf(aif, (float)xv.re, (float)yv.im));
+    } else {
+      o.re = (RY)((double)yv.re + ar * xv.re - ai * xv.im);
+      o.im = (RY)((double)yv.im + ar * xv.im + ai * xv.re);
+    }
     st_c(y + i, o);
   }
 }

@@ -51,6 +51,7 @@ struct HopParams {
   void* cg_r;
   const void* cg_p;
   const double* cg_alpha;  // device scalar
+  int cg_x32;              // x stored in FP32 (with FP16-storage r and p)
   double m[DWF_MAX_RHS];
   double kappa[DWF_MAX_RHS];
   double dls1[DWF_MAX_RHS];
@@ -566,18 +567,29 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
     if (active) {
       const size_t off = (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS + s;
       S* xs = (S*)p.cg_x + off;
+      float2* xs32 = (float2*)p.cg_x + off;
       S* rs = (S*)p.cg_r + off;
       const S* ps = (const S*)p.cg_p + off;
       const R alpha = (R)(*p.cg_alpha);
+      const bool x32 = (P == DWF_F16S) && p.cg_x32;
 #pragma unroll
       for (int c = 0; c < 12; c++) {
-        cpx<R> xv = ld_c(xs + c * LS), rv = ld_c(rs + c * LS);
+        cpx<R> xv, rv = ld_c(rs + c * LS);
+        if (x32) {
+          const float2 t = xs32[c * LS];
+          xv = cmake<R>((R)t.x, (R)t.y);
+        } else {
+          xv = ld_c(xs + c * LS);
+        }
         const cpx<R> pv = ld_c(ps + c * LS);
         xv.re = fma(alpha, pv.re, xv.re);
         xv.im = fma(alpha, pv.im, xv.im);
         rv.re = fma(-alpha, v[c].re, rv.re);
         rv.im = fma(-alpha, v[c].im, rv.im);
-        st_c(xs + c * LS, xv);
+        if (x32)
+          xs32[c * LS] = make_float2((float)xv.re, (float)xv.im);
+        else
+          st_c(xs + c * LS, xv);
         st_c(rs + c * LS, rv);
         v[c] = rv;
       }
@@ -602,11 +614,12 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
   }
 
   if (p.reduce) {
-    double acc = 0.0;
+    PartialSum<R> ps;
     if (active) {
 #pragma unroll
-      for (int c = 0; c < 12; c++) acc += (double)v[c].re * v[c].re + (double)v[c].im * v[c].im;
+      for (int c = 0; c < 12; c++) ps.add(fma(v[c].re, v[c].re, v[c].im * v[c].im));
     }
+    double acc = ps.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((tid & 31) == 0) red[tid >> 5] = acc;

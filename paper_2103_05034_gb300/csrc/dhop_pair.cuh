@@ -425,17 +425,25 @@ __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::
       const S* ps = (const S*)p.cg_p + off;
       const float al = (float)(*p.cg_alpha);
       const f2p AL = pk2(al, al), NAL = pk2(-al, -al);
+      float2* xs32 = (float2*)p.cg_x + off;
+      const bool x32 = (P == DWF_F16S) && p.cg_x32;
 #pragma unroll
       for (int c = 0; c < 12; c++) {
         f2p xr, xi, rr, ri, pr, pi;
-        PairIO<P>::ld(xs + c * LS, xr, xi);
+        if (x32)
+          PairIO<DWF_F32>::ld(xs32 + c * LS, xr, xi);
+        else
+          PairIO<P>::ld(xs + c * LS, xr, xi);
         PairIO<P>::ld(rs + c * LS, rr, ri);
         PairIO<P>::ld(ps + c * LS, pr, pi);
         xr = fma2(AL, pr, xr);
         xi = fma2(AL, pi, xi);
         rr = fma2(NAL, vr[c], rr);
         ri = fma2(NAL, vi[c], ri);
-        PairIO<P>::st(xs + c * LS, xr, xi);
+        if (x32)
+          PairIO<DWF_F32>::st(xs32 + c * LS, xr, xi);
+        else
+          PairIO<P>::st(xs + c * LS, xr, xi);
         PairIO<P>::st(rs + c * LS, rr, ri);
         vr[c] = rr;
         vi[c] = ri;
@@ -463,16 +471,18 @@ __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::
   }
 
   if (p.reduce) {
-    double acc = 0.0;
+    PartialSum<float> ps;
     if (active) {
 #pragma unroll
       for (int c = 0; c < 12; c++) {
         float a, b, e, f;
         upk2(vr[c], a, b);
         upk2(vi[c], e, f);
-        acc += (double)a * a + (double)b * b + (double)e * e + (double)f * f;
+        ps.add(fmaf(a, a, b * b));
+        ps.add(fmaf(e, e, f * f));
       }
     }
+    double acc = ps.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((tid & 31) == 0) red[tid >> 5] = acc;

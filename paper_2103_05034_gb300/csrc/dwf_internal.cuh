@@ -69,6 +69,32 @@ __device__ __forceinline__ void st_c(__half2* p, cpx<float> z) {
   *p = __floats2half2_rn(z.re, z.im);
 }
 
+// Per-thread partial sum for reductions.  FP64 data accumulate in FP64; FP32
+// and FP16-storage data accumulate in FP32 with a compensation term (Kahan's
+// summation: the rounding error of every addition is carried to the next),
+// and the partials of all threads are combined in FP64.  GB300 runs FP64 at a
+// small fraction of its FP32 rate, so a per-element FP64 sum would cost more
+// ALU time than the memory traffic of the pass.
+template <class R>
+struct PartialSum;
+template <>
+struct PartialSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct PartialSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // ------------------------------------------------------------------ geometry
 struct Geom {
   int L[4];   // Lx, Ly, Lz, Lt
@@ -145,6 +171,7 @@ struct HopLaunch {
   void* cg_r;
   const void* cg_p;
   const double* cg_alpha;
+  int cg_x32;          // x is FP32 whatever the field precision (FP16-storage CG)
 };
 
 int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* nblocks);

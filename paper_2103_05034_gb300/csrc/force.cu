@@ -11,6 +11,7 @@
 // with both fields projected by the same (1 -+ gamma) half-spinor map.
 #include <string.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "dhop_impl.cuh"
@@ -39,9 +40,9 @@ __device__ __forceinline__ void proj(cpx<R> (&h)[2][3], const cpx<R> (&ps)[12], 
   }
 }
 
-// acc_ab += sum_k hx[k][a] conj(hy[k][b])
+// o_ab = sum_k hx[k][a] conj(hy[k][b]) (one s-slice)
 template <class R>
-__device__ __forceinline__ void outer_acc(double2 (&acc)[9], const cpx<R> (&hx)[2][3], const cpx<R> (&hy)[2][3]) {
+__device__ __forceinline__ void outer2(cpx<R> (&o)[9], const cpx<R> (&hx)[2][3], const cpx<R> (&hy)[2][3]) {
 #pragma unroll
   for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -52,49 +53,51 @@ __device__ __forceinline__ void outer_acc(double2 (&acc)[9], const cpx<R> (&hx)[
         re += hx[k][a].re * hy[k][b].re + hx[k][a].im * hy[k][b].im;
         im += hx[k][a].im * hy[k][b].re - hx[k][a].re * hy[k][b].im;
       }
-      acc[a * 3 + b].x += (double)re;
-      acc[a * 3 + b].y += (double)im;
+      o[a * 3 + b] = cmake<R>(re, im);
     }
 }
 
-template <int P, int MU, int LS>
-__device__ void link_force(double2 (&A)[9], double2 (&B)[9], const typename Prec<P>::S* Xx,
-                           const typename Prec<P>::S* Yx, const typename Prec<P>::S* Xy,
-                           const typename Prec<P>::S* Yy) {
-  typedef typename Prec<P>::R R;
-  for (int s = 0; s < LS; s++) {
-    cpx<R> xa[12], ya[12], xb[12], yb[12];
+// Sum over the Ls threads of each site of one 3x3 complex matrix per thread
+// (shared-memory reduction, fixed order), into AB[site][slot] in FP64.
+template <class R, int LS, int SB>
+__device__ __forceinline__ void site_sum(R* red, double2* AB, int slot, const cpx<R> (&o)[9], int sl, int s) {
+  constexpr int NT = LS * SB;
 #pragma unroll
-    for (int c = 0; c < 12; c++) {
-      xa[c] = ld_c(Xy + c * LS + s);  // X'(x+mu)
-      ya[c] = ld_c(Yx + c * LS + s);  // Y'(x)
-      xb[c] = ld_c(Xx + c * LS + s);  // X'(x)
-      yb[c] = ld_c(Yy + c * LS + s);  // Y'(x+mu)
-    }
-    cpx<R> hx[2][3], hy[2][3];
-    proj<R, MU>(hx, xa, R(1));
-    proj<R, MU>(hy, ya, R(1));
-    outer_acc<R>(A, hx, hy);
-    proj<R, MU>(hx, xb, R(-1));
-    proj<R, MU>(hy, yb, R(-1));
-    outer_acc<R>(B, hx, hy);
+  for (int e = 0; e < 9; e++) {
+    red[((sl * LS + s) * 9 + e) * 2] = o[e].re;
+    red[((sl * LS + s) * 9 + e) * 2 + 1] = o[e].im;
   }
+  __syncthreads();
+  for (int t = threadIdx.x; t < SB * 18; t += NT) {
+    const int sl2 = t / 18, e = t - sl2 * 18;
+    R acc = 0;
+    for (int q = 0; q < LS; q++) acc += red[(sl2 * LS + q) * 18 + e];
+    double* dst = (double*)(AB + (sl2 * 8 + slot) * 9);
+    dst[e] = (double)acc;
+  }
+  __syncthreads();
 }
 
-// One thread per link (parity, checkerboard site, mu); force[lex][mu] += G.
-template <int P, int LS>
-__global__ void __launch_bounds__(128) k_force(double2* force, const typename Prec<P>::S* Xf,
-                                               const typename Prec<P>::S* Yf, const double2* links_e,
-                                               const double2* links_o, int L0, int L1, int L2, int L3, int Vh) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= 2LL * Vh * 4) return;
-  const int mu = (int)(gid & 3);
-  const long long ps = gid >> 2;
-  const int p = (int)(ps / Vh);
-  const int h = (int)(ps - (long long)p * Vh);
+// One CTA: SB checkerboard sites of one parity x Ls threads (s fastest, so
+// the neighbours' spinors are read as contiguous Ls-runs).  Each thread forms
+// the s-slice of A_mu and B_mu for the 4 directions; the Ls contributions are
+// summed per site in shared memory, and 4 threads per site form G_mu in FP64.
+template <int P, int LS, int SB>
+__global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename Prec<P>::S* Xf,
+                                                 const typename Prec<P>::S* Yf, const double2* links_e,
+                                                 const double2* links_o, int L0, int L1, int L2, int L3, int Vh) {
+  typedef typename Prec<P>::R R;
+  typedef typename Prec<P>::S S;
+  __shared__ R red[SB * LS * 18];
+  __shared__ double2 AB[SB * 8 * 9];  // per site: A_mu (slots 0-3), B_mu (slots 4-7)
+  const int tid = threadIdx.x, sl = tid / LS, s = tid - sl * LS;
+  const int p = blockIdx.y;
+  const int h = blockIdx.x * SB + sl;
+  const bool active = h < Vh;
+  const int hh = active ? h : 0;
   const int Lxh = L0 / 2;
-  int rem = h / Lxh;
-  const int xh = h - rem * Lxh;
+  int rem = hh / Lxh;
+  const int xh = hh - rem * Lxh;
   int x[4];
   x[1] = rem % L1;
   rem /= L1;
@@ -102,69 +105,114 @@ __global__ void __launch_bounds__(128) k_force(double2* force, const typename Pr
   x[3] = rem / L2;
   x[0] = 2 * xh + ((x[1] + x[2] + x[3] + p) & 1);
   const int Ld[4] = {L0, L1, L2, L3};
-  int y[4] = {x[0], x[1], x[2], x[3]};
-  y[mu] = (y[mu] + 1 == Ld[mu]) ? 0 : y[mu] + 1;
-  const long long ylex = y[0] + (long long)L0 * (y[1] + (long long)L1 * (y[2] + (long long)L2 * y[3]));
-  const long long xlex = x[0] + (long long)L0 * (x[1] + (long long)L1 * (x[2] + (long long)L2 * x[3]));
   const long long row = 12LL * LS;
-  const typename Prec<P>::S* Xx = Xf + ((long long)p * Vh + h) * row;
-  const typename Prec<P>::S* Yx = Yf + ((long long)p * Vh + h) * row;
-  const typename Prec<P>::S* Xy = Xf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row;
-  const typename Prec<P>::S* Yy = Yf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row;
-  double2 A[9], B[9];
+  cpx<R> xb[12], ya[12];
+  const S* Xx = Xf + ((long long)p * Vh + hh) * row + s;
+  const S* Yx = Yf + ((long long)p * Vh + hh) * row + s;
 #pragma unroll
-  for (int i = 0; i < 9; i++) A[i] = B[i] = make_double2(0, 0);
-  switch (mu) {
-    case 0: link_force<P, 0, LS>(A, B, Xx, Yx, Xy, Yy); break;
-    case 1: link_force<P, 1, LS>(A, B, Xx, Yx, Xy, Yy); break;
-    case 2: link_force<P, 2, LS>(A, B, Xx, Yx, Xy, Yy); break;
-    default: link_force<P, 3, LS>(A, B, Xx, Yx, Xy, Yy); break;
+  for (int c = 0; c < 12; c++) {
+    xb[c] = active ? ld_c(Xx + c * LS) : cmake<R>(0, 0);
+    ya[c] = active ? ld_c(Yx + c * LS) : cmake<R>(0, 0);
   }
-  const double2* U = (p ? links_o : links_e) + ((long long)h * 8 + 2 * mu) * 9;
-  double2 Z[9];
+  auto dir = [&](auto muc) {
+    constexpr int MU = decltype(muc)::value;
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    y[MU] = (y[MU] + 1 == Ld[MU]) ? 0 : y[MU] + 1;
+    const long long ylex = y[0] + (long long)L0 * (y[1] + (long long)L1 * (y[2] + (long long)L2 * y[3]));
+    const S* Xy = Xf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row + s;
+    const S* Yy = Yf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row + s;
+    cpx<R> xa[12], yb[12];
 #pragma unroll
-  for (int a = 0; a < 3; a++)
+    for (int c = 0; c < 12; c++) {
+      xa[c] = active ? ld_c(Xy + c * LS) : cmake<R>(0, 0);  // X'(x+mu)
+      yb[c] = active ? ld_c(Yy + c * LS) : cmake<R>(0, 0);  // Y'(x+mu)
+    }
+    cpx<R> hx[2][3], hy[2][3], o[9];
+    proj<R, MU>(hx, xa, R(1));
+    proj<R, MU>(hy, ya, R(1));
+    outer2<R>(o, hx, hy);
+    site_sum<R, LS, SB>(red, AB, MU, o, sl, s);
+    proj<R, MU>(hx, xb, R(-1));
+    proj<R, MU>(hy, yb, R(-1));
+    outer2<R>(o, hx, hy);
+    site_sum<R, LS, SB>(red, AB, 4 + MU, o, sl, s);
+  };
+  dir(std::integral_constant<int, 0>());
+  dir(std::integral_constant<int, 1>());
+  dir(std::integral_constant<int, 2>());
+  dir(std::integral_constant<int, 3>());
+  // G_mu = TA(U A - B U^dag), one thread per (site, mu)
+  for (int t = tid; t < SB * 4; t += LS * SB) {
+    const int sl2 = t >> 2, mu = t & 3;
+    const int h2 = blockIdx.x * SB + sl2;
+    if (h2 >= Vh) continue;
+    int r2 = h2 / Lxh;
+    const int xh2 = h2 - r2 * Lxh;
+    int z[4];
+    z[1] = r2 % L1;
+    r2 /= L1;
+    z[2] = r2 % L2;
+    z[3] = r2 / L2;
+    z[0] = 2 * xh2 + ((z[1] + z[2] + z[3] + p) & 1);
+    const long long zlex = z[0] + (long long)L0 * (z[1] + (long long)L1 * (z[2] + (long long)L2 * z[3]));
+    const double2* A = AB + (sl2 * 8 + mu) * 9;
+    const double2* B = AB + (sl2 * 8 + 4 + mu) * 9;
+    const double2* U = (p ? links_o : links_e) + ((long long)h2 * 8 + 2 * mu) * 9;
+    double2 Z[9];
 #pragma unroll
-    for (int b = 0; b < 3; b++) {
-      double re = 0, im = 0;
+    for (int a = 0; a < 3; a++)
 #pragma unroll
-      for (int k = 0; k < 3; k++) {
-        const double2 u = U[a * 3 + k], av = A[k * 3 + b];  // (U A)_ab
-        re += u.x * av.x - u.y * av.y;
-        im += u.x * av.y + u.y * av.x;
-        const double2 bv = B[a * 3 + k], ud = U[b * 3 + k];  // (B U^dag)_ab = B_ak conj(U_bk)
-        re -= bv.x * ud.x + bv.y * ud.y;
-        im -= bv.y * ud.x - bv.x * ud.y;
+      for (int b = 0; b < 3; b++) {
+        double re = 0, im = 0;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          const double2 u = U[a * 3 + k], av = A[k * 3 + b];  // (U A)_ab
+          re += u.x * av.x - u.y * av.y;
+          im += u.x * av.y + u.y * av.x;
+          const double2 bv = B[a * 3 + k], ud = U[b * 3 + k];  // (B U^dag)_ab = B_ak conj(U_bk)
+          re -= bv.x * ud.x + bv.y * ud.y;
+          im -= bv.y * ud.x - bv.x * ud.y;
+        }
+        Z[a * 3 + b] = make_double2(re, im);
       }
-      Z[a * 3 + b] = make_double2(re, im);
-    }
-  // TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6
-  const double trim = (Z[0].y + Z[4].y + Z[8].y) / 3.0;  // tr(Z - Z^dag)/6 = i Im tr Z / 3
-  double2* out = force + (xlex * 4 + mu) * 9;
+    // TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6
+    const double trim = (Z[0].y + Z[4].y + Z[8].y) / 3.0;  // tr(Z - Z^dag)/6 = i Im tr Z / 3
+    double2* out = force + (zlex * 4 + mu) * 9;
 #pragma unroll
-  for (int a = 0; a < 3; a++)
+    for (int a = 0; a < 3; a++)
 #pragma unroll
-    for (int b = 0; b < 3; b++) {
-      double re = 0.5 * (Z[a * 3 + b].x - Z[b * 3 + a].x);
-      double im = 0.5 * (Z[a * 3 + b].y + Z[b * 3 + a].y);
-      if (a == b) im -= trim;
-      out[a * 3 + b].x += re;
-      out[a * 3 + b].y += im;
-    }
+      for (int b = 0; b < 3; b++) {
+        double re = 0.5 * (Z[a * 3 + b].x - Z[b * 3 + a].x);
+        double im = 0.5 * (Z[a * 3 + b].y + Z[b * 3 + a].y);
+        if (a == b) im -= trim;
+        out[a * 3 + b].x += re;
+        out[a * 3 + b].y += im;
+      }
+  }
 }
 
 template <int P>
 int launch_force(dwf_ctx* c, double2* force, const void* Xf, const void* Yf, cudaStream_t st) {
-  const long long n = 2LL * c->g.Vh * 4;
-  const unsigned grid = (unsigned)((n + 127) / 128);
   typedef typename Prec<P>::S S;
   c->launches++;
-  switch (c->g.Ls) {
-    case 4: k_force<P, 4><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
-    case 8: k_force<P, 8><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
-    case 16: k_force<P, 16><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
-    default: k_force<P, 24><<<grid, 128, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0], c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], (int)c->g.Vh); break;
+#define DWF_FORCE_CASE(LSV)                                                                                  \
+  case LSV: {                                                                                                \
+    constexpr int SB = LSV >= 16 ? 8 : 64 / LSV;                                                             \
+    dim3 grid((unsigned)((c->g.Vh + SB - 1) / SB), 2);                                                       \
+    k_force<P, LSV, SB><<<grid, LSV * SB, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0],        \
+                                                   c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], \
+                                                   (int)c->g.Vh);                                            \
+    break;                                                                                                   \
   }
+  switch (c->g.Ls) {
+    DWF_FORCE_CASE(4)
+    DWF_FORCE_CASE(8)
+    DWF_FORCE_CASE(16)
+    DWF_FORCE_CASE(24)
+    default:
+      return dwf_fail(c, DWF_EINVAL, "unsupported Ls");
+  }
+#undef DWF_FORCE_CASE
   return DWF_OK;
 }
 

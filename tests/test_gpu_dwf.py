@@ -123,10 +123,11 @@ def test_reductions(case):
     assert abs(ip - want) < 1e-12 * np.sqrt(dwf.norm2(a) * dwf.norm2(b))
 
 
-@pytest.mark.parametrize("policy", [SOLVE_F64, SOLVE_MIXED_F32])
+@pytest.mark.parametrize("policy", [SOLVE_F64, SOLVE_MIXED_F32, _lib.SOLVE_MIXED_F16])
 def test_rbcg_solution_parity(policy):
     """4^4 x Ls=8, U = exp(0.3 i H), M5 = 1.8, mf = 0.01 (the small FP64
-    workload): GPU solution vs oracle solution."""
+    workload): GPU solution vs oracle solution, for FP64, FP32-inner and
+    FP16-storage-inner CG (the last two with FP64 reliable updates)."""
     L, Ls, mf = (4, 4, 4, 4), 8, 0.01
     U = synth.random_gauge(L, 0.3, synth.SEED_GAUGE)
     b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE)
