@@ -261,6 +261,19 @@ def mg_vs_fp64(ctx, w, b, bd, tol):
 
 
 # ---------------------------------------------------------------------- GPU leg
+def reduce_ranks(seconds, nbytes, device):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    and the bytes of all ranks (every rank calls this with its own values)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    b = torch.tensor([nbytes], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(b[0])
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -320,11 +333,7 @@ def run_ours(args):
     t_max = t_dev
     tot_bytes = hop_bytes
     if world > 1:
-        tt = torch.tensor([t_dev, hop_bytes], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_max, tot_bytes = float(tmax[0]), float(tt[1])
+        t_max, tot_bytes = reduce_ranks(t_dev, hop_bytes, dev)
     value = tot_bytes / t_max / 1e9
 
     # ---- dominant kernel: the FP32 hopping term, timed alone with an L2 flush before each launch
@@ -368,11 +377,7 @@ def run_ours(args):
     t_e2e = time.perf_counter() - t0
     _, e2e_bytes = ops.dwf_counters(ctx)
     if world > 1:
-        tt = torch.tensor([t_e2e, e2e_bytes], dtype=torch.float64, device=dev)
-        tm = tt.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_e2e, e2e_bytes = float(tm[0]), float(tt[1])
+        t_e2e, e2e_bytes = reduce_ranks(t_e2e, e2e_bytes, dev)
     e2e = {"value": e2e_bytes / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 8),
            "d2h_bytes_per_step": int(xh.numel() * 8),
            "note": "rbcg_solve on pinned host b and x: H2D of b and D2H of x inside the call"}
