@@ -404,7 +404,8 @@ def run_ours(args):
                       "seconds": t_max / args.steps, "wall_seconds_all_steps": t_wall},
         }
         try:  # the same solve with FP16-storage inner vectors (scaled residual)
-            from paper_2103_05034_gb300._lib import SOLVE_MIXED_F16
+            from paper_2103_05034_gb300._lib import F16S, SOLVE_MIXED_F16
+            ops.dwf_autotune(ctx, F16S, 10)
             xd.zero_()
             ops.rbcg_solve(ctx, xd, bd, mf, args.tol, 100000, SOLVE_MIXED_F16)  # warm
             xd.zero_()
