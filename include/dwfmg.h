@@ -201,6 +201,15 @@ int dwf_cdot(dwf_ctx* ctx, double* result2, const void* a, const void* b, int64_
  * Synchronises `stream`. */
 int dwf_norm2_noalloc(double* result, const void* a, int64_t n, int prec, void* stream);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): runs
+ * the two wait forms the kernels use -- polling a global counter and waiting
+ * on an mbarrier phase -- against events that never happen, each limited to
+ * about a millisecond.  gave_up[0] / gave_up[1] receive 1 when the poll / the
+ * mbarrier wait gave up.  Returns DWF_ETIMEOUT when both gave up (the
+ * expected outcome: the GPU stays usable and the status reaches the host),
+ * DWF_OK if either wait unexpectedly completed.  Synchronises `stream`. */
+int dwf_selftest_wait_timeout(int* gave_up, void* stream);
+
 /* ------------------------------------------------------------------ solvers */
 
 /* Red-black preconditioned CGNR (Sec. 5.1): solve D_DW x = b for a full

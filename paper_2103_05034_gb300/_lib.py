@@ -107,6 +107,7 @@ _SIGS = {
     "dwf_norm2": (I, [P, C.POINTER(D), P, I64, I, P]),
     "dwf_cdot": (I, [P, C.POINTER(D), P, P, I64, I, P]),
     "dwf_norm2_noalloc": (I, [C.POINTER(D), P, I64, I, P]),
+    "dwf_selftest_wait_timeout": (I, [C.POINTER(C.c_int), P]),
     "rbcg_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
     "dwf_power_max": (I, [P, C.POINTER(D), P, D, I, I, P]),
     "dwf_force": (I, [P, P, P, C.POINTER(D), I, I, P]),

@@ -240,3 +240,22 @@ def test_row_block_variant_rejected_where_it_does_not_tile():
         ops.dwf_set_hop_variant(ctx, F32, 16)
     assert e.value.code == DWF_EINVAL
     ctx.close()
+
+
+def test_bounded_waits_give_up_and_report():
+    """Failure detection without a GPU fault: a poll on a counter and an
+    mbarrier wait that nothing completes each give up after about a
+    millisecond, the status reaches the host as DWF_ETIMEOUT, and the context
+    keeps working afterwards."""
+    import ctypes as C
+    from paper_2103_05034_gb300._lib import DWF_ETIMEOUT
+    gave_up = (C.c_int * 2)(-1, -1)
+    code = _lib.lib().dwf_selftest_wait_timeout(gave_up, None)
+    assert code == DWF_ETIMEOUT
+    assert list(gave_up) == [1, 1]
+    L, Ls = (4, 4, 2, 2), 8
+    ctx = ops.Context(L, Ls, M5, synth.random_gauge(L, 0.5, 8))
+    a = ctx.new_half(F32)
+    a.fill_(1.0)
+    assert ops.dwf_norm2(ctx, a) == pytest.approx(a.numel() / 2 * 2.0, rel=1e-6)
+    ctx.close()
