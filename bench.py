@@ -424,6 +424,10 @@ def run_ours(args):
             line["coarse_apply_tc"] = coarse_apply_measure(ctx, w, "tf32", 3, 20)
         except Exception as e:
             line["coarse_apply_tc"] = {"error": str(e)}
+        try:  # the four pseudofermion solves of the force workload, batched vs one by one
+            line["batched_solves"] = batched_solves_measure(ctx, 1e-10)
+        except Exception as e:
+            line["batched_solves"] = {"error": str(e)}
         if args.mg_compare:
             try:
                 line["mg_vs_fp64"] = mg_vs_fp64(ctx, w, b, bd, args.tol)
@@ -438,6 +442,50 @@ def run_ours(args):
     if line is not None:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_solves_measure(ctx, tol):
+    """The pseudofermion solves of the force workload: x_i = (M_pc(m_i)^dag
+    M_pc(m_i))^-1 phi_i for the Hasenbusch masses 0.01, 0.05, 0.2, 1.0 on the
+    context's lattice (Gaussian FP64 phi_i, seeded), once as one batch
+    (rbcg_normal_solve_batch) and once as four single-system solves; FP32
+    inner CG, FP64 reliable updates, tol on the FP64 residual.  Wall time of
+    each after one warm call, and the algorithmic hopping bytes each moved."""
+    import torch
+
+    from paper_2103_05034_gb300 import ops
+    from paper_2103_05034_gb300._lib import SOLVE_MIXED_F32
+
+    masses = [0.01, 0.05, 0.2, 1.0]
+    n, nh = len(masses), ctx.half_numel()
+    gen = torch.Generator(device="cuda").manual_seed(synth.SEED_SOURCE + 5)
+    phi = torch.randn(n * nh, generator=gen, device="cuda", dtype=torch.float64)
+    x = torch.zeros_like(phi)
+    xs, ps = x.view(n, -1), phi.view(n, -1)
+
+    def batch():
+        return ops.rbcg_normal_solve_batch(ctx, x, phi, masses, tol, 100000, SOLVE_MIXED_F32)
+
+    def singles():
+        return [ops.rbcg_normal_solve(ctx, xs[i], ps[i], m, tol, 100000, SOLVE_MIXED_F32)
+                for i, m in enumerate(masses)]
+
+    res = {"masses": masses, "tol": tol, "policy": "FP32 inner, FP64 reliable updates"}
+    for name, fn in (("batch", batch), ("singles", singles)):
+        fn()
+        torch.cuda.synchronize()
+        ops.dwf_reset_counters(ctx)
+        t0 = time.perf_counter()
+        st = fn()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        launches, hbytes = ops.dwf_counters(ctx)
+        res[name] = {"seconds": sec, "iterations": [s["iterations"] for s in st],
+                     "reliable_updates": [s["reliable_updates"] for s in st],
+                     "true_residual": [s["true_residual"] for s in st],
+                     "hop_GBs_algorithmic": hbytes / sec / 1e9, "launches": int(launches)}
+    res["speedup_batch_vs_singles"] = res["singles"]["seconds"] / res["batch"]["seconds"]
+    return res
 
 
 def coarse_apply_measure(ctx, w, prec_name, warmup, steps):
@@ -616,6 +664,12 @@ def run_rows(args):
     emit("a4", "rbcg_solve mixed FP32/FP64", ms, hop_bytes(solve), "GB/s", hbm, "hbm",
          iterations=st["iterations"], true_residual=st["true_residual"],
          note="achieved = algorithmic hopping bytes of the whole solve / its time")
+    bs = batched_solves_measure(ctx, 1e-10)
+    emit("a4", "rbcg_normal_solve_batch, masses 0.01 0.05 0.2 1.0", 1e3 * bs["batch"]["seconds"],
+         bs["batch"]["hop_GBs_algorithmic"] * bs["batch"]["seconds"] * 1e9, "GB/s", hbm, "hbm",
+         singles_ms=1e3 * bs["singles"]["seconds"], speedup_batch_vs_singles=bs["speedup_batch_vs_singles"],
+         iterations=bs["batch"]["iterations"], true_residual=bs["batch"]["true_residual"],
+         note="one warm call timed on the host clock; achieved = algorithmic hopping bytes / time")
     f = lambda: ops.dwf_norm2(ctx, a32)
     emit("a5", "dwf_norm2 F32 (half field)", timed(f), nh * 4.0, "GB/s", hbm, "hbm")
     f = lambda: ops.dwf_cdot(ctx, a64, a64)

@@ -233,6 +233,34 @@ int rbcg_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int 
 int rbcg_normal_solve(dwf_ctx* ctx, void* x, const void* phi, double mf, double tol, int maxiter,
                       int policy, dwf_solve_stats* stats, void* stream);
 
+/* Batched red-black CGNR (Sec. 5.1 operator; several pseudofermion masses on
+ * one gauge field, as in the HMC of Sec. 6): solves D_DW(mf[i]) x_i = b_i for
+ * i < nrhs (1 <= nrhs <= 64), each rhs with its own mass.  b and x hold nrhs
+ * full FP64 fields back to back, each laid out as for rbcg_solve (even half,
+ * then odd half); both host or both device, 16-byte aligned.  Each CG
+ * iteration is one set of hopping launches over the systems still iterating
+ * (the links are read once per launch for all of them); each system keeps its
+ * own CG scalars and takes its own FP64 reliable updates, when the
+ * single-system solver would.  A system whose FP64 true residual has reached
+ * tol leaves the batch (its vectors are moved behind the active ones), so the
+ * launches shrink as the heavier masses converge.  stats (NULL or nrhs
+ * entries) receives per-system iterations (the iteration at which it reached
+ * tol), reliable updates, fine matmuls, true residuals and status; seconds is
+ * the wall time of the whole batch.  A zero source gives x_i = 0.  policy
+ * DWF_SOLVE_F64 or DWF_SOLVE_MIXED_F32.  Returns DWF_ENOCONV if any system
+ * missed tol after maxiter iterations (x is still written), DWF_EINVAL for
+ * bad arguments or a non-finite mass.  Workspace: about 18 FP64 half fields
+ * per system.  Synchronises. */
+int rbcg_solve_batch(dwf_ctx* ctx, void* x, const void* b, const double* mf, int nrhs, double tol,
+                     int maxiter, int policy, dwf_solve_stats* stats, void* stream);
+
+/* Batched form of rbcg_normal_solve: M_pc(mf[i])^dag M_pc(mf[i]) x_i = phi_i
+ * for i < nrhs, with phi and x nrhs FP64 even half fields back to back in
+ * device memory (x must not alias phi).  Same batching, per-system reliable
+ * updates, stats and errors as rbcg_solve_batch.  Synchronises. */
+int rbcg_normal_solve_batch(dwf_ctx* ctx, void* x, const void* phi, const double* mf, int nrhs, double tol,
+                            int maxiter, int policy, dwf_solve_stats* stats, void* stream);
+
 /* Pseudofermion force (HMC context of Sec. 6; the paper prints no force, it
  * is derived for the Schur operator of Sec. 5.1): for each of npf even fields
  * X_i = (M_pc^dag M_pc)^-1 phi_i (mass mf[i], host array) this adds to

@@ -252,6 +252,7 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
     hp.cg_r = h.cg_r;
     hp.cg_p = h.cg_p;
     hp.cg_alpha = h.cg_alpha;
+    hp.cg_astride = h.cg_alpha_stride;
     hp.cg_x32 = h.cg_x32;
   }
   int rc;
@@ -593,23 +594,6 @@ extern "C" int dwf_cdot(dwf_ctx* c, double* result2, const void* a, const void* 
 // ------------------------------------------------------------------ red-black CGNR
 namespace {
 
-enum {
-  WS_B = 2,     // full FP64 source (host input)
-  WS_X = 3,     // full FP64 solution (host output)
-  WS_BP = 4,    // even FP64 b'_e
-  WS_RHS = 5,   // even FP64 M_pc^dag b'_e
-  WS_RHI = 6,   // even FP64 residual / scratch
-  WS_YHI = 7,   // even FP64 temporary
-  WS_OHI = 8,   // odd FP64 temporary
-  WS_XLO = 9,   // even inner x
-  WS_RLO = 10,  // even inner r
-  WS_P = 11,    // even p
-  WS_AP = 12,   // even Ap
-  WS_YLO = 13,  // even y = M_pc p
-  WS_OLO = 14,  // odd temporary
-  WS_FULL = 15  // full FP64 temporary (true residual)
-};
-
 struct Timer {
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double sec() const {
@@ -678,6 +662,7 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
   const double delta = 0.1;
   double true_res = 0, rr_hi = 0, rho = 1, rr_max = 0, rr_lo = 0;
   bool have_x = false;
+  bool restart_p = false;  // next reliable update restarts the directions, p = r
   // FP16 storage keeps the inner system scaled: r_lo = r / sigma with sigma
   // = |r| / sqrt(n) at every reliable update, so that the stored components
   // are of order one (unscaled they would fall below FP16's range as the
@@ -778,8 +763,30 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
     if (r) return r;
     r = norm2_dev(c, rlo, he, plo, S_RR, st);
     if (r) return r;
-    r = read_scalars(c, S_TMP2, 2, st);
+    // The next step length alpha = |r|^2 / <p, A p> assumes <r, p> = |r|^2,
+    // which holds for the recursive residual but not for the recomputed one.
+    // With p kept across the update (FP32 and FP64 inner vectors) it is
+    // restored by p += (1 - <r, p> / |r|^2) r; without it the inner CG can
+    // stall or diverge once the two residuals differ by more than rounding.
+    const bool fix_p = had_x && !scaled && !restart_p;
+    if (fix_p) {
+      int np = 0;
+      r = blas_cdot_partials(c, rlo, p, he, plo, st, &np);
+      if (r) return r;
+      r = blas_finalize(c, np, 2, S_TMP0, st);
+      if (r) return r;
+    }
+    r = read_scalars(c, S_RR, S_TMP3 + 1 - S_RR, st);
     if (r) return r;
+    if (fix_p && c->hscal[S_RR] > 0) {
+      const double rr = c->hscal[S_RR];
+      r = blas_caxpy(c, 1.0 - c->hscal[S_TMP0] / rr, -c->hscal[S_TMP1] / rr, rlo, plo, p, plo, he, st);
+      if (r) return r;
+    } else if (had_x && !scaled && restart_p) {
+      r = blas_copy(c, p, plo, rlo, plo, he, st);
+      if (r) return r;
+    }
+    restart_p = false;
     true_res = sqrt(c->hscal[S_TMP2]) / bnorm;
     rr_hi = c->hscal[S_TMP3];
     rho = rr_hi > 0 ? sqrt(c->hscal[S_TMP2] / rr_hi) : 1.0;
@@ -816,9 +823,14 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
       if (!isfinite(rr_lo)) return dwf_fail(c, DWF_ENAN, "NaN in CG residual");
       if (rr_lo > rr_max) rr_max = rr_lo;
       const double predicted = rho * sqrt(rr_lo) / bnorm;
+      // a recursive residual grown a hundredfold above its value at the last
+      // reliable update means the directions have lost conjugacy: update and
+      // restart them
+      const bool diverging = rr_lo > 1e4 * rr_hi;
+      if (diverging) restart_p = true;
       // FP16 inner vectors also take a reliable update (a restart) every 64
       // iterations, in case their recursive residual stalls above delta
-      if (rr_lo < delta * delta * rr_max || predicted <= tol || it == maxiter ||
+      if (rr_lo < delta * delta * rr_max || predicted <= tol || it == maxiter || diverging ||
           (scaled && it - last_reliable_it >= 64)) {
         last_reliable_it = it;
         rc = reliable();

@@ -81,6 +81,35 @@ __global__ void __launch_bounds__(BT) k_finalize(const double* part, int n, int 
   }
 }
 
+// Batched finalize: CTA i sums the n partials part[i * n ..] into bank i.
+__global__ void __launch_bounds__(BT) k_finalize_batch(const double* part, int n, double* dscal, int dst,
+                                                       int mode) {
+  __shared__ double sh[BT / 32];
+  const double* pi = part + (size_t)blockIdx.x * n;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += BT) acc += pi[i];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    double* q = dscal + S_BANK0 + blockIdx.x * S_BANK;
+    q[dst] = t;
+    if (mode == 1) {
+      q[S_ALPHA] = q[S_RR] / q[S_PAP];
+    } else if (mode == 2) {
+      q[S_BETA] = q[S_RRNEW] / q[S_RR];
+      q[S_RR] = q[S_RRNEW];
+    }
+  }
+}
+
+// Exchange two buffers of n 16-byte words.
+__global__ void __launch_bounds__(BT) k_swap(uint4* a, uint4* b, long long n) {
+  for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
+    const uint4 t = a[i];
+    a[i] = b[i];
+    b[i] = t;
+  }
+}
+
 template <int PX, int PY>
 __global__ void __launch_bounds__(BT) k_axpby(double a, const typename Prec<PX>::S* x, double b,
                                               typename Prec<PY>::S* y, long long n) {
@@ -136,11 +165,14 @@ __global__ void __launch_bounds__(BT) k_cg_xr(typename Prec<P>::S* x, typename P
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// p = r + beta p; segment blockIdx.y (n elements) takes dscal[ibeta + y * bstride]
 template <int P>
 __global__ void __launch_bounds__(BT) k_cg_p(typename Prec<P>::S* p, const typename Prec<P>::S* r,
-                                             long long n, const double* dscal, int ibeta) {
+                                             long long n, const double* dscal, int ibeta, int bstride) {
   typedef typename Prec<P>::R R;
-  const R beta = (R)dscal[ibeta];
+  const R beta = (R)dscal[ibeta + blockIdx.y * bstride];
+  p += (size_t)blockIdx.y * n;
+  r += (size_t)blockIdx.y * n;
   for (long long i = (long long)blockIdx.x * BT + threadIdx.x; i < n; i += (long long)gridDim.x * BT) {
     auto pv = ld_c(p + i);
     const auto rv = ld_c(r + i);
@@ -315,7 +347,35 @@ int blas_cg_p(dwf_ctx* c, void* p, const void* r, int64_t n, int prec, int ibeta
   c->launches++;
   DWF_PREC_SWITCH(prec, (k_cg_p<P><<<g, BT, 0, st>>>((typename Prec<P>::S*)p,
                                                        (const typename Prec<P>::S*)r, n, c->dscal,
-                                                       ibeta)));
+                                                       ibeta, 0)));
+  return DWF_OK;
+}
+
+int blas_cg_p_batch(dwf_ctx* c, void* p, const void* r, int64_t n, int nseg, int prec, cudaStream_t st) {
+  if (nseg < 1 || nseg > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "nseg out of range");
+  int g = grid_for(n) / nseg;
+  if (g < 64) g = 64;
+  c->launches++;
+  DWF_PREC_SWITCH(prec, (k_cg_p<P><<<dim3(g, nseg), BT, 0, st>>>((typename Prec<P>::S*)p,
+                                                                   (const typename Prec<P>::S*)r, n,
+                                                                   c->dscal, S_BANK0 + S_BETA, S_BANK)));
+  return DWF_OK;
+}
+
+int blas_finalize_batch(dwf_ctx* c, int nparts_per, int nseg, int dst, int mode, cudaStream_t st) {
+  if (nseg < 1 || nseg > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "nseg out of range");
+  c->launches++;
+  k_finalize_batch<<<nseg, BT, 0, st>>>(c->partials, nparts_per, c->dscal, dst, mode);
+  return DWF_OK;
+}
+
+int blas_swap(dwf_ctx* c, void* a, void* b, size_t bytes, cudaStream_t st) {
+  if ((bytes & 15) || ((uintptr_t)a & 15) || ((uintptr_t)b & 15))
+    return dwf_fail(c, DWF_EINVAL, "swap needs 16-byte aligned buffers and sizes");
+  if (a == b || bytes == 0) return DWF_OK;
+  const long long n = (long long)(bytes / 16);
+  c->launches++;
+  k_swap<<<grid_for(n), BT, 0, st>>>((uint4*)a, (uint4*)b, n);
   return DWF_OK;
 }
 

@@ -50,7 +50,8 @@ struct HopParams {
   void* cg_x;
   void* cg_r;
   const void* cg_p;
-  const double* cg_alpha;  // device scalar
+  const double* cg_alpha;  // device scalars, cg_alpha[rhs * cg_astride]
+  int cg_astride;          // 0: one alpha for every rhs
   int cg_x32;              // x stored in FP32 (with FP16-storage r and p)
   double m[DWF_MAX_RHS];
   double kappa[DWF_MAX_RHS];
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
       float2* xs32 = (float2*)p.cg_x + off;
       S* rs = (S*)p.cg_r + off;
       const S* ps = (const S*)p.cg_p + off;
-      const R alpha = (R)(*p.cg_alpha);
+      const R alpha = (R)p.cg_alpha[(size_t)rhs * p.cg_astride];
       const bool x32 = (P == DWF_F16S) && p.cg_x32;
 #pragma unroll
       for (int c = 0; c < 12; c++) {

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::
       S* xs = (S*)p.cg_x + off;
       S* rs = (S*)p.cg_r + off;
       const S* ps = (const S*)p.cg_p + off;
-      const float al = (float)(*p.cg_alpha);
+      const float al = (float)p.cg_alpha[(size_t)rhs * p.cg_astride];
       const f2p AL = pk2(al, al), NAL = pk2(-al, -al);
       float2* xs32 = (float2*)p.cg_x + off;
       const bool x32 = (P == DWF_F16S) && p.cg_x32;

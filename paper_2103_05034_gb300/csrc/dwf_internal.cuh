@@ -11,7 +11,7 @@
 #include "../../include/dwfmg.h"
 
 #define DWF_MAX_RHS 64
-#define DWF_NWS 32  // workspace slots
+#define DWF_NWS 40  // workspace slots
 #define CG_SMALL_BYTES 384  // status and barrier counters of the persistent coarse CG
 
 // ------------------------------------------------------------------ complex helpers
@@ -171,6 +171,7 @@ struct HopLaunch {
   void* cg_r;
   const void* cg_p;
   const double* cg_alpha;
+  int cg_alpha_stride;  // doubles between consecutive rhs' alpha (0: shared)
   int cg_x32;          // x is FP32 whatever the field precision (FP16-storage CG)
 };
 
@@ -199,6 +200,16 @@ int blas_cg_xr(dwf_ctx* c, void* x, void* r, const void* p, const void* Ap, int6
                int ialpha, cudaStream_t st, int* nparts);
 //   p = r + beta p
 int blas_cg_p(dwf_ctx* c, void* p, const void* r, int64_t n, int prec, int ibeta, cudaStream_t st);
+// Batched forms over nseg consecutive vectors of n elements each, segment i
+// using the scalar bank dscal[S_BANK0 + i * S_BANK]:
+//   p_i = r_i + beta_i p_i
+int blas_cg_p_batch(dwf_ctx* c, void* p, const void* r, int64_t n, int nseg, int prec, cudaStream_t st);
+//   sum the partials of each segment (nparts_per consecutive doubles) into its
+//   bank slot dst, then mode 1: alpha = rr/pAp; 2: beta = rrnew/rr, rr = rrnew;
+//   mode 0: the sums only
+int blas_finalize_batch(dwf_ctx* c, int nparts_per, int nseg, int dst, int mode, cudaStream_t st);
+// Exchange the contents of two device buffers (16-byte aligned, bytes % 16 == 0).
+int blas_swap(dwf_ctx* c, void* a, void* b, size_t bytes, cudaStream_t st);
 // z = a x + b y + c z (same precision)
 int blas_axpbypcz(dwf_ctx* c, double a, const void* x, double b, const void* y, double cz, void* z,
                   int64_t n, int prec, cudaStream_t st);
@@ -220,6 +231,30 @@ int read_scalars(dwf_ctx* c, int first, int n, cudaStream_t st);
 // dscal[dst] = dscal[num] / dscal[den]
 int blas_scalar_div(dwf_ctx* c, int dst, int num, int den, cudaStream_t st);
 
+
+// Workspace slots of the red-black solvers (single and batched).  The MG
+// setup uses 16..27, the force 28..29, the autotuner 30..31.
+enum {
+  WS_B = 2,      // full FP64 source (host input)
+  WS_X = 3,      // full FP64 solution (host output)
+  WS_BP = 4,     // even FP64 b'_e
+  WS_RHS = 5,    // even FP64 M_pc^dag b'_e
+  WS_RHI = 6,    // even FP64 residual / scratch
+  WS_YHI = 7,    // even FP64 temporary
+  WS_OHI = 8,    // odd FP64 temporary
+  WS_XLO = 9,    // even inner x
+  WS_RLO = 10,   // even inner r
+  WS_P = 11,     // even p
+  WS_AP = 12,    // even Ap
+  WS_YLO = 13,   // even y = M_pc p
+  WS_OLO = 14,   // odd temporary
+  WS_FULL = 15,  // full FP64 temporary (true residual)
+  WS_BE = 32,    // batched solve: sources split by parity, [nrhs][half]
+  WS_BO = 33,
+  WS_XE = 34,    // batched solve: solutions split by parity
+  WS_XO = 35
+};
+
 // Device scalar slots.
 enum {
   S_RR = 0,    // |r|^2
@@ -231,5 +266,12 @@ enum {
   S_TMP1 = 9,
   S_TMP2 = 10,
   S_TMP3 = 11,
-  S_NSCAL = 32
+  // batched CG: slot i owns the bank dscal[S_BANK0 + i * S_BANK .. +S_BANK-1]
+  // with the offsets S_RR .. S_RRNEW above plus these (bank-relative)
+  S_BT0 = 6,
+  S_BT1 = 7,
+  S_BDOT = 8,  // two doubles: <r, p>
+  S_BANK0 = 32,
+  S_BANK = 10,
+  S_NSCAL = S_BANK0 + S_BANK * DWF_MAX_RHS
 };

@@ -930,20 +930,20 @@ extern "C" int mg_solve(dwf_mg* G, void* x, const void* b, double tol, dwf_solve
   void* db = (void*)b;
   void* dx = x;
   if (host_b) {
-    db = ws(c, 2, n * 16);  // solver slot WS_B
+    db = ws(c, WS_B, n * 16);
     if (!db) return dwf_fail(c, DWF_ENOMEM, "ws");
     DWF_CUDA(c, cudaMemcpyAsync(db, b, n * 16, cudaMemcpyHostToDevice, st));
   }
   if (host_x) {
-    dx = ws(c, 3, n * 16);  // WS_X
+    dx = ws(c, WS_X, n * 16);
     if (!dx) return dwf_fail(c, DWF_ENOMEM, "ws");
   }
-  void* rhs = ws(c, 15, n * 16);                     // Gamma_5 b (FP64)
-  void* r64 = ws(c, 4, n * 16);                      // FP64 residual
-  void* t64 = ws(c, 5, n * 16);                      // FP64 temporary
-  void* r32 = ws(c, 9, n * 8);                       // FP32 residual
-  void* zs = ws(c, 10, (size_t)n * 8 * nk);          // directions
-  void* wsv = ws(c, 11, (size_t)n * 8 * nk);         // H directions
+  void* rhs = ws(c, WS_FULL, n * 16);                // Gamma_5 b (FP64)
+  void* r64 = ws(c, WS_BP, n * 16);                  // FP64 residual
+  void* t64 = ws(c, WS_RHS, n * 16);                 // FP64 temporary
+  void* r32 = ws(c, WS_XLO, n * 8);                  // FP32 residual
+  void* zs = ws(c, WS_RLO, (size_t)n * 8 * nk);      // directions
+  void* wsv = ws(c, WS_P, (size_t)n * 8 * nk);       // H directions
   if (!rhs || !r64 || !t64 || !r32 || !zs || !wsv) return dwf_fail(c, DWF_ENOMEM, "mg_solve workspace");
   const double mf[1] = {G->p.mf};
   int rc = chiral(c, rhs, db, 1, DWF_F64, 1, st);  // placeholder overwritten below

@@ -326,6 +326,27 @@ def rbcg_normal_solve(ctx, x, phi, mf, tol, maxiter=100000, policy=_lib.SOLVE_MI
     return st.as_dict()
 
 
+def _batch_solve(fn, ctx, x, b, masses, tol, maxiter, policy):
+    n = len(masses)
+    mf = (C.c_double * n)(*[float(m) for m in masses])
+    st = (SolveStats * n)()
+    check(fn(ctx.h, _ptr(x), _ptr(b), mf, n, tol, maxiter, policy, st, _stream()), ctx.h)
+    return [s.as_dict() for s in st]
+
+
+def rbcg_solve_batch(ctx, x, b, masses, tol, maxiter=100000, policy=_lib.SOLVE_MIXED_F32):
+    """Red-black CGNR for len(masses) full FP64 fields stored back to back in
+    b (host or device; x the same kind), rhs i with mass masses[i], solved as
+    one batch.  Returns one stats dict per rhs."""
+    return _batch_solve(lib().rbcg_solve_batch, ctx, x, b, masses, tol, maxiter, policy)
+
+
+def rbcg_normal_solve_batch(ctx, x, phi, masses, tol, maxiter=100000, policy=_lib.SOLVE_MIXED_F32):
+    """x_i = (M_pc(m_i)^dag M_pc(m_i))^-1 phi_i for FP64 even half fields
+    stored back to back on the device.  Returns one stats dict per rhs."""
+    return _batch_solve(lib().rbcg_normal_solve_batch, ctx, x, phi, masses, tol, maxiter, policy)
+
+
 def dwf_autotune(ctx, prec=F32, reps=20):
     """Pick the fastest hopping-kernel variant for this lattice; returns
     (variant, ms per launch)."""
