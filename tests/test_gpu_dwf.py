@@ -149,6 +149,25 @@ def test_rbcg_solution_parity(policy):
     ctx.close()
 
 
+@pytest.mark.parametrize("Ls,mf", [(4, 0.05), (8, 0.01)])
+def test_rbcg_mixed_reaches_tight_tolerance(Ls, mf):
+    """A gauge field (4^4, eps 0.3, seed 43) on which the FP32-inner CG,
+    keeping its direction across reliable updates without restoring
+    <r, p> = |r|^2, diverged below a true residual of about 1e-6: every
+    policy must reach 1e-10."""
+    L = (4, 4, 4, 4)
+    U = synth.random_gauge(L, 0.3, 43)
+    b = synth.gaussian_spinor(L, Ls, 44)
+    ctx = ops.Context(L, Ls, M5, U)
+    bd = full_dev(b, L, F64)
+    for policy in (SOLVE_F64, SOLVE_MIXED_F32, _lib.SOLVE_MIXED_F16):
+        x = torch.zeros_like(bd)
+        st = ops.rbcg_solve(ctx, x, bd, mf, 1e-10, 5000, policy)
+        res = krylov.true_residual(U, dev_to_full_canon(x, L, Ls), b, M5, mf)
+        assert res <= 1e-10 * 1.01, (policy, st)
+    ctx.close()
+
+
 def test_rbcg_host_buffers():
     L, Ls, mf = (4, 4, 4, 4), 8, 0.05
     U = synth.random_gauge(L, 0.3, 3)
