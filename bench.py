@@ -526,6 +526,7 @@ def coarse_apply_measure(ctx, w, prec_name, warmup, steps):
         z.record()
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(z))
+    ops.coarse_apply_status(Cc)  # raises if a bounded wait of any timed call gave up
     ms = float(np.median(ts))
     flop = 8.0 * 9 * nb * nb * nrhs * Cc.nc
     abytes = Cc.nc * 9 * nb * nb * 8 + 2 * Cc.nc * nb * nrhs * 8  # FP32 operator + in/out vectors

@@ -334,11 +334,17 @@ int coarse_export(const dwf_coarse* coarse, void* A, int* dims);
  * prec DWF_F32: CUDA cores, FP32 arithmetic (any nb, nrhs).  prec DWF_TF32:
  * 5th-generation tensor cores (tcgen05.mma kind::tf32, inputs rounded to TF32,
  * FP32 accumulation in tensor memory) for nb = 32, an even number of coarse
- * sites and nrhs in {16, 32, 64}; other shapes return DWF_EINVAL.  The TF32
- * path synchronises `stream` (it checks the kernel's bounded-wait flag and
- * returns DWF_ETIMEOUT if a wait gave up). */
+ * sites and nrhs in {16, 32, 64}; other shapes return DWF_EINVAL.  Both
+ * paths are asynchronous on `stream`.  The tensor-core kernel's waits are
+ * bounded: one that gives up raises a sticky flag of the operator, which a
+ * later TF32 coarse_apply returns as DWF_ETIMEOUT once its copy to the host
+ * has landed, and coarse_apply_status returns after synchronising. */
 #define DWF_TF32 3
 int coarse_apply(dwf_coarse* coarse, void* out, const void* in, int nrhs, int prec, void* stream);
+/* Synchronise `stream` and return DWF_ETIMEOUT if a bounded wait of an
+ * earlier tensor-core coarse_apply on this operator gave up (the flag is then
+ * cleared), else DWF_OK. */
+int coarse_apply_status(dwf_coarse* coarse, void* stream);
 /* Coarse solve of Table 1 ("Coarse solver: CGNR"): CG on A^2 e = A r for one
  * FP32 coarse vector, stopping when the normal residual is below tol times its
  * initial value or after maxiter iterations (*iters receives the count). */

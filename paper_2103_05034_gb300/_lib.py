@@ -122,6 +122,7 @@ _SIGS = {
     "coarse_destroy": (I, [P]),
     "coarse_export": (I, [P, P, C.POINTER(C.c_int)]),
     "coarse_apply": (I, [P, P, P, I, I, P]),
+    "coarse_apply_status": (I, [P, P]),
     "coarse_solve": (I, [P, P, P, D, I, C.POINTER(C.c_int), P]),
     "dwf_restrict": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, P]),
     "dwf_prolong": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, I, P]),

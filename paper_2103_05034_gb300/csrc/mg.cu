@@ -22,7 +22,9 @@ struct dwf_coarse {
   float* At;     // tensor-core copy (real form, TF32, K-major), built on first use
   float* Bt;     // tensor-core right-hand sides (real form, TF32), per apply
   size_t Bt_bytes;
-  int* err;      // device error flag of the tensor-core kernel
+  int* err;      // device error flag of the tensor-core kernel (sticky)
+  int* err_host; // pinned mirror, copied after every tensor-core apply
+  cudaEvent_t err_ready;  // recorded after that copy
   void* ws[6];
   size_t ws_bytes[6];
   int* cg_acc;   // when set: coarse CG runs without host synchronisation and
@@ -474,6 +476,8 @@ extern "C" int coarse_destroy(dwf_coarse* C) {
   if (C->At) cudaFree(C->At);
   if (C->Bt) cudaFree(C->Bt);
   if (C->err) cudaFree(C->err);
+  if (C->err_host) cudaFreeHost(C->err_host);
+  if (C->err_ready) cudaEventDestroy(C->err_ready);
   for (int i = 0; i < 6; i++)
     if (C->ws[i]) cudaFree(C->ws[i]);
   delete C;
@@ -509,22 +513,47 @@ extern "C" int coarse_apply(dwf_coarse* C, void* out, const void* in, int nrhs, 
   if (prec != DWF_TF32) return dwf_fail(c, DWF_EINVAL, "coarse_apply precision: DWF_F32 or DWF_TF32");
   if (((uintptr_t)out & 15) || ((uintptr_t)in & 15)) return dwf_fail(c, DWF_EINVAL, "alignment");
   if (!C->err) {
-    if (cudaMalloc(&C->err, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&C->err, sizeof(int)) != cudaSuccess || cudaMallocHost(&C->err_host, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&C->err_ready, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       return dwf_fail(c, DWF_ENOMEM, "coarse error flag");
     }
+    *C->err_host = 0;
+    DWF_CUDA(c, cudaMemsetAsync(C->err, 0, sizeof(int), st));
+    DWF_CUDA(c, cudaEventRecord(C->err_ready, st));
   }
-  DWF_CUDA(c, cudaMemsetAsync(C->err, 0, sizeof(int), st));
+  // The kernel's bounded waits report through a sticky device flag that is
+  // copied to pinned host memory after every apply; a flag raised by an
+  // earlier apply whose copy has landed is returned here, without waiting.
+  if (cudaEventQuery(C->err_ready) == cudaSuccess && *C->err_host) {
+    *C->err_host = 0;
+    DWF_CUDA(c, cudaMemsetAsync(C->err, 0, sizeof(int), st));
+    return dwf_fail(c, DWF_ETIMEOUT, "tensor-core coarse apply: a bounded barrier wait gave up (earlier call)");
+  }
+  cudaGetLastError();  // cudaEventQuery's cudaErrorNotReady is not an error
   int rc = coarse_apply_tc(c, (float2*)out, (const float2*)in, C->A32, &C->At, &C->Bt, &C->Bt_bytes, C->nb, C->g.nc, C->g.Lc, nrhs,
                            C->err, st);
   if (rc == DWF_EINVAL)
     return dwf_fail(c, rc, "tensor-core coarse apply needs nb = 32, an even number of coarse sites, nrhs 16/32/64");
   if (rc) return dwf_fail(c, rc, "tensor-core coarse apply");
+  DWF_CUDA(c, cudaMemcpyAsync(C->err_host, C->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DWF_CUDA(c, cudaEventRecord(C->err_ready, st));
   DWF_CUDA(c, cudaGetLastError());
-  int herr = 0;
-  DWF_CUDA(c, cudaMemcpyAsync(&herr, C->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  DWF_CUDA(c, cudaStreamSynchronize(st));
-  if (herr) return dwf_fail(c, DWF_ETIMEOUT, "tensor-core coarse apply: a bounded barrier wait gave up");
+  return DWF_OK;
+}
+
+extern "C" int coarse_apply_status(dwf_coarse* C, void* stream) {
+  if (!C) return DWF_EINVAL;
+  dwf_ctx* c = C->ctx;
+  DWF_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+  if (!C->err_host) return DWF_OK;
+  DWF_CUDA(c, cudaEventSynchronize(C->err_ready));
+  if (*C->err_host) {
+    *C->err_host = 0;
+    DWF_CUDA(c, cudaMemsetAsync(C->err, 0, sizeof(int), (cudaStream_t)stream));
+    DWF_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+    return dwf_fail(c, DWF_ETIMEOUT, "tensor-core coarse apply: a bounded barrier wait gave up");
+  }
   return DWF_OK;
 }
 

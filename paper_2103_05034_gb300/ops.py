@@ -233,6 +233,12 @@ def coarse_apply(coarse, out, inp, nrhs=1, prec=F32):
     return out
 
 
+def coarse_apply_status(coarse):
+    """Synchronise and raise if a bounded wait of an earlier tensor-core
+    coarse_apply on this operator gave up."""
+    check(lib().coarse_apply_status(coarse.h, _stream()), coarse.ctx.h)
+
+
 def coarse_solve(coarse, e, r, tol, maxiter=1000):
     it = C.c_int()
     check(lib().coarse_solve(coarse.h, _ptr(e), _ptr(r), tol, maxiter, C.byref(it), _stream()),

@@ -341,6 +341,8 @@ def test_coarse_apply_tensor_cores(nrhs, L):
     out.zero_()
     ops.coarse_apply(C, out, vd, nrhs, prec=TF32)
     assert rel(layout.real_to_complex(out.double().cpu().numpy()).reshape(v.shape), want) < 3e-3
+    # the applies are asynchronous; no bounded wait gave up in any of them
+    ops.coarse_apply_status(C)
     C.close()
     ctx.close()
 
