@@ -232,8 +232,8 @@ int read_scalars(dwf_ctx* c, int first, int n, cudaStream_t st);
 int blas_scalar_div(dwf_ctx* c, int dst, int num, int den, cudaStream_t st);
 
 
-// Workspace slots of the red-black solvers (single and batched).  The MG
-// setup uses 16..27, the force 28..29, the autotuner 30..31.
+// Workspace slots of the red-black solvers (single and batched) and the
+// force.  The MG setup uses 16..27, the autotuner 30..31.
 enum {
   WS_B = 2,      // full FP64 source (host input)
   WS_X = 3,      // full FP64 solution (host output)
@@ -252,7 +252,10 @@ enum {
   WS_BE = 32,    // batched solve: sources split by parity, [nrhs][half]
   WS_BO = 33,
   WS_XE = 34,    // batched solve: solutions split by parity
-  WS_XO = 35
+  WS_XO = 35,
+  WS_FXO = 36,   // force: X_o, Y_e, Y_o of all pseudofermions
+  WS_FYE = 37,
+  WS_FYO = 38
 };
 
 // Device scalar slots.

@@ -58,7 +58,7 @@ __device__ __forceinline__ void outer2(cpx<R> (&o)[9], const cpx<R> (&hx)[2][3],
 }
 
 // Sum over the Ls threads of each site of one 3x3 complex matrix per thread
-// (shared-memory reduction, fixed order), into AB[site][slot] in FP64.
+// (shared-memory reduction, fixed order), added to AB[site][slot] in FP64.
 template <class R, int LS, int SB>
 __device__ __forceinline__ void site_sum(R* red, double2* AB, int slot, const cpx<R> (&o)[9], int sl, int s) {
   constexpr int NT = LS * SB;
@@ -73,24 +73,33 @@ __device__ __forceinline__ void site_sum(R* red, double2* AB, int slot, const cp
     R acc = 0;
     for (int q = 0; q < LS; q++) acc += red[(sl2 * LS + q) * 18 + e];
     double* dst = (double*)(AB + (sl2 * 8 + slot) * 9);
-    dst[e] = (double)acc;
+    dst[e] += (double)acc;
   }
   __syncthreads();
 }
 
 // One CTA: SB checkerboard sites of one parity x Ls threads (s fastest, so
-// the neighbours' spinors are read as contiguous Ls-runs).  Each thread forms
-// the s-slice of A_mu and B_mu for the 4 directions; the Ls contributions are
-// summed per site in shared memory, and 4 threads per site form G_mu in FP64.
+// the neighbours' spinors are read as contiguous Ls-runs), all npf
+// pseudofermions.  Each thread forms the s-slice of A_mu and B_mu for the 4
+// directions; the Ls slices (and the pseudofermions, G being linear in A and
+// B) are summed per site in shared memory, and 4 threads per site form G_mu,
+// reading each link once for all pseudofermions.  The final products run in
+// the fields' precision (FP32 fields: FP32, FP64 fields: FP64), the sums and
+// the force in FP64.
 template <int P, int LS, int SB>
-__global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename Prec<P>::S* Xf,
-                                                 const typename Prec<P>::S* Yf, const double2* links_e,
-                                                 const double2* links_o, int L0, int L1, int L2, int L3, int Vh) {
+__global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename Prec<P>::S* Xe,
+                                                 const typename Prec<P>::S* Xo, const typename Prec<P>::S* Ye,
+                                                 const typename Prec<P>::S* Yo, long long fstride, int npf,
+                                                 const typename Prec<P>::LS* links_e,
+                                                 const typename Prec<P>::LS* links_o, int L0, int L1, int L2, int L3,
+                                                 int Vh) {
   typedef typename Prec<P>::R R;
   typedef typename Prec<P>::S S;
   __shared__ R red[SB * LS * 18];
   __shared__ double2 AB[SB * 8 * 9];  // per site: A_mu (slots 0-3), B_mu (slots 4-7)
   const int tid = threadIdx.x, sl = tid / LS, s = tid - sl * LS;
+  for (int i = tid; i < SB * 8 * 9; i += LS * SB) AB[i] = make_double2(0.0, 0.0);
+  // (the first site_sum's barrier orders these stores before its additions)
   const int p = blockIdx.y;
   const int h = blockIdx.x * SB + sl;
   const bool active = h < Vh;
@@ -106,41 +115,51 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
   x[0] = 2 * xh + ((x[1] + x[2] + x[3] + p) & 1);
   const int Ld[4] = {L0, L1, L2, L3};
   const long long row = 12LL * LS;
-  cpx<R> xb[12], ya[12];
-  const S* Xx = Xf + ((long long)p * Vh + hh) * row + s;
-  const S* Yx = Yf + ((long long)p * Vh + hh) * row + s;
+  // neighbour half-lattice indices in the +mu directions (other parity)
+  int nbh[4];
 #pragma unroll
-  for (int c = 0; c < 12; c++) {
-    xb[c] = active ? ld_c(Xx + c * LS) : cmake<R>(0, 0);
-    ya[c] = active ? ld_c(Yx + c * LS) : cmake<R>(0, 0);
-  }
-  auto dir = [&](auto muc) {
-    constexpr int MU = decltype(muc)::value;
+  for (int mu = 0; mu < 4; mu++) {
     int y[4] = {x[0], x[1], x[2], x[3]};
-    y[MU] = (y[MU] + 1 == Ld[MU]) ? 0 : y[MU] + 1;
+    y[mu] = (y[mu] + 1 == Ld[mu]) ? 0 : y[mu] + 1;
     const long long ylex = y[0] + (long long)L0 * (y[1] + (long long)L1 * (y[2] + (long long)L2 * y[3]));
-    const S* Xy = Xf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row + s;
-    const S* Yy = Yf + ((long long)(1 - p) * Vh + (ylex >> 1)) * row + s;
-    cpx<R> xa[12], yb[12];
+    nbh[mu] = (int)(ylex >> 1);
+  }
+  for (int f = 0; f < npf; f++) {
+    const S* Xs = (p ? Xo : Xe) + f * fstride;  // fields of this site's parity
+    const S* Ys = (p ? Yo : Ye) + f * fstride;
+    const S* Xn = (p ? Xe : Xo) + f * fstride;  // and of the neighbours'
+    const S* Yn = (p ? Ye : Yo) + f * fstride;
+    cpx<R> xb[12], ya[12];
 #pragma unroll
     for (int c = 0; c < 12; c++) {
-      xa[c] = active ? ld_c(Xy + c * LS) : cmake<R>(0, 0);  // X'(x+mu)
-      yb[c] = active ? ld_c(Yy + c * LS) : cmake<R>(0, 0);  // Y'(x+mu)
+      xb[c] = active ? ld_c(Xs + hh * row + c * LS + s) : cmake<R>(0, 0);
+      ya[c] = active ? ld_c(Ys + hh * row + c * LS + s) : cmake<R>(0, 0);
     }
-    cpx<R> hx[2][3], hy[2][3], o[9];
-    proj<R, MU>(hx, xa, R(1));
-    proj<R, MU>(hy, ya, R(1));
-    outer2<R>(o, hx, hy);
-    site_sum<R, LS, SB>(red, AB, MU, o, sl, s);
-    proj<R, MU>(hx, xb, R(-1));
-    proj<R, MU>(hy, yb, R(-1));
-    outer2<R>(o, hx, hy);
-    site_sum<R, LS, SB>(red, AB, 4 + MU, o, sl, s);
-  };
-  dir(std::integral_constant<int, 0>());
-  dir(std::integral_constant<int, 1>());
-  dir(std::integral_constant<int, 2>());
-  dir(std::integral_constant<int, 3>());
+    auto dir = [&](auto muc) {
+      constexpr int MU = decltype(muc)::value;
+      const S* Xy = Xn + nbh[MU] * row + s;
+      const S* Yy = Yn + nbh[MU] * row + s;
+      cpx<R> xa[12], yb[12];
+#pragma unroll
+      for (int c = 0; c < 12; c++) {
+        xa[c] = active ? ld_c(Xy + c * LS) : cmake<R>(0, 0);  // X'(x+mu)
+        yb[c] = active ? ld_c(Yy + c * LS) : cmake<R>(0, 0);  // Y'(x+mu)
+      }
+      cpx<R> hx[2][3], hy[2][3], o[9];
+      proj<R, MU>(hx, xa, R(1));
+      proj<R, MU>(hy, ya, R(1));
+      outer2<R>(o, hx, hy);
+      site_sum<R, LS, SB>(red, AB, MU, o, sl, s);
+      proj<R, MU>(hx, xb, R(-1));
+      proj<R, MU>(hy, yb, R(-1));
+      outer2<R>(o, hx, hy);
+      site_sum<R, LS, SB>(red, AB, 4 + MU, o, sl, s);
+    };
+    dir(std::integral_constant<int, 0>());
+    dir(std::integral_constant<int, 1>());
+    dir(std::integral_constant<int, 2>());
+    dir(std::integral_constant<int, 3>());
+  }
   // G_mu = TA(U A - B U^dag), one thread per (site, mu)
   for (int t = tid; t < SB * 4; t += LS * SB) {
     const int sl2 = t >> 2, mu = t & 3;
@@ -157,33 +176,35 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
     const long long zlex = z[0] + (long long)L0 * (z[1] + (long long)L1 * (z[2] + (long long)L2 * z[3]));
     const double2* A = AB + (sl2 * 8 + mu) * 9;
     const double2* B = AB + (sl2 * 8 + 4 + mu) * 9;
-    const double2* U = (p ? links_o : links_e) + ((long long)h2 * 8 + 2 * mu) * 9;
-    double2 Z[9];
+    const typename Prec<P>::LS* U = (p ? links_o : links_e) + ((long long)h2 * 8 + 2 * mu) * 9;
+    cpx<R> Z[9];
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
       for (int b = 0; b < 3; b++) {
-        double re = 0, im = 0;
+        R re = 0, im = 0;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-          const double2 u = U[a * 3 + k], av = A[k * 3 + b];  // (U A)_ab
-          re += u.x * av.x - u.y * av.y;
-          im += u.x * av.y + u.y * av.x;
-          const double2 bv = B[a * 3 + k], ud = U[b * 3 + k];  // (B U^dag)_ab = B_ak conj(U_bk)
-          re -= bv.x * ud.x + bv.y * ud.y;
-          im -= bv.y * ud.x - bv.x * ud.y;
+          const R ux = (R)U[a * 3 + k].x, uy = (R)U[a * 3 + k].y;  // (U A)_ab
+          const R ax = (R)A[k * 3 + b].x, ay = (R)A[k * 3 + b].y;
+          re += ux * ax - uy * ay;
+          im += ux * ay + uy * ax;
+          const R bx = (R)B[a * 3 + k].x, by = (R)B[a * 3 + k].y;  // (B U^dag)_ab = B_ak conj(U_bk)
+          const R vx = (R)U[b * 3 + k].x, vy = (R)U[b * 3 + k].y;
+          re -= bx * vx + by * vy;
+          im -= by * vx - bx * vy;
         }
-        Z[a * 3 + b] = make_double2(re, im);
+        Z[a * 3 + b] = cmake<R>(re, im);
       }
     // TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6
-    const double trim = (Z[0].y + Z[4].y + Z[8].y) / 3.0;  // tr(Z - Z^dag)/6 = i Im tr Z / 3
+    const double trim = ((double)Z[0].im + (double)Z[4].im + (double)Z[8].im) / 3.0;  // i Im tr Z / 3
     double2* out = force + (zlex * 4 + mu) * 9;
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
       for (int b = 0; b < 3; b++) {
-        double re = 0.5 * (Z[a * 3 + b].x - Z[b * 3 + a].x);
-        double im = 0.5 * (Z[a * 3 + b].y + Z[b * 3 + a].y);
+        double re = 0.5 * ((double)Z[a * 3 + b].re - (double)Z[b * 3 + a].re);
+        double im = 0.5 * ((double)Z[a * 3 + b].im + (double)Z[b * 3 + a].im);
         if (a == b) im -= trim;
         out[a * 3 + b].x += re;
         out[a * 3 + b].y += im;
@@ -192,16 +213,21 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
 }
 
 template <int P>
-int launch_force(dwf_ctx* c, double2* force, const void* Xf, const void* Yf, cudaStream_t st) {
+int launch_force(dwf_ctx* c, double2* force, const void* Xe, const void* Xo, const void* Ye, const void* Yo,
+                 int npf, cudaStream_t st) {
   typedef typename Prec<P>::S S;
+  typedef typename Prec<P>::LS LT;
+  const LT* le = P == DWF_F64 ? (const LT*)c->links64[0] : (const LT*)c->links32[0];
+  const LT* lo = P == DWF_F64 ? (const LT*)c->links64[1] : (const LT*)c->links32[1];
+  const long long fs = c->g.Vh * 12LL * c->g.Ls;
   c->launches++;
 #define DWF_FORCE_CASE(LSV)                                                                                  \
   case LSV: {                                                                                                \
     constexpr int SB = LSV >= 16 ? 8 : 64 / LSV;                                                             \
     dim3 grid((unsigned)((c->g.Vh + SB - 1) / SB), 2);                                                       \
-    k_force<P, LSV, SB><<<grid, LSV * SB, 0, st>>>(force, (const S*)Xf, (const S*)Yf, c->links64[0],        \
-                                                   c->links64[1], c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3], \
-                                                   (int)c->g.Vh);                                            \
+    k_force<P, LSV, SB><<<grid, LSV * SB, 0, st>>>(force, (const S*)Xe, (const S*)Xo, (const S*)Ye,         \
+                                                   (const S*)Yo, fs, npf, le, lo, c->g.L[0], c->g.L[1],      \
+                                                   c->g.L[2], c->g.L[3], (int)c->g.Vh);                      \
     break;                                                                                                   \
   }
   switch (c->g.Ls) {
@@ -221,38 +247,36 @@ int launch_force(dwf_ctx* c, double2* force, const void* Xf, const void* Yf, cud
 extern "C" int dwf_force(dwf_ctx* c, void* force, const void* X, const double* mf, int npf, int prec,
                          void* stream) {
   if (!c || !force || !X || !mf || npf < 1) return DWF_EINVAL;
+  if (npf > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "npf out of range");
   if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
   if (!dwf_is_device_ptr(force) || !dwf_is_device_ptr(X)) return dwf_fail(c, DWF_EINVAL, "device buffers required");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t he = c->g.Vh * 12 * c->g.Ls;
-  const size_t cb = dwf_complex_bytes(prec);
-  char* Xf = (char*)dwf_workspace(c, 28, 2 * he * cb);
-  char* Yf = (char*)dwf_workspace(c, 29, 2 * he * cb);
-  if (!Xf || !Yf) return dwf_fail(c, DWF_ENOMEM, "force workspace");
-  for (int i = 0; i < npf; i++) {
-    const char* Xe = (const char*)X + (size_t)i * he * cb;
-    const double m1[1] = {mf[i]};
-    DWF_CUDA(c, cudaMemcpyAsync(Xf, Xe, he * cb, cudaMemcpyDeviceToDevice, st));
-    // X_o = M_oo^-1 (-1/2 D_oe X_e) and Y_e = M_ee X_e + 1/2 D_eo X_o  (= M_pc X_e)
-    int rc = mpc_apply(c, Yf, Xf, Xf + he * cb, m1, 0, prec, 1, 0, st, nullptr);
-    if (rc) return rc;
-    // Y_o = M_oo^-dag (-1/2 D^dag_oe Y_e)
-    HopLaunch h;
-    memset(&h, 0, sizeof(h));
-    h.out = Yf + he * cb;
-    h.in = Yf;
-    h.out_parity = 1;
-    h.dagger = 1;
-    h.nrhs = 1;
-    h.alpha = -0.5;
-    h.inv_mode = 2;
-    h.mf = m1;
-    rc = launch_hop(c, h, prec, st, nullptr);
-    if (rc) return rc;
-    rc = prec == DWF_F64 ? launch_force<DWF_F64>(c, (double2*)force, Xf, Yf, st)
-                         : launch_force<DWF_F32>(c, (double2*)force, Xf, Yf, st);
-    if (rc) return rc;
-  }
+  const size_t bytes = (size_t)npf * he * dwf_complex_bytes(prec);
+  void* Xo = dwf_workspace(c, WS_FXO, bytes);
+  void* Ye = dwf_workspace(c, WS_FYE, bytes);
+  void* Yo = dwf_workspace(c, WS_FYO, bytes);
+  if (!Xo || !Ye || !Yo) return dwf_fail(c, DWF_ENOMEM, "force workspace");
+  // all pseudofermions at once, each with its own mass:
+  // X_o = M_oo^-1 (-1/2 D_oe X_e) and Y_e = M_ee X_e + 1/2 D_eo X_o  (= M_pc X_e)
+  int rc = mpc_apply(c, Ye, X, Xo, mf, 0, prec, npf, 0, st, nullptr);
+  if (rc) return rc;
+  // Y_o = M_oo^-dag (-1/2 D^dag_oe Y_e)
+  HopLaunch h;
+  memset(&h, 0, sizeof(h));
+  h.out = Yo;
+  h.in = Ye;
+  h.out_parity = 1;
+  h.dagger = 1;
+  h.nrhs = npf;
+  h.alpha = -0.5;
+  h.inv_mode = 2;
+  h.mf = mf;
+  rc = launch_hop(c, h, prec, st, nullptr);
+  if (rc) return rc;
+  rc = prec == DWF_F64 ? launch_force<DWF_F64>(c, (double2*)force, X, Xo, Ye, Yo, npf, st)
+                       : launch_force<DWF_F32>(c, (double2*)force, X, Xo, Ye, Yo, npf, st);
+  if (rc) return rc;
   DWF_CUDA(c, cudaGetLastError());
   return DWF_OK;
 }
