@@ -81,9 +81,9 @@ __device__ __forceinline__ void site_sum(R* red, double2* AB, int slot, const cp
 // One CTA: SB checkerboard sites of one parity x Ls threads (s fastest, so
 // the neighbours' spinors are read as contiguous Ls-runs), all npf
 // pseudofermions.  Each thread forms the s-slice of A_mu and B_mu for the 4
-// directions summed over the pseudofermions (G is linear in A and B); the Ls
-// slices are summed per site in shared memory, and 4 threads per site form
-// G_mu, reading each link once for all pseudofermions.  The final products run in
+// directions; the Ls slices (and the pseudofermions, G being linear in A and
+// B) are summed per site in shared memory, and 4 threads per site form G_mu,
+// reading each link once for all pseudofermions.  The final products run in
 // the fields' precision (FP32 fields: FP32, FP64 fields: FP64), the sums and
 // the force in FP64.
 template <int P, int LS, int SB>
@@ -124,54 +124,42 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
     const long long ylex = y[0] + (long long)L0 * (y[1] + (long long)L1 * (y[2] + (long long)L2 * y[3]));
     nbh[mu] = (int)(ylex >> 1);
   }
-  // direction outermost: each thread sums its s-slice of A_mu and B_mu over
-  // the pseudofermions in registers, then one shared-memory sum over s per
-  // matrix (8 per CTA, whatever npf)
-  auto dir = [&](auto muc) {
-    constexpr int MU = decltype(muc)::value;
-    cpx<R> oA[9], oB[9];
+  for (int f = 0; f < npf; f++) {
+    const S* Xs = (p ? Xo : Xe) + f * fstride;  // fields of this site's parity
+    const S* Ys = (p ? Yo : Ye) + f * fstride;
+    const S* Xn = (p ? Xe : Xo) + f * fstride;  // and of the neighbours'
+    const S* Yn = (p ? Ye : Yo) + f * fstride;
+    cpx<R> xb[12], ya[12];
 #pragma unroll
-    for (int e = 0; e < 9; e++) oA[e] = oB[e] = cmake<R>(0, 0);
-    for (int f = 0; f < npf; f++) {
-      const S* Xs = (p ? Xo : Xe) + f * fstride + hh * row + s;  // this site
-      const S* Ys = (p ? Yo : Ye) + f * fstride + hh * row + s;
-      const S* Xy = (p ? Xe : Xo) + f * fstride + nbh[MU] * row + s;  // x + mu
-      const S* Yy = (p ? Ye : Yo) + f * fstride + nbh[MU] * row + s;
-      cpx<R> xa[12], ya[12], hx[2][3], hy[2][3], o[9];
+    for (int c = 0; c < 12; c++) {
+      xb[c] = active ? ld_c(Xs + hh * row + c * LS + s) : cmake<R>(0, 0);
+      ya[c] = active ? ld_c(Ys + hh * row + c * LS + s) : cmake<R>(0, 0);
+    }
+    auto dir = [&](auto muc) {
+      constexpr int MU = decltype(muc)::value;
+      const S* Xy = Xn + nbh[MU] * row + s;
+      const S* Yy = Yn + nbh[MU] * row + s;
+      cpx<R> xa[12], yb[12];
 #pragma unroll
       for (int c = 0; c < 12; c++) {
         xa[c] = active ? ld_c(Xy + c * LS) : cmake<R>(0, 0);  // X'(x+mu)
-        ya[c] = active ? ld_c(Ys + c * LS) : cmake<R>(0, 0);  // Y'(x)
+        yb[c] = active ? ld_c(Yy + c * LS) : cmake<R>(0, 0);  // Y'(x+mu)
       }
+      cpx<R> hx[2][3], hy[2][3], o[9];
       proj<R, MU>(hx, xa, R(1));
       proj<R, MU>(hy, ya, R(1));
       outer2<R>(o, hx, hy);
-#pragma unroll
-      for (int e = 0; e < 9; e++) {
-        oA[e].re += o[e].re;
-        oA[e].im += o[e].im;
-      }
-#pragma unroll
-      for (int c = 0; c < 12; c++) {
-        xa[c] = active ? ld_c(Xs + c * LS) : cmake<R>(0, 0);  // X'(x)
-        ya[c] = active ? ld_c(Yy + c * LS) : cmake<R>(0, 0);  // Y'(x+mu)
-      }
-      proj<R, MU>(hx, xa, R(-1));
-      proj<R, MU>(hy, ya, R(-1));
+      site_sum<R, LS, SB>(red, AB, MU, o, sl, s);
+      proj<R, MU>(hx, xb, R(-1));
+      proj<R, MU>(hy, yb, R(-1));
       outer2<R>(o, hx, hy);
-#pragma unroll
-      for (int e = 0; e < 9; e++) {
-        oB[e].re += o[e].re;
-        oB[e].im += o[e].im;
-      }
-    }
-    site_sum<R, LS, SB>(red, AB, MU, oA, sl, s);
-    site_sum<R, LS, SB>(red, AB, 4 + MU, oB, sl, s);
-  };
-  dir(std::integral_constant<int, 0>());
-  dir(std::integral_constant<int, 1>());
-  dir(std::integral_constant<int, 2>());
-  dir(std::integral_constant<int, 3>());
+      site_sum<R, LS, SB>(red, AB, 4 + MU, o, sl, s);
+    };
+    dir(std::integral_constant<int, 0>());
+    dir(std::integral_constant<int, 1>());
+    dir(std::integral_constant<int, 2>());
+    dir(std::integral_constant<int, 3>());
+  }
   // G_mu = TA(U A - B U^dag), one thread per (site, mu)
   for (int t = tid; t < SB * 4; t += LS * SB) {
     const int sl2 = t >> 2, mu = t & 3;
