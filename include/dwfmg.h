@@ -128,7 +128,8 @@ int dwf_reset_counters(dwf_ctx* ctx);
  * inner-loop form: scalar, neighbour prefetch, packed FP32 on (re, im) pairs,
  * 2^4 hypercube tiles, two s-slices per thread with packed FP32 over the
  * pair (loads into registers, or staged in shared memory by cp.async with 2,
- * 4 or 8 neighbours in flight), CTAs of 2 or 4 y-rows; DWF_HOP_VARIANTS
+ * 4 or 8 neighbours in flight), CTAs of 2 or 4 y-rows, the scalar form
+ * with an L2 prefetch of the rows a CTA a wave later reads first; DWF_HOP_VARIANTS
  * variants for FP32 and FP16
  * storage at Ls >= 16, one otherwise) on this context's lattice, `reps`
  * launches each, keeps the fastest for precision `prec` and returns its time
@@ -138,7 +139,7 @@ int dwf_reset_counters(dwf_ctx* ctx);
  * read the choice (0 = untuned default; valid ids 0 .. DWF_HOP_VARIANTS-1;
  * dwf_set_hop_variant returns DWF_EINVAL for a variant that does not tile
  * the lattice). */
-#define DWF_HOP_VARIANTS 23
+#define DWF_HOP_VARIANTS 26
 int dwf_autotune(dwf_ctx* ctx, int prec, int reps, double* best_ms, void* stream);
 int dwf_set_hop_variant(dwf_ctx* ctx, int prec, int variant);
 int dwf_get_hop_variant(const dwf_ctx* ctx, int prec);

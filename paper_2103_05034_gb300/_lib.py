@@ -18,7 +18,7 @@ DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ENOCONV, DWF_ENAN, DWF_ECUDA, DWF_ETIMEOUT, 
     0, -1, -2, -3, -4, -5, -6, -7
 F64, F32, F16S, TF32 = 0, 1, 2, 3
 SOLVE_F64, SOLVE_MIXED_F32, SOLVE_MIXED_F16 = 0, 1, 2
-HOP_VARIANTS = 23  # DWF_HOP_VARIANTS
+HOP_VARIANTS = 26  # DWF_HOP_VARIANTS
 STATUS_NAMES = {0: "DWF_OK", -1: "DWF_EINVAL", -2: "DWF_ENOMEM", -3: "DWF_ENOCONV",
                 -4: "DWF_ENAN", -5: "DWF_ECUDA", -6: "DWF_ETIMEOUT", -7: "DWF_ERANGE"}
 

@@ -38,6 +38,8 @@ struct HopParams {
   int L0, L1, L2, L3, Lxh;
   int Vh;
   int zc;  // traversal z-chunk (even divisor of L2; L2 = lexicographic order)
+  int l2pf; // > 0: each CTA prefetches into L2 the input rows first read by the
+            // CTA l2pf positions later in the traversal (scalar kernel only)
   int out_parity;
   float sg;  // +1: D_hop, -1: D_hop^dag
   double alpha;
@@ -287,6 +289,11 @@ __device__ __forceinline__ void minv_row_inplace(cpx<R>* row, bool fwd, R d, R m
 
 extern __shared__ __align__(16) unsigned char hop_dyn_smem[];
 
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Register cap: REGS registers per thread give at least 65536/(LS*SB*REGS)
 // resident CTAs per SM (REGS = 0: no cap).  PF: prefetch the next neighbour.
 template <int LS, int SB, int REGS>
@@ -320,27 +327,46 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
   // lattices whose full time slice does not fit (zc = L2 is the plain
   // lexicographic order).
   const int zc = p.zc;
-  int site0;
-  if (RY > 1 || (!(PF == 3) && zc < p.L2 && (p.Lxh % SB) == 0)) {
-    // (RY > 1 needs SB | Lxh and RY | L1; the host launches it only then)
-    const int nseg = p.Lxh / SB;
-    const int ny = p.L1 / RY;
-    int r = blockIdx.x;
-    const int seg = r % nseg;
-    r /= nseg;
-    const int yy = (r % ny) * RY;
-    r /= ny;
-    const int zl = r % zc;
-    r /= zc;
-    const int tt = r % p.L3;
-    const int zz = (r / p.L3) * zc + zl;
-    site0 = ((tt * p.L2 + zz) * p.L1 + yy) * p.Lxh + seg * SB;
-  } else {
-    site0 = blockIdx.x * SB;
+  const int rhs = blockIdx.y;
+  auto cta_site0 = [&](int bx) -> int {
+    if (RY > 1 || (!(PF == 3) && zc < p.L2 && (p.Lxh % SB) == 0)) {
+      // (RY > 1 needs SB | Lxh and RY | L1; the host launches it only then)
+      const int nseg = p.Lxh / SB;
+      const int ny = p.L1 / RY;
+      int r = bx;
+      const int seg = r % nseg;
+      r /= nseg;
+      const int yy = (r % ny) * RY;
+      r /= ny;
+      const int zl = r % zc;
+      r /= zc;
+      const int tt = r % p.L3;
+      const int zz = (r / p.L3) * zc + zl;
+      return ((tt * p.L2 + zz) * p.L1 + yy) * p.Lxh + seg * SB;
+    }
+    return bx * SB;
+  };
+  const int site0 = cta_site0(blockIdx.x);
+  if (PF == 0 && RY == 1 && p.l2pf > 0 && tid == 0 && blockIdx.x + p.l2pf < gridDim.x) {
+    // The rows a CTA reads first in the traversal are the t+1 and z+1
+    // neighbour rows of its own row; fetch those of a CTA that starts about a
+    // wave later into L2 now, so that its first reads hit L2.
+    const int s2 = cta_site0(blockIdx.x + p.l2pf);  // < Vh: the CTA exists
+    int rr = s2 / p.Lxh;
+    const int y2 = rr % p.L1;
+    rr /= p.L1;
+    const int z2 = rr % p.L2;
+    const int t2 = rr / p.L2;
+    const int zq = z2 + 1 == p.L2 ? 0 : z2 + 1, tq = t2 + 1 == p.L3 ? 0 : t2 + 1;
+    const unsigned rowb = (unsigned)(p.Lxh * 12 * LS * sizeof(S));
+    const char* base = (const char*)((const S*)p.in + (size_t)rhs * p.rhs_stride);
+    if ((((uintptr_t)base) & 15) == 0 && (rowb & 15) == 0) {  // bulk-copy alignment
+      prefetch_l2(base + (size_t)((tq * p.L2 + z2) * p.L1 + y2) * rowb, rowb);
+      prefetch_l2(base + (size_t)((t2 * p.L2 + zq) * p.L1 + y2) * rowb, rowb);
+    }
   }
   // site of the l-th CTA slot (rows of SB sites, Lxh apart)
   auto row_site = [&](int l) { return RY > 1 ? site0 + (l / SB) * p.Lxh + (l % SB) : site0 + l; };
-  const int rhs = blockIdx.y;
   // PF == 3: the CTA handles the 8 output-parity sites of one 2^4 hypercube
   // (SB = 8), so half of every site's neighbours are the hypercube's other 8
   // sites, shared through L1 by the CTA.  Otherwise SB consecutive sites.
@@ -690,12 +716,16 @@ struct HopShape {
 // Tuning variants of the hopping kernel: (register cap, prefetch).  Variant 0
 // is the uncapped kernel; the autotuner (dwf_autotune) times the rest on the
 // context's lattice and keeps the fastest per precision.
-static_assert(DWF_HOP_VARIANTS == 23, "variant table below");
+static_assert(DWF_HOP_VARIANTS == 26, "variant table below");
 __host__ __device__ constexpr int hop_variant_regs(int v) {
   return v == 0 ? 0 : v == 1 ? 96 : v == 2 ? 80 : v == 3 ? 64 : v == 4 ? 128 : v == 5 ? 96 : v == 6 ? 64 : v == 7 ? 80
          : v == 8 ? 64 : v == 9 ? 80 : v == 10 ? 128 : v == 11 ? 112 : v == 12 ? 96 : v == 13 ? 0
-         : v == 14 ? 64 : v == 15 ? 80 : v == 16 ? 64 : v == 17 ? 80 : v == 18 ? 56 : v == 19 ? 48 : 0;
+         : v == 14 ? 64 : v == 15 ? 80 : v == 16 ? 64 : v == 17 ? 80 : v == 18 ? 56 : v == 19 ? 48
+         : v == 23 ? 64 : v == 24 ? 64 : v == 25 ? 80 : 0;
 }
+// L2 prefetch distance of the scalar kernel in waves of resident CTAs
+// (variants 23-25)
+__host__ __device__ constexpr int hop_variant_l2pf(int v) { return v == 23 ? 1 : v == 24 ? 2 : v == 25 ? 1 : 0; }
 // s-pair kernel with asynchronous shared-memory staging, neighbours in flight
 // per thread (variants 20-22)
 __host__ __device__ constexpr int hop_variant_depth(int v) { return v == 20 ? 8 : v == 21 ? 4 : v == 22 ? 2 : 0; }
@@ -708,8 +738,8 @@ __host__ __device__ constexpr int hop_variant_rows(int v) {
 // CTA), 4: two s-slices per thread, packed FP32 over the s-pair
 // (hop_kernel_pair)
 __host__ __device__ constexpr int hop_variant_pf(int v) {
-  return v >= 20 ? 4 : v >= 14 ? 0 : v >= 10 ? 4 : v >= 8 ? 3 : v >= 6 ? 2 : v >= 4 ? 1 : 0;
-}  // 18, 19: scalar with 56 / 48 registers
+  return v >= 23 ? 0 : v >= 20 ? 4 : v >= 14 ? 0 : v >= 10 ? 4 : v >= 8 ? 3 : v >= 6 ? 2 : v >= 4 ? 1 : 0;
+}  // 18, 19: scalar with 56 / 48 registers; 23-25: scalar with L2 prefetch
 
 // Dynamic shared memory of one launch: links (SBC*72 complex, twice for the
 // (re,re,-im,im) packed form), or the M_ee^-1 stage (SBC*12*(LS+1) complex)
@@ -739,6 +769,21 @@ inline void launch_hop_v(const HopParams& hp, dim3 grid, cudaStream_t st) {
         grid, LSV / 2 * SB, pair_smem_bytes<P, LSV, SB, D>(hp.inv_mode != 0), hp, st);
   } else if constexpr (PF == 4) {
     hop_launch_smem<hop_kernel_pair<P, LSV, SB, hop_variant_regs(V)>>(grid, LSV / 2 * SB, bytes, hp, st);
+  } else if constexpr (hop_variant_l2pf(V) > 0) {
+    // prefetch distance: the given number of waves of resident CTAs
+    static int resident = 0;  // CTAs per GPU, one per instantiation
+    if (!resident) {
+      int dev = 0, nsm = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, hop_kernel<P, LSV, SB, hop_variant_regs(V), PF, RY>,
+                                                    LSV * SB * RY, bytes);
+      resident = nsm * (per > 0 ? per : 1);
+      if (resident < 1) resident = 1;
+    }
+    HopParams h2 = hp;
+    h2.l2pf = hop_variant_l2pf(V) * resident;
+    hop_launch_smem<hop_kernel<P, LSV, SB, hop_variant_regs(V), PF, RY>>(grid, LSV * SB * RY, bytes, h2, st);
   } else {
     hop_launch_smem<hop_kernel<P, LSV, SB, hop_variant_regs(V), PF, RY>>(grid, LSV * SB * RY, bytes, hp, st);
   }
@@ -773,6 +818,9 @@ inline int launch_hop_ls(const HopParams& hp, dim3 grid, int variant, cudaStream
       case 20: launch_hop_v<P, LSV, 20>(hp, grid, st); break;
       case 21: launch_hop_v<P, LSV, 21>(hp, grid, st); break;
       case 22: launch_hop_v<P, LSV, 22>(hp, grid, st); break;
+      case 23: launch_hop_v<P, LSV, 23>(hp, grid, st); break;
+      case 24: launch_hop_v<P, LSV, 24>(hp, grid, st); break;
+      case 25: launch_hop_v<P, LSV, 25>(hp, grid, st); break;
       default: launch_hop_v<P, LSV, 0>(hp, grid, st); break;
     }
   }
