@@ -659,47 +659,78 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
   }
 }
 
-// Site-local M, M^dag, M^-1 or M^-dag of Eq. (4) on whole Ls-rows: one thread
-// per (site, spin, colour).
+// Rows of Ls complex numbers per CTA of the site-local kernel: 128, or 64
+// where 128 padded rows would exceed 48 KB of static shared memory.
+template <int P, int LS>
+struct MooRows {
+  static constexpr int v =
+      128 * (LS + 1) * sizeof(cpx<typename Prec<P>::R>) <= 48 * 1024 ? 128 : 64;
+};
+
+// Site-local M, M^dag, M^-1 or M^-dag of Eq. (4) on whole Ls-rows, one row
+// (site, spin, colour) per thread.  The CTA's rows are moved between global
+// and shared memory with consecutive threads on consecutive numbers, so that
+// the global accesses are coalesced; each thread works on its own row in
+// registers.
 template <int P, int LS>
 __global__ void __launch_bounds__(128) mooee_kernel(typename Prec<P>::S* out,
                                                     const typename Prec<P>::S* in, int Vh,
                                                     int dagger, int inverse, long long rhs_stride,
                                                     HopParams p) {
   typedef typename Prec<P>::R R;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  typedef typename Prec<P>::S S;
+  constexpr int RB = MooRows<P, LS>::v;
+  __shared__ cpx<R> tile[RB * (LS + 1)];
+  const int tid = threadIdx.x;
   const int rhs = blockIdx.y;
-  if (gid >= (long long)Vh * 12) return;
-  const int c = (int)(gid % 12);
-  const size_t off = (size_t)rhs * rhs_stride + (size_t)gid * LS;
-  cpx<R> row[LS];
+  const long long nrows = (long long)Vh * 12;
+  const long long row0 = (long long)blockIdx.x * RB;
+  const int nr = (int)(nrows - row0 < RB ? nrows - row0 : RB);
+  const size_t base = (size_t)rhs * rhs_stride + (size_t)row0 * LS;
+  const S* src = in + base;
+  for (int e = tid; e < nr * LS; e += 128) {
+    const int r = e / LS, q = e - r * LS;
+    tile[r * (LS + 1) + q] = ld_c(src + e);
+  }
+  __syncthreads();
+  if (tid < nr) {
+    cpx<R>* rp = tile + tid * (LS + 1);
+    const int c = (int)((row0 + tid) % 12);
+    cpx<R> row[LS];
 #pragma unroll
-  for (int q = 0; q < LS; q++) row[q] = ld_c(in + off + q);
-  const R d = (R)p.d, m = (R)p.m[rhs];
-  const bool plus_rule = (c < 6) != (dagger != 0);  // M_+ type (couples s-1)
-  if (inverse) {
-    minv_row<R, LS>(row, plus_rule, d, m, (R)p.kappa[rhs], (R)p.dls1[rhs]);
-  } else {
-    cpx<R> res[LS];
+    for (int q = 0; q < LS; q++) row[q] = rp[q];
+    const R d = (R)p.d, m = (R)p.m[rhs];
+    const bool plus_rule = (c < 6) != (dagger != 0);  // M_+ type (couples s-1)
+    if (inverse) {
+      minv_row<R, LS>(row, plus_rule, d, m, (R)p.kappa[rhs], (R)p.dls1[rhs]);
+    } else {
+      cpx<R> res[LS];
 #pragma unroll
-    for (int q = 0; q < LS; q++) {
-      int qn;
-      R co;
-      if (plus_rule) {
-        qn = q > 0 ? q - 1 : LS - 1;
-        co = q > 0 ? R(-1) : m;
-      } else {
-        qn = q < LS - 1 ? q + 1 : 0;
-        co = q < LS - 1 ? R(-1) : m;
+      for (int q = 0; q < LS; q++) {
+        int qn;
+        R co;
+        if (plus_rule) {
+          qn = q > 0 ? q - 1 : LS - 1;
+          co = q > 0 ? R(-1) : m;
+        } else {
+          qn = q < LS - 1 ? q + 1 : 0;
+          co = q < LS - 1 ? R(-1) : m;
+        }
+        res[q].re = fma(d, row[q].re, co * row[qn].re);
+        res[q].im = fma(d, row[q].im, co * row[qn].im);
       }
-      res[q].re = fma(d, row[q].re, co * row[qn].re);
-      res[q].im = fma(d, row[q].im, co * row[qn].im);
+#pragma unroll
+      for (int q = 0; q < LS; q++) row[q] = res[q];
     }
 #pragma unroll
-    for (int q = 0; q < LS; q++) row[q] = res[q];
+    for (int q = 0; q < LS; q++) rp[q] = row[q];
   }
-#pragma unroll
-  for (int q = 0; q < LS; q++) st_c(out + off + q, row[q]);
+  __syncthreads();
+  S* dst = out + base;
+  for (int e = tid; e < nr * LS; e += 128) {
+    const int r = e / LS, q = e - r * LS;
+    st_c(dst + e, tile[r * (LS + 1) + q]);
+  }
 }
 
 }  // namespace dwfk
@@ -856,12 +887,14 @@ template <int P>
 int launch_mooee_prec(void* out, const void* in, const HopParams& hp, int dagger, int inverse,
                       int Ls, int nrhs, long long rhs_stride, cudaStream_t st) {
   typedef typename Prec<P>::S S;
-  dim3 grid((unsigned)((hp.Vh * 12LL + 127) / 128), nrhs, 1);
-#define DWF_MOO_CASE(LSV)                                                                    \
-  case LSV:                                                                                  \
-    mooee_kernel<P, LSV><<<grid, 128, 0, st>>>((S*)out, (const S*)in, hp.Vh, dagger, inverse, \
-                                               rhs_stride, hp);                              \
-    return DWF_OK;
+#define DWF_MOO_CASE(LSV)                                                                         \
+  case LSV: {                                                                                     \
+    constexpr int RB = MooRows<P, LSV>::v;                                                        \
+    dim3 grid((unsigned)((hp.Vh * 12LL + RB - 1) / RB), nrhs, 1);                                 \
+    mooee_kernel<P, LSV><<<grid, 128, 0, st>>>((S*)out, (const S*)in, hp.Vh, dagger, inverse,      \
+                                               rhs_stride, hp);                                   \
+    return DWF_OK;                                                                                \
+  }
   switch (Ls) {
     DWF_MOO_CASE(4)
     DWF_MOO_CASE(8)
