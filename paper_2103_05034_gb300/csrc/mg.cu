@@ -773,7 +773,7 @@ int vgraph_build(VGraph& V, dwf_mg* G, cudaStream_t st) {
   V.launches = c->launches - l0;
   c->launches = l0;
   if (rc || ec != cudaSuccess || !graph || cudaGraphInstantiate(&V.exec, graph, 0) != cudaSuccess) {
-    // capture not possible (e.g. a launch form the driver cannot record):
+    // capture not possible (e.g. a launch form the CUDA driver cannot record):
     // the solve continues with plain launches
     if (graph) cudaGraphDestroy(graph);
     V.exec = nullptr;
