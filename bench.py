@@ -685,6 +685,18 @@ def run_rows(args):
          singles_ms=1e3 * bs["singles"]["seconds"], speedup_batch_vs_singles=bs["speedup_batch_vs_singles"],
          iterations=bs["batch"]["iterations"], true_residual=bs["batch"]["true_residual"],
          note="one warm call timed on the host clock; achieved = algorithmic hopping bytes / time")
+    # the unpreconditioned baseline of the Krylov comparison (FP64 CGNR on the
+    # full lattice), one call on the host clock
+    ops.dwf_reset_counters(ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sc = ops.cgnr_solve(ctx, xd, bd, mf, args.tol, 100000)
+    torch.cuda.synchronize()
+    t_cg = time.perf_counter() - t0
+    emit("a4", "cgnr_solve unpreconditioned FP64 (full lattice)", 1e3 * t_cg, ops.dwf_counters(ctx)[1], "GB/s",
+         hbm, "hbm", iterations=sc["iterations"], true_residual=sc["true_residual"],
+         fine_matmuls=sc["fine_matmuls"], rbcg_iterations=st["iterations"],
+         note="FP64 hopping launches are ALU-bound on GB300; compare iterations with the red-black row")
     f = lambda: ops.dwf_norm2(ctx, a32)
     emit("a5", "dwf_norm2 F32 (half field)", timed(f), nh * 4.0, "GB/s", hbm, "hbm")
     f = lambda: ops.dwf_cdot(ctx, a64, a64)

@@ -234,6 +234,19 @@ int rbcg_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int 
 int rbcg_normal_solve(dwf_ctx* ctx, void* x, const void* phi, double mf, double tol, int maxiter,
                       int policy, dwf_solve_stats* stats, void* stream);
 
+/* Unpreconditioned CGNR on the full lattice (the baseline row of the Krylov
+ * comparison of Sec. 5.1: CG on D_DW^dag D_DW x = D_DW^dag b without the
+ * red-black Schur complement), FP64 throughout.  x and b: full FP64 fields in
+ * device memory (layout as for rbcg_solve, x must not alias b).  The
+ * normal-equation residual is checked every 8 iterations; when it falls
+ * below tol times |D_DW^dag b| the FP64 true residual ||b - D_DW x|| / ||b||
+ * decides, and the normal-equation target tightens tenfold if it is above
+ * tol.  stats: iterations, fine_matmuls (full-lattice D_DW or D_DW^dag
+ * applications, two per iteration), true_residual.  DWF_ENOCONV after maxiter
+ * iterations.  Synchronises. */
+int cgnr_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int maxiter,
+               dwf_solve_stats* stats, void* stream);
+
 /* Batched red-black CGNR (Sec. 5.1 operator; several pseudofermion masses on
  * one gauge field, as in the HMC of Sec. 6): solves D_DW(mf[i]) x_i = b_i for
  * i < nrhs (1 <= nrhs <= 64), each rhs with its own mass.  b and x hold nrhs

@@ -112,6 +112,7 @@ _SIGS = {
     "dwf_power_max": (I, [P, C.POINTER(D), P, D, I, I, P]),
     "dwf_force": (I, [P, P, P, C.POINTER(D), I, I, P]),
     "rbcg_normal_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
+    "cgnr_solve": (I, [P, P, P, D, D, I, C.POINTER(SolveStats), P]),
     "rbcg_solve_batch": (I, [P, P, P, C.POINTER(D), I, D, I, I, C.POINTER(SolveStats), P]),
     "rbcg_normal_solve_batch": (I, [P, P, P, C.POINTER(D), I, D, I, I, C.POINTER(SolveStats), P]),
     "cheby_filter": (I, [P, P, P, I, D, D, I, D, I, P]),

@@ -332,6 +332,14 @@ def rbcg_normal_solve(ctx, x, phi, mf, tol, maxiter=100000, policy=_lib.SOLVE_MI
     return st.as_dict()
 
 
+def cgnr_solve(ctx, x, b, mf, tol, maxiter=100000):
+    """Unpreconditioned FP64 CGNR on the full lattice (full FP64 device
+    fields).  Returns the solver statistics as a dict."""
+    st = SolveStats()
+    check(lib().cgnr_solve(ctx.h, _ptr(x), _ptr(b), mf, tol, maxiter, C.byref(st), _stream()), ctx.h)
+    return st.as_dict()
+
+
 def _batch_solve(fn, ctx, x, b, masses, tol, maxiter, policy):
     n = len(masses)
     mf = (C.c_double * n)(*[float(m) for m in masses])

@@ -168,6 +168,38 @@ def test_rbcg_mixed_reaches_tight_tolerance(Ls, mf):
     ctx.close()
 
 
+def test_cgnr_unpreconditioned_matches_oracle():
+    """Full-lattice CGNR without red-black preconditioning (the baseline row
+    of the Krylov comparison, Sec. 5.1), FP64: the solution against the
+    oracle's, the true residual by the oracle, and the iteration count
+    against the oracle's CG on D^dag D (more iterations than red-black CG)."""
+    L, Ls, mf, tol = (4, 4, 4, 4), 8, 0.01, 1e-10
+    U = synth.random_gauge(L, 0.3, synth.SEED_GAUGE)
+    b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE)
+    ctx = ops.Context(L, Ls, M5, U)
+    bd = full_dev(b, L, F64)
+    x = torch.zeros_like(bd)
+    st = ops.cgnr_solve(ctx, x, bd, mf, tol, 20000)
+    xg = dev_to_full_canon(x, L, Ls)
+    assert krylov.true_residual(U, xg, b, M5, mf) <= tol * 1.01, st
+    xr, it_rb, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert rel(xg, xr) < 1e-7
+    rhs = dwf.ddw(U, b, M5, mf, dag=True)
+    _, it_lo, _ = krylov.cg(lambda v: dwf.mdagm(U, v, M5, mf), rhs, tol, 20000)
+    _, it_hi, _ = krylov.cg(lambda v: dwf.mdagm(U, v, M5, mf), rhs, tol * 1e-3, 20000)
+    assert it_lo - 8 <= st["iterations"] <= it_hi + 8, (st, it_lo, it_hi)
+    _, it_rb10, _ = krylov.rbcg_solve(U, b, M5, mf, tol)
+    assert st["iterations"] > it_rb10
+    assert st["fine_matmuls"] >= 2 * st["iterations"]
+    # zero source; aliasing rejected
+    z = torch.zeros_like(bd)
+    assert ops.cgnr_solve(ctx, x, z, mf, tol, 10)["iterations"] == 0 and float(x.abs().max()) == 0.0
+    with pytest.raises(DWFError) as e:
+        ops.cgnr_solve(ctx, bd, bd, mf, tol, 10)
+    assert e.value.code == DWF_EINVAL
+    ctx.close()
+
+
 def test_rbcg_host_buffers():
     L, Ls, mf = (4, 4, 4, 4), 8, 0.05
     U = synth.random_gauge(L, 0.3, 3)
