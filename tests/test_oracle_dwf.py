@@ -208,6 +208,20 @@ def test_rbcg_matches_dense_solve(tiny):
     assert krylov.true_residual(U, x, b, M5, 0.05) < 1e-11
 
 
+def test_cgnr_matches_dense_solve(tiny):
+    """CG on D^dag D x = D^dag b (the unpreconditioned baseline of Sec. 5.1)
+    reaches the dense solution, in more iterations than the red-black solve
+    (the Schur complement is better conditioned)."""
+    L, Ls, U, shape, D = tiny
+    b = rand_field(L, Ls, 10)
+    x_dense = np.linalg.solve(D, b.ravel()).reshape(shape)
+    rhs = dwf.ddw(U, b, M5, 0.05, dag=True)
+    x, it, _ = krylov.cg(lambda v: dwf.mdagm(U, v, M5, 0.05), rhs, 1e-13, 10000)
+    assert np.linalg.norm(x - x_dense) / np.linalg.norm(x_dense) < 1e-10
+    _, it_rb, _ = krylov.rbcg_solve(U, b, M5, 0.05, 1e-13)
+    assert it > it_rb
+
+
 def test_hdw_spectrum_real_and_squares(tiny):
     """H_DW is hermitian; its squared spectrum is that of D^dag D."""
     L, Ls, U, shape, D = tiny
