@@ -16,6 +16,16 @@ is derived from first principles for the red-black operator of Sec. 5.1.
     B_mu(x)_{ab} = sum_{s,i,j} (1 + gamma_mu)_{ij} X'_{s j a}(x) conj(Y'_{s i b}(x+mu))
   The force G = TA(Z) (TA(M) = (M - M^dag)/2 - tr(M - M^dag)/6) then gives
   dS/deps = sum Re tr(G^dag Q) for every traceless anti-hermitian Q.
+
+Hasenbusch ratio factor (the intermediate determinant ratios of Sec. 6,
+det[M(m1)^dag M(m1)] / det[M(m2)^dag M(m2)]), represented by
+  S_r(U) = phi^dag M2 (M1^dag M1)^-1 M2^dag phi,  M_i = M_pc(m_i):
+  chi = M2^dag phi,  X = (M1^dag M1)^-1 chi,  Y = M1 X,
+  dS_r = 2 Re phi^dag dM2 X - 2 Re Y^dag dM1 X.
+  Each term is a bilinear -2 Re L^dag dM R of the form above with its full
+  fields R' = R + M_oo^-1 M_oe R, L' = L + M_oo^-dag M_eo^dag L (at that
+  term's mass), so G_r = G(X'_1, Y'_1) - G(X'_2, phi'_2).  With m1 = m2 the
+  action is phi^dag phi, independent of U, and G_r vanishes.
 """
 from __future__ import annotations
 
@@ -54,6 +64,13 @@ def force_fields(U, phi, M5, mf, tol=1e-13):
     return X + Xo, Y + Yo
 
 
+def bilinear_fields(U, R, L, M5, mf):
+    """Full fields R', L' of a bilinear -2 Re L^dag dM_pc R (R, L even)."""
+    Ro = dwf.mooee_inv(dwf.meo(U, R, 1), M5, mf)
+    Lo = dwf.mooee_inv(dwf.meo(U, L, 1, dag=True), M5, mf, dag=True)
+    return R + Ro, L + Lo
+
+
 def force_from_fields(U, Xf, Yf):
     """G_mu(x) = TA(U A - B U^dag) for the fields X', Y'.  (T,Z,Y,X,4,3,3)."""
     G = np.zeros_like(U)
@@ -75,6 +92,24 @@ def force(U, phis, masses, M5, tol=1e-13):
         Xf, Yf = force_fields(U, phi, M5, mf, tol)
         G += force_from_fields(U, Xf, Yf)
     return G
+
+
+def ratio_action(U, phi, m1, m2, M5, tol=1e-13):
+    """S_r = phi^dag M2 (M1^dag M1)^-1 M2^dag phi by the estimator
+    2 Re <chi, X> - <X, M1^dag M1 X> (chi = M2^dag phi)."""
+    chi = dwf.mpc_dag(U, phi, M5, m2)
+    X = solve_normal(U, chi, M5, m1, tol)
+    return 2 * dwf.inner(chi, X).real - dwf.inner(X, dwf.mpcdag_mpc(U, X, M5, m1)).real
+
+
+def ratio_force(U, phi, m1, m2, M5, tol=1e-13):
+    """G_r of the ratio factor (derivation in the module docstring)."""
+    chi = dwf.mpc_dag(U, phi, M5, m2)
+    X = solve_normal(U, chi, M5, m1, tol)
+    Y = dwf.mpc(U, X, M5, m1)
+    Xf1, Yf1 = bilinear_fields(U, X, Y, M5, m1)
+    Xf2, Pf2 = bilinear_fields(U, X, phi, M5, m2)
+    return force_from_fields(U, Xf1, Yf1) - force_from_fields(U, Xf2, Pf2)
 
 
 def exp_su3(Q):

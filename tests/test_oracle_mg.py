@@ -289,3 +289,52 @@ def test_force_gauge_covariance(force_case):
     Gg = force.force(Ug, phig, masses, M5)
     want = np.einsum("tzyxab,tzyxmbc,tzyxdc->tzyxmad", g, G, g.conj())
     assert np.allclose(Gg, want, atol=1e-10)
+
+
+# ------------------------------------------------------------ Hasenbusch ratio
+@pytest.fixture(scope="module")
+def ratio_case():
+    L = (4, 4, 4, 4)
+    Ls = 4
+    U = synth.random_gauge(L, 0.5, 63)
+    phi = dwf.project_parity(synth.gaussian_spinor(L, Ls, 72), L, 0)
+    return L, Ls, U, phi
+
+
+def test_ratio_force_matches_finite_difference(ratio_case):
+    """dS_r/deps along a random su(3) field against sum Re tr(G_r^dag Q)."""
+    L, Ls, U, phi = ratio_case
+    m1, m2 = 0.05, 0.3
+    G = force.ratio_force(U, phi, m1, m2, M5)
+    assert np.allclose(G, -dwf.dagger(G), atol=1e-14)
+    Q = synth.random_su3_algebra(U.shape[:-2], 84)
+    eps = 1e-5
+    Up = np.einsum("...ij,...jk->...ik", force.exp_su3(eps * Q), U)
+    Um = np.einsum("...ij,...jk->...ik", force.exp_su3(-eps * Q), U)
+    fd = (force.ratio_action(Up, phi, m1, m2, M5) - force.ratio_action(Um, phi, m1, m2, M5)) / (2 * eps)
+    an = np.sum(np.trace(np.conj(np.swapaxes(G, -1, -2)) @ Q, axis1=-2, axis2=-1)).real
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3)
+
+
+def test_ratio_with_equal_masses_is_gauge_independent(ratio_case):
+    """m1 = m2: S_r = phi^dag phi for every U, so its force vanishes while
+    each of its two terms alone does not."""
+    L, Ls, U, phi = ratio_case
+    m = 0.1
+    assert force.ratio_action(U, phi, m, m, M5) == pytest.approx(dwf.norm2(phi), rel=1e-11)
+    G = force.ratio_force(U, phi, m, m, M5)
+    G1 = force.force(U, [dwf.mpc_dag(U, phi, M5, m)], [m], M5)
+    assert np.max(np.abs(G)) <= 1e-10 * np.max(np.abs(G1))
+    assert np.max(np.abs(G1)) > 1e-3
+
+
+def test_ratio_force_gauge_covariance(ratio_case):
+    L, Ls, U, phi = ratio_case
+    g = synth.random_gauge_transform(L, 93)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Ug[..., mu, :, :] = g @ U[..., mu, :, :] @ dwf.dagger(dwf.shift(g, mu, +1))
+    G = force.ratio_force(U, phi, 0.05, 0.3, M5)
+    Gg = force.ratio_force(Ug, dwf.apply_color(g, phi), 0.05, 0.3, M5)
+    want = np.einsum("tzyxab,tzyxmbc,tzyxdc->tzyxmad", g, G, g.conj())
+    assert np.allclose(Gg, want, atol=1e-10)
