@@ -10,6 +10,12 @@ Paper: arXiv:2103.05034.
            dimensional coarsening, so Gamma_5 is a sign on the coarse space
   Sec. 4, Table 1: HDCR coarsens M = H_DW with blocks spanning all of Ls
 
+  Sec. 5.3 (the 48^3 study): a red-black solver on the coarse space; the
+           nearest-neighbour stencil couples each coarse site to itself and
+           to sites of the other coarse parity only, so A = [[A_ee, A_eo],
+           [A_oe, A_oo]] with block-diagonal A_ee, A_oo (the nb x nb self
+           terms) and the even Schur complement S = A_ee - A_eo A_oo^-1 A_oe
+
 Readings:
   * Blocks are b_x x b_y x b_z x b_t x Ls (the whole fifth dimension).
   * The paper implies P^dag P = 1 but does not say how; each (block,
@@ -205,3 +211,58 @@ def coarse_cgnr(A, rc, tol, maxiter):
         rr = rr_new
         it += 1
     return x, it
+
+
+def coarse_parity_mask(Lc_shape):
+    """1 on even coarse sites ((xc + yc + zc + tc) even) of a (Tc,Zc,Yc,Xc) lattice."""
+    t, z, y, x = np.indices(Lc_shape)
+    return ((x + y + z + t) % 2 == 0).astype(float)
+
+
+def coarse_rb_solve(A, rc, tol, maxiter):
+    """Red-black solve of A e = r_c (Sec. 5.3): CG on S^2 e_e = S r'_e with
+    the even Schur complement S (hermitian when A is), r'_e = r_e - A_eo
+    A_oo^-1 r_o, then e_o = A_oo^-1 (r_o - A_oe e_e).  Stops when the
+    normal-equation residual falls below tol times its initial value.  Needs
+    even coarse extents (otherwise the stencil couples a parity to itself:
+    ValueError).  Returns (e, iterations)."""
+    shape = A.shape[1:5]
+    if any(n % 2 for n in shape):
+        raise ValueError("red-black coarse solve needs even coarse extents")
+    me = coarse_parity_mask(shape)[..., None]
+    mo = 1.0 - me
+    self_inv = np.linalg.inv(A[0])
+
+    def off(v):  # sum over the eight neighbour terms
+        out = np.zeros_like(v)
+        for d in range(1, NDIR):
+            out += np.einsum("...jk,...k->...j", A[d], coarse_neighbour(v, d))
+        return out
+
+    def self_apply(M, v):
+        return np.einsum("...jk,...k->...j", M, v)
+
+    def schur(v):  # S v on even sites (v even)
+        t = mo * self_apply(self_inv, mo * off(v))
+        return me * (self_apply(A[0], v) - off(t))
+
+    r_e, r_o = me * rc, mo * rc
+    rp = r_e - me * off(mo * self_apply(self_inv, r_o))
+    b = schur(rp)
+    x = np.zeros_like(rc)
+    r = b.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    bb = rr
+    it = 0
+    while it < maxiter and rr > tol * tol * bb:
+        Ap = schur(schur(p))
+        alpha = rr / np.vdot(p, Ap).real
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    e_o = mo * self_apply(self_inv, r_o - mo * off(x))
+    return x + e_o, it

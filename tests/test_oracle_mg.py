@@ -200,6 +200,33 @@ def test_coarse_apply_and_cgnr(coarse_case):
     assert np.allclose(dense @ e.ravel(), v.ravel(), atol=1e-9 * np.linalg.norm(v))
 
 
+def test_coarse_red_black_solve(coarse_case):
+    """The red-black coarse solve (Sec. 5.3) reaches the dense solution, its
+    Schur complement of the dense operator is hermitian, and it needs no
+    more iterations than CG on A^2 for the same tolerance; odd coarse
+    extents are refused."""
+    L, Ls, block, mf, U, basis = coarse_case
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    shp = A.shape[1:5] + (len(basis),)
+    v = synth.complex_gaussian(6, shp)
+    if any(n % 2 for n in A.shape[1:5]):
+        with pytest.raises(ValueError):
+            coarse.coarse_rb_solve(A, v, 1e-12, 2000)
+        return
+    dense = coarse.coarse_dense_from_stencil(A)
+    e, it = coarse.coarse_rb_solve(A, v, 1e-12, 2000)
+    assert np.allclose(dense @ e.ravel(), v.ravel(), atol=1e-9 * np.linalg.norm(v))
+    # Schur complement against the dense blocks
+    nb = len(basis)
+    par = np.repeat(coarse.coarse_parity_mask(A.shape[1:5]).ravel(), nb) > 0.5
+    ie, io = np.where(par)[0], np.where(~par)[0]
+    S = dense[np.ix_(ie, ie)] - dense[np.ix_(ie, io)] @ np.linalg.solve(dense[np.ix_(io, io)], dense[np.ix_(io, ie)])
+    assert np.allclose(S, S.conj().T, atol=1e-10)
+    _, it_full = coarse.coarse_cgnr(A, v, 1e-8, 2000)
+    _, it_rb = coarse.coarse_rb_solve(A, v, 1e-8, 2000)
+    assert it_rb <= it_full  # half the unknowns, no worse conditioned
+
+
 # ------------------------------------------------------------ V(1,1) and the MG solve
 def test_vcycle_identity_dense(tiny):
     """The sequential x1, x2, x3 update (Eqs. 26-28) equals Eq. (31)'s
