@@ -217,6 +217,17 @@ def mpcdag_mpc(U, psi_e, M5, mf):
     return mpc_dag(U, mpc(U, psi_e, M5, mf), M5, mf)
 
 
+def mpc2(U, psi_e, M5, mf):
+    """The second Schur form of Table 5, (1 - M_ee^-1 M_eo M_oo^-1 M_oe) psi_e,
+    which is M_ee^-1 M_pc psi_e."""
+    return mooee_inv(mpc(U, psi_e, M5, mf), M5, mf)
+
+
+def mpc2_dag(U, psi_e, M5, mf):
+    """(1 - M_ee^-1 M_eo M_oo^-1 M_oe)^dag psi_e = M_pc^dag M_ee^-dag psi_e."""
+    return mpc_dag(U, mooee_inv(psi_e, M5, mf, dag=True), M5, mf)
+
+
 # ---------------------------------------------------------------- inner products
 def inner(a, b):
     """<a, b> = sum conj(a) b."""

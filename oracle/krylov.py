@@ -10,7 +10,8 @@ Readings (the paper gives no details of these standard algorithms):
   * CG is textbook Hestenes-Stiefel CG.
   * The red-black solve prepares the even source b'_e = b_e - M_eo M_oo^-1 b_o,
     solves M_pc^dag M_pc x_e = M_pc^dag b'_e, and reconstructs
-    x_o = M_oo^-1 (b_o - M_oe x_e).
+    x_o = M_oo^-1 (b_o - M_oe x_e).  The second Schur form of Table 5 solves
+    M2 x_e = M_ee^-1 b'_e with M2 = M_ee^-1 M_pc by CG on its normal equations.
   * A solve is judged by the true relative residual ||b - D_DW x|| / ||b||.
 """
 from __future__ import annotations
@@ -66,6 +67,19 @@ def rbcg_solve(U, b, M5, mf, tol, maxiter=100000):
     the even normal equations; the caller judges the true residual."""
     rhs = rb_prepare_source(U, b, M5, mf)
     xe, it, hist = cg(lambda v: dwf.mpcdag_mpc(U, v, M5, mf), rhs, tol, maxiter)
+    return rb_reconstruct(U, b, xe, M5, mf), it, hist
+
+
+def rbcg2_solve(U, b, M5, mf, tol, maxiter=100000):
+    """Red-black CGNR with the second Schur form of Table 5: CG on
+    M2^dag M2 x_e = M2^dag M_ee^-1 b'_e, M2 = 1 - M_ee^-1 M_eo M_oo^-1 M_oe
+    (b'_e = b_e - M_eo M_oo^-1 b_o, x_o reconstructed as for the first form)."""
+    L = dwf.lattice_dims(b)
+    be = dwf.project_parity(b, L, 0)
+    bo = dwf.project_parity(b, L, 1)
+    bprime = be - dwf.meo(U, dwf.mooee_inv(bo, M5, mf), 0)
+    rhs = dwf.mpc2_dag(U, dwf.mooee_inv(bprime, M5, mf), M5, mf)
+    xe, it, hist = cg(lambda v: dwf.mpc2_dag(U, dwf.mpc2(U, v, M5, mf), M5, mf), rhs, tol, maxiter)
     return rb_reconstruct(U, b, xe, M5, mf), it, hist
 
 

@@ -208,6 +208,24 @@ def test_rbcg_matches_dense_solve(tiny):
     assert krylov.true_residual(U, x, b, M5, 0.05) < 1e-11
 
 
+def test_second_schur_form_matches_dense_solve(tiny):
+    """Table 5's second red-black form, (1 - M_ee^-1 M_eo M_oo^-1 M_oe), is
+    M_ee^-1 times the Schur complement, and its CGNR reaches the dense
+    solution."""
+    L, Ls, U, shape, D = tiny
+    mask = np.broadcast_to(dwf.parity_mask(L)[..., None, None, None], shape).ravel() > 0.5
+    e, o = np.where(mask)[0], np.where(~mask)[0]
+    S = D[np.ix_(e, e)] - D[np.ix_(e, o)] @ np.linalg.solve(D[np.ix_(o, o)], D[np.ix_(o, e)])
+    S2 = np.linalg.solve(D[np.ix_(e, e)], S)
+    v = dwf.project_parity(rand_field(L, Ls, 11), L, 0)
+    assert np.allclose(dwf.mpc2(U, v, M5, 0.05).ravel()[e], S2 @ v.ravel()[e], atol=1e-12)
+    assert np.allclose(dwf.mpc2_dag(U, v, M5, 0.05).ravel()[e], S2.conj().T @ v.ravel()[e], atol=1e-12)
+    b = rand_field(L, Ls, 12)
+    x_dense = np.linalg.solve(D, b.ravel()).reshape(shape)
+    x, it, _ = krylov.rbcg2_solve(U, b, M5, 0.05, 1e-13)
+    assert np.linalg.norm(x - x_dense) / np.linalg.norm(x_dense) < 1e-10
+
+
 def test_cgnr_matches_dense_solve(tiny):
     """CG on D^dag D x = D^dag b (the unpreconditioned baseline of Sec. 5.1)
     reaches the dense solution, in more iterations than the red-black solve
