@@ -10,6 +10,12 @@ Paper: arXiv:2103.05034.
            dimensional coarsening, so Gamma_5 is a sign on the coarse space
   Sec. 4, Table 1: HDCR coarsens M = H_DW with blocks spanning all of Ls
 
+  Sec. 3.4 (coarse deflation) and the setup table of Sec. 5: the coarse
+           solve is CG on the normal equations deflated with Lanczos
+           eigenvectors, the Lanczos run on a Chebyshev polynomial of the
+           operator (the high-order polynomial grows fast outside [-1, 1]
+           and so enhances the wanted low modes); the vectors serve as a
+           basis in which the operator is diagonal
   Sec. 5.3 (the 48^3 study): a red-black solver on the coarse space; the
            nearest-neighbour stencil couples each coarse site to itself and
            to sites of the other coarse parity only, so A = [[A_ee, A_eo],
@@ -17,6 +23,12 @@ Paper: arXiv:2103.05034.
            terms) and the even Schur complement S = A_ee - A_eo A_oo^-1 A_oe
 
 Readings:
+  * Coarse deflation: Lanczos with full reorthogonalisation on
+    B = T_n(y(A^2)), y(t) = 2 (t - lam_lo) / (lam_max - lam_lo) - 1 (n even,
+    so the modes of A^2 below lam_lo are B's largest), for nk steps from a
+    Gaussian start; the nev Ritz vectors of B's largest Ritz values are then
+    diagonalised with A^2 itself (Rayleigh-Ritz), giving pairs (theta_i,
+    v_i); the deflated coarse CG starts from sum_i v_i <v_i, b> / theta_i.
   * Blocks are b_x x b_y x b_z x b_t x Ls (the whole fifth dimension).
   * The paper implies P^dag P = 1 but does not say how; each (block,
     chirality) group is orthonormalised by modified Gram-Schmidt, applied
@@ -266,3 +278,63 @@ def coarse_rb_solve(A, rc, tol, maxiter):
         it += 1
     e_o = mo * self_apply(self_inv, r_o - mo * off(x))
     return x + e_o, it
+
+
+def cheby_lanczos(apply_AA, v0, nev, nk, order, lam_lo, lam_max):
+    """Chebyshev-preconditioned Lanczos (reading above) on the hermitian
+    positive operator A^2 (apply_AA): returns (theta, V), nev Rayleigh-Ritz
+    pairs for its lowest modes, V a list of orthonormal vectors."""
+    if order % 2:
+        raise ValueError("even Chebyshev order")
+    from .cheby import cheby_filter
+    B = lambda v: cheby_filter(apply_AA, v, order, lam_lo, lam_max)
+    Q = [v0 / np.sqrt(np.vdot(v0, v0).real)]
+    alpha, beta = [], []
+    for j in range(nk):
+        w = B(Q[j])
+        a = np.vdot(Q[j], w).real
+        alpha.append(a)
+        w = w - a * Q[j] - (beta[j - 1] * Q[j - 1] if j > 0 else 0)
+        for q in Q:  # full reorthogonalisation
+            w = w - np.vdot(q, w) * q
+        b = np.sqrt(np.vdot(w, w).real)
+        if j == nk - 1 or b < 1e-14:
+            break
+        beta.append(b)
+        Q.append(w / b)
+    k = len(alpha)
+    T = np.diag(alpha) + np.diag(beta[:k - 1], 1) + np.diag(beta[:k - 1], -1)
+    mu, S = np.linalg.eigh(T)
+    top = np.argsort(mu)[::-1][:nev]  # B's largest: A^2's lowest
+    W = [sum(S[i, t] * Q[i] for i in range(k)) for t in top]
+    # Rayleigh-Ritz with A^2 on span(W)
+    H = np.array([[np.vdot(wi, apply_AA(wj)) for wj in W] for wi in W])
+    th, C = np.linalg.eigh(0.5 * (H + H.conj().T))
+    V = [sum(C[i, t] * W[i] for i in range(len(W))) for t in range(len(W))]
+    return th, V
+
+
+def coarse_deflated_cgnr(A, rc, theta, V, tol, maxiter):
+    """CG on A^2 e = A r_c (as coarse_cgnr) started from the deflation guess
+    e_0 = sum_i v_i <v_i, A r_c> / theta_i; stops when the normal-equation
+    residual falls below tol times that of the zero start."""
+    b = coarse_apply(A, rc)
+    x = np.zeros_like(rc)
+    for th, v in zip(theta, V):
+        x = x + v * (np.vdot(v, b) / th)
+    AA = lambda u: coarse_apply(A, coarse_apply(A, u))
+    r = b - AA(x)
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    bb = np.vdot(b, b).real
+    it = 0
+    while it < maxiter and rr > tol * tol * bb:
+        Ap = AA(p)
+        alpha = rr / np.vdot(p, Ap).real
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it

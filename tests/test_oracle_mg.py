@@ -227,6 +227,30 @@ def test_coarse_red_black_solve(coarse_case):
     assert it_rb <= it_full  # half the unknowns, no worse conditioned
 
 
+def test_coarse_deflation(coarse_case):
+    """Chebyshev-preconditioned Lanczos on the coarse A^2 finds its lowest
+    eigenvalues (against a dense eigensolver), and the deflated coarse CG
+    reaches the dense solution in fewer iterations than without deflation."""
+    L, Ls, block, mf, U, basis = coarse_case
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    shp = A.shape[1:5] + (len(basis),)
+    dense = coarse.coarse_dense_from_stencil(A)
+    ev = np.linalg.eigvalsh(dense.conj().T @ dense)
+    nev = 6
+    AA = lambda u: coarse.coarse_apply(A, coarse.coarse_apply(A, u))
+    lam_max = 1.1 * krylov.power_max(AA, synth.complex_gaussian(7, shp), 200)
+    lam_lo = 0.5 * (ev[nev] + ev[nev + 1])
+    theta, V = coarse.cheby_lanczos(AA, synth.complex_gaussian(8, shp), nev, 3 * nev, 8, lam_lo, lam_max)
+    assert np.allclose(np.sort(theta), ev[:nev], rtol=1e-8, atol=1e-12 * ev[-1])
+    for th, v in zip(theta, V):
+        assert np.linalg.norm(AA(v) - th * v) <= 1e-6 * ev[-1] * np.linalg.norm(v)
+    r = synth.complex_gaussian(9, shp)
+    e, it_d = coarse.coarse_deflated_cgnr(A, r, theta, V, 1e-10, 5000)
+    assert np.allclose(dense @ e.ravel(), r.ravel(), atol=1e-7 * np.linalg.norm(r))
+    _, it_0 = coarse.coarse_cgnr(A, r, 1e-10, 5000)
+    assert it_d < it_0
+
+
 # ------------------------------------------------------------ V(1,1) and the MG solve
 def test_vcycle_identity_dense(tiny):
     """The sequential x1, x2, x3 update (Eqs. 26-28) equals Eq. (31)'s
