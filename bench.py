@@ -139,46 +139,110 @@ def build_workload(name, rank):
 
 
 # ---------------------------------------------------------------------- CPU oracle legs
-def oracle_dhop_sample(w, U, b):
+# The oracle cannot hold a field of the 48^3 x 96 x 24 workload (49 GB per FP64
+# vector), so its CPU legs run on a sample lattice with the same Ls and link
+# recipe: 8^3 x 16 x Ls, about a second of numpy per D_hop.
+SAMPLE_L = (8, 8, 8, 16)
+
+
+def oracle_sample(w, seed):
+    """(L, U, psi) of the oracle's sample lattice for workload w."""
+    L = w["L"] if int(np.prod(w["L"])) * w["Ls"] <= (1 << 22) else SAMPLE_L
+    U = synth.random_gauge(L, w["eps"], synth.SEED_GAUGE, ape_steps=w["ape"])
+    return L, U, synth.gaussian_spinor(L, w["Ls"], seed)
+
+
+def oracle_dhop_sample(L, Ls, U, psi):
     """One full-lattice FP64 oracle D_hop; returns (seconds, algorithmic bytes)."""
     from oracle import dwf
-    L, Ls = w["L"], w["Ls"]
     t0 = time.perf_counter()
-    dwf.dhop(U, b)
+    dwf.dhop(U, psi)
     dt = time.perf_counter() - t0
-    V5 = int(np.prod(L)) * Ls
-    nbytes = V5 * (24 * 16) + int(np.prod(L)) * 8 * 9 * 16  # FP64 spinors in+out, 8 links per site
+    V4 = int(np.prod(L))
+    nbytes = V4 * Ls * (24 * 16) + V4 * 8 * 9 * 16  # FP64 spinors in+out, 8 links per site
     return dt, nbytes
 
 
-def cpu_baseline_leg(w, U, b):
-    dt, nbytes = oracle_dhop_sample(w, U, b)
-    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full-lattice FP64 numpy D_hop at {'x'.join(map(str, w['L']))}x{w['Ls']} "
-                      f"({dt:.1f} s, single-threaded numpy)",
-            "seconds": dt}
+def _oracle_worker(args):
+    """Spawned worker: `reps` oracle D_hops of its own sample; (seconds, bytes)."""
+    name, seed, reps = args
+    w = synth.WORKLOADS[name]
+    L, U, psi = oracle_sample(w, seed)
+    tot, nb = 0.0, 0
+    for _ in range(reps):
+        dt, b = oracle_dhop_sample(L, w["Ls"], U, psi)
+        tot += dt
+        nb += b
+    return tot, nb
+
+
+def cpu_baseline_leg(name):
+    """The oracle's FP64 D_hop on the host cores: one process, then one process
+    per core (spawned, single-threaded numpy each), every process on its own
+    sample; value = the all-cores throughput in GB/s of algorithmic bytes."""
+    import multiprocessing as mp
+    w = synth.WORKLOADS[name]
+    L, U, psi = oracle_sample(w, synth.SEED_SOURCE)
+    oracle_dhop_sample(L, w["Ls"], U, psi)  # warm
+    reps1 = 3
+    t1, b1 = 0.0, 0
+    for _ in range(reps1):
+        dt, nb = oracle_dhop_sample(L, w["Ls"], U, psi)
+        t1 += dt
+        b1 += nb
+    v1 = b1 / t1 / 1e9
+    ncpu = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    env_before = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"  # inherited by the spawned workers
+    try:
+        t0 = time.perf_counter()
+        with ctx.Pool(ncpu) as pool:
+            res = pool.map(_oracle_worker, [(name, synth.SEED_SOURCE + 10 + i, reps1) for i in range(ncpu)])
+        wall = time.perf_counter() - t0
+    finally:
+        if env_before is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = env_before
+    vall = sum(r[1] for r in res) / max(r[0] for r in res) / 1e9
+    V5w = int(np.prod(w["L"])) * w["Ls"]
+    V5s = int(np.prod(L)) * w["Ls"]
+    per_site_s = t1 / reps1 / V5s
+    sample = f"FP64 numpy oracle D_hop on a {'x'.join(map(str, L))}x{w['Ls']} lattice with the workload's link recipe"
+    return {"value": vall, "unit": UNIT, "cores": ncpu, "kind": "oracle",
+            "sample": sample + f": {reps1} per process, {ncpu} spawned single-threaded processes",
+            "single_core": {"value": v1, "cores": 1, "seconds_per_dhop": t1 / reps1},
+            "all_cores_wall_s": wall,
+            "workload_dhop_seconds_extrapolated": {
+                "one_core": per_site_s * V5w, "all_cores": per_site_s * V5w * v1 / vall,
+                "note": f"per-5D-site time of the sample x the workload's {V5w} sites (extrapolated)"}}
 
 
 def run_reference(args):
+    """--impl reference: the oracle (FP64 numpy, one process) timed on the host
+    cores, each step one full-lattice D_hop on the sample lattice of the
+    workload (its own lattice when that is small)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w, U, b = build_workload(args.workload, 0)
+    w = synth.WORKLOADS[args.workload]
+    L, U, psi = oracle_sample(w, synth.SEED_SOURCE)
     for _ in range(args.warmup):
-        oracle_dhop_sample(w, U, b)
+        oracle_dhop_sample(L, w["Ls"], U, psi)
     times, nbytes = [], 0
     for _ in range(args.steps):
-        dt, nb = oracle_dhop_sample(w, U, b)
+        dt, nb = oracle_dhop_sample(L, w["Ls"], U, psi)
         times.append(dt)
         nbytes += nb
     tot = sum(times)
     val = nbytes / tot / 1e9
-    sample = f"one full-lattice FP64 numpy D_hop at {'x'.join(map(str, w['L']))}x{w['Ls']} per step"
+    sample = f"one full-lattice FP64 numpy D_hop at {'x'.join(map(str, L))}x{w['Ls']} per step"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "oracle": "numpy FP64",
-                                             "l2": "n/a (host)"},
+                                             "sample_lattice": list(L), "l2": "n/a (host)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -290,12 +354,36 @@ def reduce_ranks(seconds, nbytes, device):
     return float(t[0]), float(b[0])
 
 
+def host_mem_available():
+    """MemAvailable of the host in bytes (0 if unknown)."""
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def device_source(ctx, w, b, rank, dev):
+    """The FP64 full-field source on the device: the host Gaussian of the
+    workload when it has one, else a Gaussian drawn on the device (seeded)."""
+    import torch
+
+    from paper_2103_05034_gb300 import layout
+    from paper_2103_05034_gb300._lib import F64
+    if b is not None:
+        return torch.from_numpy(layout.complex_to_real(layout.to_full(b, w["L"]), F64)).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(synth.SEED_SOURCE + rank)
+    return torch.randn(2 * ctx.half_numel(), generator=gen, device=dev, dtype=torch.float64)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2103_05034_gb300 import layout, ops
-    from paper_2103_05034_gb300._lib import F32, F64, SOLVE_MIXED_F32
+    from paper_2103_05034_gb300 import ops
+    from paper_2103_05034_gb300._lib import F32, SOLVE_F64, SOLVE_MIXED_F32
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -308,19 +396,50 @@ def run_ours(args):
     w, U, b = build_workload(args.workload, rank)
     L, Ls, M5, mf = w["L"], w["Ls"], w["M5"], w["mf"]
     ctx = ops.Context(L, Ls, M5, U)
+    del U
     hop_variant, hop_tuned_ms = ops.dwf_autotune(ctx, F32, 20)  # setup, not timed
-    bfull = layout.complex_to_real(layout.to_full(b, L), F64)
-    bd = torch.from_numpy(bfull).to(dev)
-    xd = torch.zeros_like(bd)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def solve(x, bb):
-        return ops.rbcg_solve(ctx, x, bb, mf, args.tol, 100000, SOLVE_MIXED_F32)
+    # ---- dominant kernel first (before the solver's workspace exists): the
+    # FP32 hopping term, timed alone with an L2 flush before each launch
+    gen = torch.Generator(device=dev).manual_seed(synth.SEED_SOURCE + 1)
+    inp = torch.randn(ctx.half_numel(), generator=gen, device=dev, dtype=torch.float32)
+    out = torch.zeros_like(inp)
+    hop_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for _ in range(3):
+        ops.dwf_dhop(ctx, out, inp, 0)
+    for k, (e0, e1) in enumerate(hop_ev):
+        flush.fill_(float(k))
+        e0.record(stream)
+        ops.dwf_dhop(ctx, out, inp, 0)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    hop_ms = float(np.mean([a.elapsed_time(bq) for a, bq in hop_ev]))
+    del inp, out
+    torch.cuda.empty_cache()
+    Vh = ctx.Vh
+    hop_alg_bytes = Vh * (Ls * 24 * 8 + 72 * 8)
+    peaks, peak_kind = measured_peaks()
+    achieved = hop_alg_bytes / (hop_ms / 1e3) / 1e9
+    shash = source_hash("paper_2103_05034_gb300/csrc/dhop_impl.cuh")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": profile_traffic(f"hop_kernel_f32_ls{Ls}_{args.workload}", shash),
+                "kernel": f"dwfk::hop_kernel<F32, Ls={Ls}> (dwf_dhop, plain epilogue, variant {hop_variant})",
+                "launch_ms": hop_ms, "algorithmic_bytes_per_launch": hop_alg_bytes,
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "source_hash": shash}
+
+    # ---- the timed steps: a block of the mixed-precision red-black CG
+    bd = device_source(ctx, w, b, rank, dev)
+    xd = torch.zeros_like(bd)
+    step_iters = args.step_iters if args.step_iters > 0 else 100000
+
+    def step(x, bb):
+        return ops.rbcg_solve(ctx, x, bb, mf, args.tol, step_iters, SOLVE_MIXED_F32, noconv_ok=True)
 
     for _ in range(args.warmup):
-        xd.zero_()
-        solve(xd, bd)
+        step(xd, bd)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -336,7 +455,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        st = solve(xd, bd)
+        st = step(xd, bd)
         ev[k][1].record(stream)
         stats.append(st)
     torch.cuda.synchronize()
@@ -352,53 +471,59 @@ def run_ours(args):
         t_max, tot_bytes = reduce_ranks(t_dev, hop_bytes, dev)
     value = tot_bytes / t_max / 1e9
 
-    # ---- dominant kernel: the FP32 hopping term, timed alone with an L2 flush before each launch
-    inp = ctx.new_half(F32)
-    inp.copy_(torch.from_numpy(layout.complex_to_real(layout.to_half(b, L, 1), F32).reshape(-1)).to(dev))
-    out = torch.zeros_like(inp)
-    hop_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(20)]
-    for _ in range(3):
-        ops.dwf_dhop(ctx, out, inp, 0)
-    for k, (e0, e1) in enumerate(hop_ev):
-        flush.fill_(float(k))
-        e0.record(stream)
-        ops.dwf_dhop(ctx, out, inp, 0)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    hop_ms = float(np.mean([a.elapsed_time(bq) for a, bq in hop_ev]))
-    Vh = ctx.Vh
-    hop_alg_bytes = Vh * (Ls * 24 * 8 + 72 * 8)
-    peaks, peak_kind = measured_peaks()
-    achieved = hop_alg_bytes / (hop_ms / 1e3) / 1e9
-    shash = source_hash("paper_2103_05034_gb300/csrc/dhop_impl.cuh")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"],
-                "traffic": profile_traffic(f"hop_kernel_f32_ls{Ls}_{args.workload}", shash),
-                "kernel": f"dwfk::hop_kernel<F32, Ls={Ls}> (dwf_dhop, plain epilogue)",
-                "launch_ms": hop_ms, "algorithmic_bytes_per_launch": hop_alg_bytes,
-                "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "source_hash": shash}
+    line = None
+    legs = {}
+    if rank == 0:
+        # time to the tolerance on the same GPU: the mixed-precision solve, and
+        # FP64 red-black CG (whole solve with --fp64-full; otherwise a
+        # 16-iteration block whose per-iteration cost projects the solve)
+        try:
+            xd.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sm = ops.rbcg_solve(ctx, xd, bd, mf, args.tol, 100000, SOLVE_MIXED_F32)
+            torch.cuda.synchronize()
+            legs["mixed_rbcg_to_tol"] = {"seconds": time.perf_counter() - t0, "iterations": sm["iterations"],
+                                         "reliable_updates": sm["reliable_updates"],
+                                         "true_residual": sm["true_residual"], "fine_matmuls": sm["fine_matmuls"]}
+        except Exception as e:
+            legs["mixed_rbcg_to_tol"] = {"error": str(e)}
+        try:
+            legs["fp64_rbcg"] = fp64_rbcg_leg(ops, ctx, xd, bd, mf, args, legs.get("mixed_rbcg_to_tol", {}))
+        except Exception as e:
+            legs["fp64_rbcg"] = {"error": str(e)}
 
-    # ---- end to end through the C ABI with pinned host buffers
-    bh = torch.from_numpy(bfull).pin_memory()
-    xh = torch.zeros_like(bh).pin_memory()
-    solve(xh, bh)  # warm
+    # ---- end to end through the C ABI with host buffers (the library copies b
+    # in and x out inside the call); the device copies are freed first
+    n_full = bd.numel()
+    e2e_steps = min(args.steps, args.e2e_steps)
+    need = 2 * n_full * 8
+    avail = host_mem_available()
+    pinned = avail > 3 * need  # pinned buffers only with ample host memory to spare
+    bh = torch.empty(n_full, dtype=torch.float64, pin_memory=pinned)
+    bh.copy_(bd)  # the same source, now in host memory
+    del bd, xd
+    torch.cuda.empty_cache()
+    xh = torch.zeros(n_full, dtype=torch.float64, pin_memory=pinned)
+    step(xh, bh)  # warm (workspace for host buffers)
     ops.dwf_reset_counters(ctx)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_stats = []
-    for _ in range(args.steps):
-        e2e_stats.append(solve(xh, bh))
+    for _ in range(e2e_steps):
+        step(xh, bh)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     _, e2e_bytes = ops.dwf_counters(ctx)
     if world > 1:
         t_e2e, e2e_bytes = reduce_ranks(t_e2e, e2e_bytes, dev)
     e2e = {"value": e2e_bytes / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(bh.numel() * 8),
-           "d2h_bytes_per_step": int(xh.numel() * 8),
-           "note": "rbcg_solve on pinned host b and x: H2D of b and D2H of x inside the call"}
+           "d2h_bytes_per_step": int(xh.numel() * 8), "steps": e2e_steps,
+           "note": f"rbcg_solve on {'pinned' if pinned else 'pageable'} host b and x: H2D of b and D2H of x "
+                   f"inside the call, host clock"}
+    del bh, xh
+    ctx.close()
+    torch.cuda.empty_cache()
 
-    line = None
     if rank == 0:
         s0 = stats[-1]
         line = {
@@ -407,55 +532,93 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "lattice": list(L), "Ls": Ls, "M5": M5, "mf": mf,
-                       "solver": "red-black CGNR, FP32 inner, FP64 reliable updates",
-                       "tol_true_residual": args.tol, "l2": "flushed (512 MB write) before each step",
+                       "step": (f"rbcg_solve from x = 0 stopped after {args.step_iters} CG iterations "
+                                f"(source preparation, FP32 inner CG, FP64 reliable updates, reconstruction, "
+                                f"FP64 true residual)" if args.step_iters > 0 else
+                                f"rbcg_solve to a true residual of {args.tol}"),
+                       "tol_true_residual": args.tol,
+                       "l2": "inputs larger than L2 (one FP32 half field 12 GB) and 512 MB flush before each step",
                        "parallelism": f"replicas{world}",
                        "hop_variant_f32": hop_variant, "hop_autotune_ms": hop_tuned_ms},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "roofline": roofline,
             "e2e": e2e,
-            "solve": {"iterations": s0["iterations"], "reliable_updates": s0["reliable_updates"],
-                      "true_residual": s0["true_residual"], "fine_matmuls": s0["fine_matmuls"],
-                      "seconds": t_max / args.steps, "wall_seconds_all_steps": t_wall},
+            "step_solve": {"iterations": s0["iterations"], "reliable_updates": s0["reliable_updates"],
+                           "true_residual": s0["true_residual"], "fine_matmuls": s0["fine_matmuls"],
+                           "seconds": t_max / args.steps, "wall_seconds_all_steps": t_wall},
         }
-        try:  # the same solve with FP16-storage inner vectors (scaled residual)
-            from paper_2103_05034_gb300._lib import F16S, SOLVE_MIXED_F16
-            ops.dwf_autotune(ctx, F16S, 10)
-            xd.zero_()
-            ops.rbcg_solve(ctx, xd, bd, mf, args.tol, 100000, SOLVE_MIXED_F16)  # warm
-            xd.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s16 = ops.rbcg_solve(ctx, xd, bd, mf, args.tol, 100000, SOLVE_MIXED_F16)
-            torch.cuda.synchronize()
-            line["solve_mixed_f16"] = {"seconds": time.perf_counter() - t0, "iterations": s16["iterations"],
-                                       "reliable_updates": s16["reliable_updates"],
-                                       "true_residual": s16["true_residual"]}
-        except Exception as e:
-            line["solve_mixed_f16"] = {"error": str(e)}
-        try:  # the tensor-core coarse stencil (multi-RHS), measured beside the solve
-            line["coarse_apply_tc"] = coarse_apply_measure(ctx, w, "tf32", 3, 20)
-        except Exception as e:
-            line["coarse_apply_tc"] = {"error": str(e)}
-        try:  # the four pseudofermion solves of the force workload, batched vs one by one
-            line["batched_solves"] = batched_solves_measure(ctx, 1e-10)
-        except Exception as e:
-            line["batched_solves"] = {"error": str(e)}
-        if args.mg_compare:
+        line.update(legs)
+        # legs on the 16^3 x 32 x 16 workload (the fields of the 48^3 one are
+        # too large for their setups): tensor-core coarse stencil, batched
+        # pseudofermion solves, MG against FP64 RB-CG
+        small = "dwf_16x16x16x32_ls16"
+        try:
+            ws_, Us, bs = build_workload(small, 0)
+            cs = ops.Context(ws_["L"], ws_["Ls"], ws_["M5"], Us)
+            ops.dwf_autotune(cs, F32, 10)
             try:
-                line["mg_vs_fp64"] = mg_vs_fp64(ctx, w, b, bd, args.tol)
-            except Exception as e:  # reported, not hidden: the line says what failed
-                line["mg_vs_fp64"] = {"error": str(e)}
+                line["coarse_apply_tc"] = coarse_apply_measure(cs, ws_, "tf32", 3, 20)
+            except Exception as e:
+                line["coarse_apply_tc"] = {"error": str(e)}
+            try:
+                line["batched_solves"] = batched_solves_measure(cs, 1e-10)
+            except Exception as e:
+                line["batched_solves"] = {"error": str(e)}
+            if args.mg_compare:
+                try:
+                    bsd = device_source(cs, ws_, bs, 0, dev)
+                    line["mg_vs_fp64"] = mg_vs_fp64(cs, ws_, bs, bsd, args.tol)
+                    del bsd
+                except Exception as e:  # reported, not hidden: the line says what failed
+                    line["mg_vs_fp64"] = {"error": str(e)}
+            cs.close()
+        except Exception as e:
+            line["small_workload_legs"] = {"error": str(e)}
         if args.cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline_leg(w, U, b)
-    ctx.close()
+            line["cpu_baseline"] = cpu_baseline_leg(args.workload)
+            line["host"] = {"cpu_count": os.cpu_count(), "mem_available_gb": host_mem_available() / 1e9}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if line is not None:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def fp64_rbcg_leg(ops, ctx, xd, bd, mf, args, mixed):
+    """FP64 red-black CG on the same source.  With --fp64-full the whole solve
+    to the tolerance; otherwise blocks of 8 and 16 iterations give the cost of
+    an FP64 iteration (their difference / 8) and of the fixed work (source
+    preparation, reconstruction, true residual), and the solve time is
+    projected with the mixed solve's iteration count (FP64 CG needs the same
+    count here to within a few per cent: 336 against 336 at 16^3 x 32 x 16)."""
+    import torch
+
+    from paper_2103_05034_gb300._lib import SOLVE_F64
+
+    def run(maxiter):
+        xd.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ops.rbcg_solve(ctx, xd, bd, mf, args.tol, maxiter, SOLVE_F64, noconv_ok=True)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, st
+
+    if args.fp64_full:
+        sec, st = run(100000)
+        return {"seconds": sec, "iterations": st["iterations"], "true_residual": st["true_residual"],
+                "measured": "whole solve"}
+    t8, _ = run(8)
+    t16, _ = run(16)
+    per_it = (t16 - t8) / 8
+    fixed = t8 - 8 * per_it
+    out = {"seconds_per_iteration": per_it, "fixed_seconds": fixed, "measured": "blocks of 8 and 16 iterations"}
+    if "iterations" in mixed:
+        out["projected_seconds_to_tol"] = fixed + per_it * mixed["iterations"]
+        out["projected_with_iterations"] = mixed["iterations"]
+        out["speedup_mixed_over_fp64_projected"] = out["projected_seconds_to_tol"] / mixed["seconds"]
+    return out
 
 
 def batched_solves_measure(ctx, tol):
@@ -864,7 +1027,12 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dwf_16x16x16x32_ls16", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="dwf_48x48x48x96_ls24", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--step-iters", type=int, default=48,
+                    help="CG iterations of one timed step (a block of the mixed-precision solve); 0: whole solve")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end (host buffer) measurement")
+    ap.add_argument("--fp64-full", action="store_true",
+                    help="run the whole FP64 red-black CG solve (minutes at 48^3) instead of projecting it")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-mg-compare", dest="mg_compare", action="store_false",

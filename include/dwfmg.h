@@ -134,8 +134,8 @@ int dwf_reset_counters(dwf_ctx* ctx);
  * storage at Ls >= 16, one otherwise) on this context's lattice, `reps`
  * launches each, keeps the fastest for precision `prec` and returns its time
  * per launch in *best_ms (may be NULL).  Variants that do not tile the
- * lattice are skipped.  Uses context workspace; tuning launches are not
- * counted.  Synchronises.  dwf_set_hop_variant / dwf_get_hop_variant pin or
+ * lattice are skipped.  Uses two half fields of context workspace, released
+ * before returning; tuning launches are not counted.  Synchronises.  dwf_set_hop_variant / dwf_get_hop_variant pin or
  * read the choice (0 = untuned default; valid ids 0 .. DWF_HOP_VARIANTS-1;
  * dwf_set_hop_variant returns DWF_EINVAL for a variant that does not tile
  * the lattice). */
@@ -192,13 +192,19 @@ int dwf_cdot(dwf_ctx* ctx, double* result2, const void* a, const void* b, int64_
 /* Allocation-free |a|^2 (the paper has no counterpart; this serves callers
  * that cannot call cudaMalloc when they need a global sum, e.g. code running
  * under a memory pool that forbids new allocations or a plug-in handed only
- * its buffers).  Same result as dwf_norm2 (FP64 accumulation, fixed order) for
- * n complex numbers of precision prec at device address a; *result on host.
+ * its buffers).  |a|^2 of n complex numbers of precision prec at device address
+ * a, summed in FP64 in a fixed order; *result on host.  For FP64 data this is
+ * dwf_norm2's result up to summation order; for FP32 and FP16-storage data it
+ * agrees with dwf_norm2 (which sums each thread's share in compensated FP32)
+ * to within that FP32 reduction error (about 1e-7 relative).
  * Needs no context and allocates nothing: the reduction scratch is a static
  * device array in the library (512 KiB per GPU that loads it, held until
  * exit).  n <= 2^31, else DWF_EINVAL.  All calls on a device share that
  * scratch: calls that overlap on the GPU race.  The first call on a device
- * looks up the scratch address and should come before any stream capture.
+ * looks up the scratch address and should come before any stream capture;
+ * the address is cached for the device's primary context, so the call must
+ * not be used on a device again after cudaDeviceReset in the same process.
+ * Returns DWF_ECUDA if a launch or the copy of the result fails.
  * Synchronises `stream`. */
 int dwf_norm2_noalloc(double* result, const void* a, int64_t n, int prec, void* stream);
 
@@ -210,6 +216,14 @@ int dwf_norm2_noalloc(double* result, const void* a, int64_t n, int prec, void* 
  * expected outcome: the GPU stays usable and the status reaches the host),
  * DWF_OK if either wait unexpectedly completed.  Synchronises `stream`. */
 int dwf_selftest_wait_timeout(int* gave_up, void* stream);
+
+/* Measured fused multiply-add rates of this GPU's CUDA cores (no counterpart
+ * in the paper: the ALU roof for the FP64 hopping kernel and the FP64 parts
+ * of the solvers, measured instead of taken from a spec sheet).  Runs 8
+ * independent FMA chains per thread on 8 CTAs of 256 threads per SM, best of
+ * three timed launches per type (CUDA events); 2 flops per FMA.  Results in
+ * TFLOP/s on the host.  Synchronises `stream`.  DWF_ECUDA if a launch fails. */
+int dwf_measure_fma_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
 
 /* ------------------------------------------------------------------ solvers */
 
@@ -225,6 +239,17 @@ int dwf_selftest_wait_timeout(int* gave_up, void* stream);
  * may be NULL. */
 int rbcg_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int maxiter,
                int policy, dwf_solve_stats* stats, void* stream);
+
+/* The second Schur form of Table 5 (second prec-CGNR row): the same
+ * red-black solve of D_DW x = b with the even operator
+ * M2 = 1 - M_ee^-1 M_eo M_oo^-1 M_oe = M_ee^-1 M_pc: CG on M2^dag M2 x_e =
+ * M2^dag M_ee^-1 b'_e, then x_o = M_oo^-1 (b_o - M_oe x_e).  Same buffers,
+ * stopping rule (FP64 true residual of D_DW), stats and errors as
+ * rbcg_solve; policy DWF_SOLVE_F64 or DWF_SOLVE_MIXED_F32 (DWF_EINVAL
+ * otherwise).  The paper's comparison point: more iterations than the first
+ * form for the same residual. */
+int rbcg2_solve(dwf_ctx* ctx, void* x, const void* b, double mf, double tol, int maxiter,
+                int policy, dwf_solve_stats* stats, void* stream);
 
 /* CG on the even normal equations M_pc^dag M_pc x = phi (Sec. 2.1, Eq. 9),
  * the pseudofermion solve of HMC: phi and x are FP64 even half fields in
@@ -289,6 +314,35 @@ int rbcg_normal_solve_batch(dwf_ctx* ctx, void* x, const void* phi, const double
  * or DWF_F32), device memory. */
 int dwf_force(dwf_ctx* ctx, void* force, const void* X, const double* mf, int npf, int prec,
               void* stream);
+
+/* Hasenbusch ratio factors (Sec. 6: the intermediate determinant ratios
+ * det[M(m1)^dag M(m1)] / det[M(m2)^dag M(m2)] of the HMC), represented by
+ *   S_r = phi^dag M2 (M1^dag M1)^-1 M2^dag phi,  M_i = M_pc(m_i)  (Sec. 5.1).
+ * With X = (M1^dag M1)^-1 M2^dag phi (the caller's normal solve of
+ * chi = M2^dag phi, e.g. rbcg_normal_solve after dwf_mpc with dagger = 1),
+ * dS_r = 2 Re phi^dag dM2 X - 2 Re (M1 X)^dag dM1 X, and this call adds
+ *   G_r = G(X', (M1 X)'; m1) - G(X', phi'; m2)
+ * to `force` for each of nratio factors (1 <= nratio <= 32), G the bilinear
+ * force of dwf_force with the full fields R' = R + M_oo^-1 M_oe R and
+ * L' = L + M_oo^-dag M_eo^dag L at that term's mass.  Same convention,
+ * layouts and force buffer as dwf_force; X and phi: nratio even half fields
+ * of precision prec (DWF_F64 or DWF_F32) back to back, device memory;
+ * m1, m2: host arrays of nratio finite masses.  With m1 = m2 the factor is
+ * phi^dag phi and its force vanishes.  DWF_EINVAL for bad arguments,
+ * DWF_ENOMEM when the workspace (eight half fields per factor) does not fit. */
+int dwf_ratio_force(dwf_ctx* ctx, void* force, const void* X, const void* phi, const double* m1,
+                    const double* m2, int nratio, int prec, void* stream);
+
+/* Pseudofermion action by the variational estimator (HMC context of Sec. 6
+ * on the operator of Sec. 5.1):
+ *   *S = sum_i [2 Re <phi_i, X_i> - |M_pc(mf[i]) X_i|^2]
+ * for npf FP64 even half fields phi, X back to back in device memory (X an
+ * approximate (M_pc^dag M_pc)^-1 phi; the estimator's error is quadratic in
+ * the solve's).  With phi replaced by chi = M2^dag phi and mf by m1 it is the
+ * action of the ratio factors of dwf_ratio_force.  FP64 sums; *S on host;
+ * DWF_ENAN if the result is not finite.  Synchronises. */
+int dwf_pf_action(dwf_ctx* ctx, double* S, const void* phi, const void* X, const double* mf, int npf,
+                  void* stream);
 
 /* Power method estimate of the largest eigenvalue of D_DW^dag D_DW (Sec. 3.4),
  * `iters` iterations (v <- A v / |A v|, lambda = <v, A v>) from the FP64 full

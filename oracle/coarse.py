@@ -10,7 +10,7 @@ Paper: arXiv:2103.05034.
            dimensional coarsening, so Gamma_5 is a sign on the coarse space
   Sec. 4, Table 1: HDCR coarsens M = H_DW with blocks spanning all of Ls
 
-  Sec. 3.4 (coarse deflation) and the setup table of Sec. 5: the coarse
+  Sec. 3.5 (coarse space deflation) and the setup table of Sec. 5: the coarse
            solve is CG on the normal equations deflated with Lanczos
            eigenvectors, the Lanczos run on a Chebyshev polynomial of the
            operator (the high-order polynomial grows fast outside [-1, 1]

@@ -108,9 +108,13 @@ _SIGS = {
     "dwf_cdot": (I, [P, C.POINTER(D), P, P, I64, I, P]),
     "dwf_norm2_noalloc": (I, [C.POINTER(D), P, I64, I, P]),
     "dwf_selftest_wait_timeout": (I, [C.POINTER(C.c_int), P]),
+    "dwf_measure_fma_peaks": (I, [C.POINTER(D), C.POINTER(D), P]),
     "rbcg_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
+    "rbcg2_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
     "dwf_power_max": (I, [P, C.POINTER(D), P, D, I, I, P]),
     "dwf_force": (I, [P, P, P, C.POINTER(D), I, I, P]),
+    "dwf_ratio_force": (I, [P, P, P, P, C.POINTER(D), C.POINTER(D), I, I, P]),
+    "dwf_pf_action": (I, [P, C.POINTER(D), P, P, C.POINTER(D), I, P]),
     "rbcg_normal_solve": (I, [P, P, P, D, D, I, I, C.POINTER(SolveStats), P]),
     "cgnr_solve": (I, [P, P, P, D, D, I, C.POINTER(SolveStats), P]),
     "rbcg_solve_batch": (I, [P, P, P, C.POINTER(D), I, D, I, I, C.POINTER(SolveStats), P]),

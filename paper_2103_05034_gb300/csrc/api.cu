@@ -344,6 +344,13 @@ extern "C" int dwf_autotune(dwf_ctx* c, int prec, int reps, double* best_ms, voi
   c->hop_variant[prec] = best;
   c->launches = launches0;  // tuning launches are not counted
   c->hop_bytes = bytes0;
+  // the two tuning fields are released (at 48^3 x 96 x 24 they are 24 GB)
+  DWF_CUDA(c, cudaStreamSynchronize(st));
+  for (int slot = 30; slot <= 31; slot++) {
+    if (c->ws[slot]) cudaFree(c->ws[slot]);
+    c->ws[slot] = nullptr;
+    c->ws_bytes[slot] = 0;
+  }
   if (best_ms) *best_ms = best_t;
   DWF_CUDA(c, cudaGetLastError());
   return DWF_OK;
@@ -464,6 +471,33 @@ int mpc_apply(dwf_ctx* c, void* out, const void* in, void* tmp, const double* mf
   h2.mf = mf;
   h2.reduce = reduce;
   return launch_hop(c, h2, prec, st, nparts);
+}
+
+// The second Schur form of Table 5, M2 = 1 - M_ee^-1 M_eo M_oo^-1 M_oe =
+// M_ee^-1 M_pc: the second hopping launch of M_pc ends with M_ee^-1 in its
+// epilogue, M_ee^-1 (M_ee in + 1/2 D_eo tmp).  reduce: |out|^2 partials.
+static int mpc2_apply(dwf_ctx* c, void* out, const void* in, void* tmp, const double* mf, int prec, int nrhs,
+                      int reduce, cudaStream_t st, int* nparts) {
+  HopLaunch h1 = hop_base(tmp, in, 1, 0, nrhs, -0.5);
+  h1.inv_mode = 1;
+  h1.mf = mf;
+  int rc = launch_hop(c, h1, prec, st, nullptr);
+  if (rc) return rc;
+  HopLaunch h2 = hop_base(out, tmp, 0, 0, nrhs, 0.5);
+  h2.aux = in;
+  h2.aux_mode = 2;
+  h2.inv_mode = 1;
+  h2.mf = mf;
+  h2.reduce = reduce;
+  return launch_hop(c, h2, prec, st, nparts);
+}
+
+// M_ee^-dag M_ee^-1 v in place (one field of precision prec): the factor that
+// turns M_pc^dag into M2^dag M_ee^-1 (M2^dag = M_pc^dag M_ee^-dag).
+static int mee_inv_pair(dwf_ctx* c, void* v, const double* mf, int prec, cudaStream_t st) {
+  int rc = launch_mooee(c, v, v, mf, 0, 1, prec, 1, 0, st);
+  if (rc) return rc;
+  return launch_mooee(c, v, v, mf, 1, 1, prec, 1, 0, st);
 }
 
 enum { WS_TMP_O = 0, WS_TMP_E = 1 };
@@ -618,13 +652,21 @@ static int cg_apply(dwf_ctx* c, void* Ap, const void* p, void* y, void* todd, co
 // One fused CG step: y = M_pc p (|y|^2 = <p, A p> -> alpha), then
 // A p = M_pc^dag y whose last hopping launch updates x += alpha p,
 // r -= alpha A p and reduces |r|^2 (A p is never stored); *nparts partials.
+// Schur form 2 (form = 2): y = M2 p, then w = M_ee^-dag y in wtmp and A p =
+// M_pc^dag w, so that A = M2^dag M2.
 static int cg_step_fused(dwf_ctx* c, void* x, void* r, const void* p, void* y, void* todd, const double* mf,
-                         int prec, cudaStream_t st, int* nparts) {
+                         int prec, cudaStream_t st, int* nparts, int form = 1, void* wtmp = nullptr) {
   int np = 0;
-  int rc = mpc_apply(c, y, p, todd, mf, 0, prec, 1, 1, st, &np);
+  int rc = form == 2 ? mpc2_apply(c, y, p, todd, mf, prec, 1, 1, st, &np)
+                     : mpc_apply(c, y, p, todd, mf, 0, prec, 1, 1, st, &np);
   if (rc) return rc;
   rc = blas_finalize_mode(c, np, 1, S_PAP, 1, st);
   if (rc) return rc;
+  if (form == 2) {
+    rc = launch_mooee(c, wtmp, y, mf, 1, 1, prec, 1, 0, st);
+    if (rc) return rc;
+    y = wtmp;
+  }
   HopLaunch h1 = hop_base(todd, y, 1, 1, 1, -0.5);
   h1.inv_mode = 2;
   h1.mf = mf;
@@ -653,7 +695,7 @@ struct CGBufs {
 };
 
 static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, double tol, int maxiter, int plo,
-                   const double* mfa, dwf_solve_stats& S, double& matmuls, cudaStream_t st) {
+                   const double* mfa, dwf_solve_stats& S, double& matmuls, cudaStream_t st, int form = 1) {
   const int64_t he = half_elems(c);
   const size_t b64 = he * 16, blo = he * dwf_complex_bytes(plo);
   int rc;
@@ -709,6 +751,10 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
         r = norm2_dev(c, yhi, he, DWF_F64, S_TMP2, st);
         if (r) return r;
         if (plo == DWF_F64) {
+          if (form == 2) {  // r = M2^dag M_ee^-1 y = M_pc^dag M_ee^-dag M_ee^-1 y
+            r = mee_inv_pair(c, yhi, mfa, DWF_F64, st);
+            if (r) return r;
+          }
           r = mpc_apply(c, rhi, yhi, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
         } else if (scaled) {  // M_pc^dag on y / sigma_y, scaled back into rhi
           r = read_scalars(c, S_TMP2, 1, st);
@@ -723,6 +769,10 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
         } else {
           r = blas_copy(c, B.ylo, plo, yhi, DWF_F64, he, st);
           if (r) return r;
+          if (form == 2) {
+            r = mee_inv_pair(c, B.ylo, mfa, plo, st);
+            if (r) return r;
+          }
           r = mpc_apply(c, rlo, B.ylo, B.olo, mfa, 1, plo, 1, 0, st, nullptr);
           if (r) return r;
           r = blas_copy(c, rhi, DWF_F64, rlo, plo, he, st);
@@ -808,7 +858,7 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
   bool converged = true_res <= tol;
   while (!converged && it < maxiter) {
     int np = 0;
-    rc = cg_step_fused(c, xin, rlo, p, B.ylo, B.olo, mfa, plo, st, &np);
+    rc = cg_step_fused(c, xin, rlo, p, B.ylo, B.olo, mfa, plo, st, &np, form, B.Ap);
     if (rc) return rc;
     rc = blas_finalize_mode(c, np, 1, S_RRNEW, 2, st);
     if (rc) return rc;
@@ -845,12 +895,34 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
   return DWF_OK;
 }
 
-extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double tol, int maxiter,
-                          int policy, dwf_solve_stats* stats, void* stream) {
+// |b_e - (D x)_e|^2 into dscal[dst] and |b_o - (D x)_o|^2 into dscal[dst+1]
+// for full FP64 fields x, b (FP64 D_DW at mass mfa[0]); te, to: half temporaries.
+static int true_residual_halves(dwf_ctx* c, const void* x, const void* b, void* te, void* to, const double* mfa,
+                                int dst, cudaStream_t st) {
+  const int64_t he = half_elems(c);
+  for (int po = 0; po < 2; po++) {
+    void* t = po ? to : te;
+    HopLaunch h = hop_base(t, (const double2*)x + (1 - po) * he, po, 0, 1, -0.5);
+    h.aux = (const double2*)x + po * he;
+    h.aux_mode = 2;
+    h.mf = mfa;
+    int rc = launch_hop(c, h, DWF_F64, st, nullptr);
+    if (rc) return rc;
+    rc = blas_axpby(c, 1.0, (const double2*)b + po * he, DWF_F64, -1.0, t, DWF_F64, he, st);
+    if (rc) return rc;
+    rc = norm2_dev(c, t, he, DWF_F64, dst + po, st);
+    if (rc) return rc;
+  }
+  return DWF_OK;
+}
+
+// Red-black CGNR on Schur form `form` (1: M_pc, 2: M2 = M_ee^-1 M_pc).
+static int rbcg_solve_form(dwf_ctx* c, void* x, const void* b, double mf, double tol, int maxiter, int policy,
+                           dwf_solve_stats* stats, void* stream, int form) {
   Timer timer;
   if (!c || !x || !b) return DWF_EINVAL;
   if (!(tol > 0) || maxiter < 1) return dwf_fail(c, DWF_EINVAL, "bad tol or maxiter");
-  if (policy < DWF_SOLVE_F64 || policy > DWF_SOLVE_MIXED_F16)
+  if (policy < DWF_SOLVE_F64 || policy > DWF_SOLVE_MIXED_F16 || (form == 2 && policy == DWF_SOLVE_MIXED_F16))
     return dwf_fail(c, DWF_EINVAL, "bad policy");
   cudaStream_t st = (cudaStream_t)stream;
   const int plo = policy == DWF_SOLVE_F64 ? DWF_F64 : policy == DWF_SOLVE_MIXED_F16 ? DWF_F16S : DWF_F32;
@@ -875,18 +947,30 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
     dx = (double2*)w;
   }
   if (((uintptr_t)db & 15) || ((uintptr_t)dx & 15)) return dwf_fail(c, DWF_EINVAL, "alignment");
+  // Buffers that are never live at the same time share memory, so that the
+  // solve fits one GPU at 48^3 x 96 x 24 (one FP64 half field: 24.5 GB):
+  //  * rhs is read once, by the first reliable update, which copies it into rhi;
+  //  * FP64 inner vectors: rlo is rhi's copy made at every reliable update, and
+  //    the step temporaries ylo, olo are free while the reliable update uses
+  //    yhi, ohi;
+  //  * FP32 inner vectors: rhi is only the FP64 copy of rlo, formed after the
+  //    reliable update is done with yhi; the FP32 M_pc x of an early update
+  //    goes to rlo, which the update then recomputes;
+  //  * Ap is needed only by the second Schur form (M_ee^-dag M2 p).
+  // FP16-storage vectors keep separate buffers (rhi holds the unscaled residual).
+  const bool f64 = plo == DWF_F64, f32 = plo == DWF_F32;
   void* bp = dwf_workspace(c, WS_BP, b64);
-  void* rhs = dwf_workspace(c, WS_RHS, b64);
-  void* rhi = dwf_workspace(c, WS_RHI, b64);
   void* yhi = dwf_workspace(c, WS_YHI, b64);
   void* ohi = dwf_workspace(c, WS_OHI, b64);
-  void* xlo = plo == DWF_F64 ? nullptr : dwf_workspace(c, WS_XLO, plo == DWF_F16S ? he * 8 : blo);
-  void* rlo = dwf_workspace(c, WS_RLO, blo);
+  void* rhi = f32 ? yhi : dwf_workspace(c, WS_RHI, b64);
+  void* rhs = rhi;
+  void* xlo = f64 ? nullptr : dwf_workspace(c, WS_XLO, plo == DWF_F16S ? he * 8 : blo);
+  void* rlo = f64 ? rhi : dwf_workspace(c, WS_RLO, blo);
   void* p = dwf_workspace(c, WS_P, blo);
-  void* Ap = dwf_workspace(c, WS_AP, blo);
-  void* ylo = dwf_workspace(c, WS_YLO, blo);
-  void* olo = dwf_workspace(c, WS_OLO, blo);
-  if (!bp || !rhs || !rhi || !yhi || !ohi || (plo != DWF_F64 && !xlo) || !rlo || !p || !Ap || !ylo || !olo)
+  void* ylo = f64 ? yhi : dwf_workspace(c, WS_YLO, blo);
+  void* olo = f64 ? ohi : dwf_workspace(c, WS_OLO, blo);
+  void* Ap = (form == 2 || plo == DWF_F16S) ? dwf_workspace(c, WS_AP, blo) : rlo;
+  if (!bp || !rhs || !rhi || !yhi || !ohi || (!f64 && !xlo) || !rlo || !p || !Ap || !ylo || !olo)
     return dwf_fail(c, DWF_ENOMEM, "solver workspace");
   const double2* b_e = db;
   const double2* b_o = db + he;
@@ -920,13 +1004,24 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
     rc = launch_hop(c, h, DWF_F64, st, nullptr);
     if (rc) return rc;
   }
-  // rhs = M_pc^dag b'_e
-  rc = mpc_apply(c, rhs, bp, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+  // rhs = M_pc^dag b'_e (form 1) or M2^dag M_ee^-1 b'_e = M_pc^dag M_ee^-dag
+  // M_ee^-1 b'_e (form 2; yhi is free here and is not rhs in that form)
+  if (form == 2) {
+    // with FP32 inner vectors rhs is yhi: the temporary is then x_e, which
+    // the CG clears before its first use
+    void* t = rhs == yhi ? (void*)x_e : yhi;
+    DWF_CUDA(c, cudaMemcpyAsync(t, bp, b64, cudaMemcpyDeviceToDevice, st));
+    rc = mee_inv_pair(c, t, mfa, DWF_F64, st);
+    if (rc) return rc;
+    rc = mpc_apply(c, rhs, t, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+  } else {
+    rc = mpc_apply(c, rhs, bp, ohi, mfa, 1, DWF_F64, 1, 0, st, nullptr);
+  }
   if (rc) return rc;
   matmuls += 3;
 
   CGBufs B = {rhs, bp, rhi, yhi, ohi, xlo, rlo, p, Ap, ylo, olo};
-  rc = cg_core(c, x_e, B, bnorm, tol, maxiter, plo, mfa, S, matmuls, st);
+  rc = cg_core(c, x_e, B, bnorm, tol, maxiter, plo, mfa, S, matmuls, st, form);
   if (rc) return rc;
 
 
@@ -941,20 +1036,15 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
     if (rc) return rc;
   }
   matmuls += 1;
-  // true residual ||b - D x|| / ||b|| in FP64
-  void* full = dwf_workspace(c, WS_FULL, 2 * b64);
-  if (!full) return dwf_fail(c, DWF_ENOMEM, "workspace");
-  rc = ddw_apply(c, full, dx, mfa, 0, 0, DWF_F64, 1, st);
+  // true residual ||b - D x|| / ||b|| in FP64, one parity at a time in the
+  // half-field temporaries: (D x)_p = M_pp x_p - 1/2 D_hop x_{1-p}
+  rc = true_residual_halves(c, dx, db, yhi, ohi, mfa, S_TMP2, st);
   if (rc) return rc;
   matmuls += 2;
-  rc = blas_axpby(c, 1.0, db, DWF_F64, -1.0, full, DWF_F64, 2 * he, st);
-  if (rc) return rc;
-  rc = norm2_dev(c, full, 2 * he, DWF_F64, S_TMP2, st);
-  if (rc) return rc;
   if (host_x) DWF_CUDA(c, cudaMemcpyAsync(x, dx, 2 * b64, cudaMemcpyDeviceToHost, st));
-  rc = read_scalars(c, S_TMP2, 1, st);
+  rc = read_scalars(c, S_TMP2, 2, st);
   if (rc) return rc;
-  S.true_residual = sqrt(c->hscal[S_TMP2]) / bnorm;
+  S.true_residual = sqrt(c->hscal[S_TMP2] + c->hscal[S_TMP2 + 1]) / bnorm;
   S.fine_matmuls = matmuls / 2.0;
   S.seconds = timer.sec();
   S.status = S.true_residual <= tol ? DWF_OK : DWF_ENOCONV;
@@ -962,6 +1052,16 @@ extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double 
   if (stats) *stats = S;
   if (S.status == DWF_ENOCONV) return dwf_fail(c, DWF_ENOCONV, "maxiter reached before tol");
   return DWF_OK;
+}
+
+extern "C" int rbcg_solve(dwf_ctx* c, void* x, const void* b, double mf, double tol, int maxiter, int policy,
+                          dwf_solve_stats* stats, void* stream) {
+  return rbcg_solve_form(c, x, b, mf, tol, maxiter, policy, stats, stream, 1);
+}
+
+extern "C" int rbcg2_solve(dwf_ctx* c, void* x, const void* b, double mf, double tol, int maxiter, int policy,
+                           dwf_solve_stats* stats, void* stream) {
+  return rbcg_solve_form(c, x, b, mf, tol, maxiter, policy, stats, stream, 2);
 }
 
 extern "C" int rbcg_normal_solve(dwf_ctx* c, void* x, const void* phi, double mf, double tol, int maxiter,

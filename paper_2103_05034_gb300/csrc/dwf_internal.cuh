@@ -255,7 +255,8 @@ enum {
   WS_XO = 35,
   WS_FXO = 36,   // force: X_o, Y_e, Y_o of all pseudofermions
   WS_FYE = 37,
-  WS_FYO = 38
+  WS_FYO = 38,
+  WS_FXE = 39    // ratio force: X twice (one copy per bilinear)
 };
 
 // Device scalar slots.

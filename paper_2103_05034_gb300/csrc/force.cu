@@ -9,6 +9,7 @@
 // so that dS/deps = sum Re tr(G^dag Q) for U -> exp(eps Q) U, Q in su(3).
 // Each spin trace is a two-spinor product: Y^dag (1 -+ gamma) X = h_Y^dag h_X
 // with both fields projected by the same (1 -+ gamma) half-spinor map.
+#include <math.h>
 #include <string.h>
 
 #include <type_traits>
@@ -60,7 +61,8 @@ __device__ __forceinline__ void outer2(cpx<R> (&o)[9], const cpx<R> (&hx)[2][3],
 // Sum over the Ls threads of each site of one 3x3 complex matrix per thread
 // (shared-memory reduction, fixed order), added to AB[site][slot] in FP64.
 template <class R, int LS, int SB>
-__device__ __forceinline__ void site_sum(R* red, double2* AB, int slot, const cpx<R> (&o)[9], int sl, int s) {
+__device__ __forceinline__ void site_sum(R* red, double2* AB, int slot, const cpx<R> (&o)[9], int sl, int s,
+                                         double coef) {
   constexpr int NT = LS * SB;
 #pragma unroll
   for (int e = 0; e < 9; e++) {
@@ -73,14 +75,20 @@ __device__ __forceinline__ void site_sum(R* red, double2* AB, int slot, const cp
     R acc = 0;
     for (int q = 0; q < LS; q++) acc += red[(sl2 * LS + q) * 18 + e];
     double* dst = (double*)(AB + (sl2 * 8 + slot) * 9);
-    dst[e] += (double)acc;
+    dst[e] += coef * (double)acc;
   }
   __syncthreads();
 }
 
+// Weight of each field pair in the sum (+1 for a pseudofermion; +1 and -1
+// for the two bilinears of a Hasenbusch ratio factor).
+struct ForceCoef {
+  double c[DWF_MAX_RHS];
+};
+
 // One CTA: SB checkerboard sites of one parity x Ls threads (s fastest, so
 // the neighbours' spinors are read as contiguous Ls-runs), all npf
-// pseudofermions.  Each thread forms the s-slice of A_mu and B_mu for the 4
+// pseudofermions (field pairs f, each weighted by coef.c[f]).  Each thread forms the s-slice of A_mu and B_mu for the 4
 // directions; the Ls slices (and the pseudofermions, G being linear in A and
 // B) are summed per site in shared memory, and 4 threads per site form G_mu,
 // reading each link once for all pseudofermions.  The final products run in
@@ -92,7 +100,7 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
                                                  const typename Prec<P>::S* Yo, long long fstride, int npf,
                                                  const typename Prec<P>::LS* links_e,
                                                  const typename Prec<P>::LS* links_o, int L0, int L1, int L2, int L3,
-                                                 int Vh) {
+                                                 int Vh, const ForceCoef coef) {
   typedef typename Prec<P>::R R;
   typedef typename Prec<P>::S S;
   __shared__ R red[SB * LS * 18];
@@ -149,11 +157,11 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
       proj<R, MU>(hx, xa, R(1));
       proj<R, MU>(hy, ya, R(1));
       outer2<R>(o, hx, hy);
-      site_sum<R, LS, SB>(red, AB, MU, o, sl, s);
+      site_sum<R, LS, SB>(red, AB, MU, o, sl, s, coef.c[f]);
       proj<R, MU>(hx, xb, R(-1));
       proj<R, MU>(hy, yb, R(-1));
       outer2<R>(o, hx, hy);
-      site_sum<R, LS, SB>(red, AB, 4 + MU, o, sl, s);
+      site_sum<R, LS, SB>(red, AB, 4 + MU, o, sl, s, coef.c[f]);
     };
     dir(std::integral_constant<int, 0>());
     dir(std::integral_constant<int, 1>());
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
 
 template <int P>
 int launch_force(dwf_ctx* c, double2* force, const void* Xe, const void* Xo, const void* Ye, const void* Yo,
-                 int npf, cudaStream_t st) {
+                 int npf, const ForceCoef& coef, cudaStream_t st) {
   typedef typename Prec<P>::S S;
   typedef typename Prec<P>::LS LT;
   const LT* le = P == DWF_F64 ? (const LT*)c->links64[0] : (const LT*)c->links32[0];
@@ -227,7 +235,7 @@ int launch_force(dwf_ctx* c, double2* force, const void* Xe, const void* Xo, con
     dim3 grid((unsigned)((c->g.Vh + SB - 1) / SB), 2);                                                       \
     k_force<P, LSV, SB><<<grid, LSV * SB, 0, st>>>(force, (const S*)Xe, (const S*)Xo, (const S*)Ye,         \
                                                    (const S*)Yo, fs, npf, le, lo, c->g.L[0], c->g.L[1],      \
-                                                   c->g.L[2], c->g.L[3], (int)c->g.Vh);                      \
+                                                   c->g.L[2], c->g.L[3], (int)c->g.Vh, coef);                \
     break;                                                                                                   \
   }
   switch (c->g.Ls) {
@@ -244,12 +252,57 @@ int launch_force(dwf_ctx* c, double2* force, const void* Xe, const void* Xo, con
 
 }  // namespace
 
+// Odd halves of the field pairs and the force kernel: Xo (when not given) =
+// M_oo^-1 M_oe Xe and Yo = M_oo^-dag M_eo^dag Ye, each pair f with its own
+// mass mf[f]; then force += sum_f coef[f] G(X'_f, Y'_f).
+static int force_tail(dwf_ctx* c, void* force, const void* Xe, void* Xo, bool have_xo, const void* Ye, void* Yo,
+                      const double* mf, const ForceCoef& coef, int nf, int prec, cudaStream_t st) {
+  int rc;
+  if (!have_xo) {
+    HopLaunch hx;
+    memset(&hx, 0, sizeof(hx));
+    hx.out = Xo;
+    hx.in = Xe;
+    hx.out_parity = 1;
+    hx.nrhs = nf;
+    hx.alpha = -0.5;
+    hx.inv_mode = 1;
+    hx.mf = mf;
+    rc = launch_hop(c, hx, prec, st, nullptr);
+    if (rc) return rc;
+  }
+  HopLaunch h;
+  memset(&h, 0, sizeof(h));
+  h.out = Yo;
+  h.in = Ye;
+  h.out_parity = 1;
+  h.dagger = 1;
+  h.nrhs = nf;
+  h.alpha = -0.5;
+  h.inv_mode = 2;
+  h.mf = mf;
+  rc = launch_hop(c, h, prec, st, nullptr);
+  if (rc) return rc;
+  rc = prec == DWF_F64 ? launch_force<DWF_F64>(c, (double2*)force, Xe, Xo, Ye, Yo, nf, coef, st)
+                       : launch_force<DWF_F32>(c, (double2*)force, Xe, Xo, Ye, Yo, nf, coef, st);
+  if (rc) return rc;
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+static int force_args(dwf_ctx* c, const void* force, const void* X, int npf, int max_npf, int prec) {
+  if (npf > max_npf) return dwf_fail(c, DWF_EINVAL, "npf out of range");
+  if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
+  if (!dwf_is_device_ptr(force) || !dwf_is_device_ptr(X)) return dwf_fail(c, DWF_EINVAL, "device buffers required");
+  if (((uintptr_t)force & 15) || ((uintptr_t)X & 15)) return dwf_fail(c, DWF_EINVAL, "alignment");
+  return DWF_OK;
+}
+
 extern "C" int dwf_force(dwf_ctx* c, void* force, const void* X, const double* mf, int npf, int prec,
                          void* stream) {
   if (!c || !force || !X || !mf || npf < 1) return DWF_EINVAL;
-  if (npf > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "npf out of range");
-  if (prec != DWF_F64 && prec != DWF_F32) return dwf_fail(c, DWF_EINVAL, "bad precision");
-  if (!dwf_is_device_ptr(force) || !dwf_is_device_ptr(X)) return dwf_fail(c, DWF_EINVAL, "device buffers required");
+  int rc = force_args(c, force, X, npf, DWF_MAX_RHS, prec);
+  if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t he = c->g.Vh * 12 * c->g.Ls;
   const size_t bytes = (size_t)npf * he * dwf_complex_bytes(prec);
@@ -259,24 +312,92 @@ extern "C" int dwf_force(dwf_ctx* c, void* force, const void* X, const double* m
   if (!Xo || !Ye || !Yo) return dwf_fail(c, DWF_ENOMEM, "force workspace");
   // all pseudofermions at once, each with its own mass:
   // X_o = M_oo^-1 (-1/2 D_oe X_e) and Y_e = M_ee X_e + 1/2 D_eo X_o  (= M_pc X_e)
-  int rc = mpc_apply(c, Ye, X, Xo, mf, 0, prec, npf, 0, st, nullptr);
+  rc = mpc_apply(c, Ye, X, Xo, mf, 0, prec, npf, 0, st, nullptr);
   if (rc) return rc;
-  // Y_o = M_oo^-dag (-1/2 D^dag_oe Y_e)
-  HopLaunch h;
-  memset(&h, 0, sizeof(h));
-  h.out = Yo;
-  h.in = Ye;
-  h.out_parity = 1;
-  h.dagger = 1;
-  h.nrhs = npf;
-  h.alpha = -0.5;
-  h.inv_mode = 2;
-  h.mf = mf;
-  rc = launch_hop(c, h, prec, st, nullptr);
+  ForceCoef coef;
+  for (int f = 0; f < DWF_MAX_RHS; f++) coef.c[f] = 1.0;
+  return force_tail(c, force, X, Xo, true, Ye, Yo, mf, coef, npf, prec, st);
+}
+
+// Hasenbusch ratio factors S_r = phi^dag M2 (M1^dag M1)^-1 M2^dag phi: with
+// X = (M1^dag M1)^-1 M2^dag phi, dS_r = 2 Re phi^dag dM2 X - 2 Re (M1 X)^dag
+// dM1 X, so G_r = G(X', (M1 X)'; m1) - G(X', phi'; m2): two field pairs per
+// factor in one force launch, weights +1 and -1.
+extern "C" int dwf_ratio_force(dwf_ctx* c, void* force, const void* X, const void* phi, const double* m1,
+                               const double* m2, int nratio, int prec, void* stream) {
+  if (!c || !force || !X || !phi || !m1 || !m2 || nratio < 1) return DWF_EINVAL;
+  int rc = force_args(c, force, X, nratio, DWF_MAX_RHS / 2, prec);
   if (rc) return rc;
-  rc = prec == DWF_F64 ? launch_force<DWF_F64>(c, (double2*)force, X, Xo, Ye, Yo, npf, st)
-                       : launch_force<DWF_F32>(c, (double2*)force, X, Xo, Ye, Yo, npf, st);
+  if (!dwf_is_device_ptr(phi) || ((uintptr_t)phi & 15)) return dwf_fail(c, DWF_EINVAL, "phi: aligned device buffer");
+  for (int i = 0; i < nratio; i++)
+    if (!isfinite(m1[i]) || !isfinite(m2[i])) return dwf_fail(c, DWF_EINVAL, "masses must be finite");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = nratio;
+  const int64_t he = c->g.Vh * 12 * c->g.Ls;
+  const size_t fb = (size_t)he * dwf_complex_bytes(prec);
+  void* Xe = dwf_workspace(c, WS_FXE, 2 * n * fb);
+  void* Xo = dwf_workspace(c, WS_FXO, 2 * n * fb);
+  void* Ye = dwf_workspace(c, WS_FYE, 2 * n * fb);
+  void* Yo = dwf_workspace(c, WS_FYO, 2 * n * fb);
+  if (!Xe || !Xo || !Ye || !Yo) return dwf_fail(c, DWF_ENOMEM, "force workspace");
+  std::vector<double> mass(2 * n);
+  ForceCoef coef;
+  for (int f = 0; f < DWF_MAX_RHS; f++) coef.c[f] = 0.0;
+  for (int i = 0; i < n; i++) {
+    mass[i] = m1[i];
+    mass[n + i] = m2[i];
+    coef.c[i] = 1.0;
+    coef.c[n + i] = -1.0;
+  }
+  // pairs 0..n-1: (X, M1 X) at m1; pairs n..2n-1: (X, phi) at m2
+  DWF_CUDA(c, cudaMemcpyAsync(Xe, X, n * fb, cudaMemcpyDeviceToDevice, st));
+  DWF_CUDA(c, cudaMemcpyAsync((char*)Xe + n * fb, X, n * fb, cudaMemcpyDeviceToDevice, st));
+  DWF_CUDA(c, cudaMemcpyAsync((char*)Ye + n * fb, phi, n * fb, cudaMemcpyDeviceToDevice, st));
+  rc = mpc_apply(c, Ye, X, Xo, mass.data(), 0, prec, n, 0, st, nullptr);  // M1 X, and M_oo^-1 M_oe X at m1
   if (rc) return rc;
+  {  // M_oo^-1 M_oe X at m2
+    HopLaunch hx;
+    memset(&hx, 0, sizeof(hx));
+    hx.out = (char*)Xo + n * fb;
+    hx.in = X;
+    hx.out_parity = 1;
+    hx.nrhs = n;
+    hx.alpha = -0.5;
+    hx.inv_mode = 1;
+    hx.mf = mass.data() + n;
+    rc = launch_hop(c, hx, prec, st, nullptr);
+    if (rc) return rc;
+  }
+  return force_tail(c, force, Xe, Xo, true, Ye, Yo, mass.data(), coef, 2 * n, prec, st);
+}
+
+// S = sum_i [2 Re <phi_i, X_i> - |M_pc(mf_i) X_i|^2] (the variational
+// estimator of phi^dag (M^dag M)^-1 phi, error quadratic in the solve's).
+extern "C" int dwf_pf_action(dwf_ctx* c, double* S, const void* phi, const void* X, const double* mf, int npf,
+                             void* stream) {
+  if (!c || !S || !phi || !X || !mf || npf < 1) return DWF_EINVAL;
+  if (npf > DWF_MAX_RHS) return dwf_fail(c, DWF_EINVAL, "npf out of range");
+  if (!dwf_is_device_ptr(phi) || !dwf_is_device_ptr(X)) return dwf_fail(c, DWF_EINVAL, "device buffers required");
+  if (((uintptr_t)phi & 15) || ((uintptr_t)X & 15)) return dwf_fail(c, DWF_EINVAL, "alignment");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t he = c->g.Vh * 12 * c->g.Ls;
+  const size_t bytes = (size_t)npf * he * 16;
+  void* Xo = dwf_workspace(c, WS_FXO, bytes);
+  void* Y = dwf_workspace(c, WS_FYE, bytes);
+  if (!Xo || !Y) return dwf_fail(c, DWF_ENOMEM, "workspace");
+  int np = 0;
+  int rc = blas_cdot_partials(c, phi, X, npf * he, DWF_F64, st, &np);
+  if (rc) return rc;
+  rc = blas_finalize(c, np, 2, S_TMP0, st);
+  if (rc) return rc;
+  rc = mpc_apply(c, Y, X, Xo, mf, 0, DWF_F64, npf, 1, st, &np);  // |M X|^2 partials of every field
+  if (rc) return rc;
+  rc = blas_finalize(c, np, 1, S_TMP2, st);
+  if (rc) return rc;
+  rc = read_scalars(c, S_TMP0, 3, st);
+  if (rc) return rc;
+  *S = 2.0 * c->hscal[S_TMP0] - c->hscal[S_TMP2];
+  if (!isfinite(*S)) return dwf_fail(c, DWF_ENAN, "action is not finite");
   DWF_CUDA(c, cudaGetLastError());
   return DWF_OK;
 }

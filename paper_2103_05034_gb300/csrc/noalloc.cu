@@ -19,7 +19,10 @@
 //    return wrong sums.  Serialise them (one stream, or events).
 //  * the first call on a device looks up the device address of the scratch
 //    (cudaGetSymbolAddress, with that device current) and caches it; make that
-//    first call before any stream capture.
+//    first call before any stream capture.  The cached address belongs to the
+//    device's primary context: after cudaDeviceReset (or any other teardown of
+//    that context) in the same process, this entry point must not be used
+//    again on that device.
 #include <mutex>
 
 #include "dwf_internal.cuh"
@@ -118,7 +121,11 @@ extern "C" int dwf_norm2_noalloc(double* result, const void* a, int64_t n, int p
       k_noalloc_partial<DWF_F16S><<<nparts, NT, 0, st>>>((const __half2*)a, n, scratch);
       break;
   }
+  // a launch that failed (no kernel image, bad stream) would leave the last
+  // call's sum in the scratch: report it instead of returning a stale result
+  if (cudaGetLastError() != cudaSuccess) return DWF_ECUDA;
   k_noalloc_final<<<1, NT, 0, st>>>(nparts, scratch);
+  if (cudaGetLastError() != cudaSuccess) return DWF_ECUDA;
   if (cudaMemcpyAsync(result, scratch + DWF_NOALLOC_MAXPART, sizeof(double), cudaMemcpyDeviceToHost, st) !=
       cudaSuccess) {
     cudaGetLastError();

@@ -145,13 +145,25 @@ def dwf_cdot(ctx, a, b):
     return complex(r[0], r[1])
 
 
-def rbcg_solve(ctx, x, b, mf, tol, maxiter=100000, policy=_lib.SOLVE_MIXED_F32):
+def rbcg_solve(ctx, x, b, mf, tol, maxiter=100000, policy=_lib.SOLVE_MIXED_F32, noconv_ok=False):
     """Red-black CGNR solve of D_DW x = b (full FP64 fields, host or device).
-    Returns the solver statistics as a dict."""
+    Returns the solver statistics as a dict.  noconv_ok: a solve stopped by
+    maxiter (DWF_ENOCONV, x still written) returns its statistics instead of
+    raising."""
     st = SolveStats()
     code = lib().rbcg_solve(ctx.h, _ptr(x), _ptr(b), mf, tol, maxiter, policy, C.byref(st),
                             _stream())
-    check(code, ctx.h)
+    if not (noconv_ok and code == _lib.DWF_ENOCONV):
+        check(code, ctx.h)
+    return st.as_dict()
+
+
+def rbcg2_solve(ctx, x, b, mf, tol, maxiter=100000, policy=_lib.SOLVE_F64):
+    """Red-black CGNR with the second Schur form M_ee^-1 M_pc (Table 5);
+    arguments and result as rbcg_solve."""
+    st = SolveStats()
+    check(lib().rbcg2_solve(ctx.h, _ptr(x), _ptr(b), mf, tol, maxiter, policy, C.byref(st), _stream()),
+          ctx.h)
     return st.as_dict()
 
 
@@ -324,6 +336,27 @@ def dwf_force(ctx, force, X, masses):
     return force
 
 
+def dwf_ratio_force(ctx, force, X, phi, m1, m2):
+    """force += sum_i G_r,i of the Hasenbusch ratio factors phi_i^dag M2 (M1^dag
+    M1)^-1 M2^dag phi_i (X_i = (M1^dag M1)^-1 M2^dag phi_i; X and phi hold the
+    factors' even half fields back to back, same precision)."""
+    n = len(m1)
+    a = (C.c_double * n)(*[float(m) for m in m1])
+    b = (C.c_double * n)(*[float(m) for m in m2])
+    check(lib().dwf_ratio_force(ctx.h, _ptr(force), _ptr(X), _ptr(phi), a, b, n, _prec_of(X), _stream()),
+          ctx.h)
+    return force
+
+
+def dwf_pf_action(ctx, phi, X, masses):
+    """sum_i 2 Re <phi_i, X_i> - |M_pc(m_i) X_i|^2 (FP64 even half fields back to back)."""
+    n = len(masses)
+    m = (C.c_double * n)(*[float(v) for v in masses])
+    S = C.c_double()
+    check(lib().dwf_pf_action(ctx.h, C.byref(S), _ptr(phi), _ptr(X), m, n, _stream()), ctx.h)
+    return S.value
+
+
 def rbcg_normal_solve(ctx, x, phi, mf, tol, maxiter=100000, policy=_lib.SOLVE_MIXED_F32):
     """x = (M_pc^dag M_pc)^-1 phi on the even parity (FP64 device half fields)."""
     st = SolveStats()
@@ -359,6 +392,13 @@ def rbcg_normal_solve_batch(ctx, x, phi, masses, tol, maxiter=100000, policy=_li
     """x_i = (M_pc(m_i)^dag M_pc(m_i))^-1 phi_i for FP64 even half fields
     stored back to back on the device.  Returns one stats dict per rhs."""
     return _batch_solve(lib().rbcg_normal_solve_batch, ctx, x, phi, masses, tol, maxiter, policy)
+
+
+def dwf_measure_fma_peaks():
+    """(FP64, FP32) FMA rates of this GPU in TFLOP/s, measured by the library."""
+    a, b = C.c_double(), C.c_double()
+    check(lib().dwf_measure_fma_peaks(C.byref(a), C.byref(b), _stream()))
+    return a.value, b.value
 
 
 def dwf_autotune(ctx, prec=F32, reps=20):

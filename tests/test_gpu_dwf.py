@@ -149,6 +149,38 @@ def test_rbcg_solution_parity(policy):
     ctx.close()
 
 
+@pytest.mark.parametrize("policy", [SOLVE_F64, SOLVE_MIXED_F32])
+def test_rbcg2_second_schur_form_matches_oracle(policy):
+    """The second Schur form of Table 5 (M2 = M_ee^-1 M_pc, CGNR on M2^dag M2)
+    on the small FP64 workload: the GPU solution against the oracle's
+    rbcg2_solve, the true residual by the oracle, the FP64 iteration count
+    against the oracle's CG on the same operator, and (Table 5) more
+    iterations than the first form for the same residual."""
+    L, Ls, mf = (4, 4, 4, 4), 8, 0.01
+    U = synth.random_gauge(L, 0.3, synth.SEED_GAUGE)
+    b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE)
+    ctx = ops.Context(L, Ls, M5, U)
+    tol = 1e-10
+    bd = full_dev(b, L, F64)
+    x = torch.zeros_like(bd)
+    st = ops.rbcg2_solve(ctx, x, bd, mf, tol, 20000, policy)
+    xg = dev_to_full_canon(x, L, Ls)
+    res = krylov.true_residual(U, xg, b, M5, mf)
+    assert res <= tol * 1.01, st
+    assert st["true_residual"] == pytest.approx(res, rel=1e-3, abs=1e-14)
+    xr, _, _ = krylov.rbcg2_solve(U, b, M5, mf, 1e-13)
+    assert rel(xg, xr) < 1e-7
+    x1 = torch.zeros_like(bd)
+    st1 = ops.rbcg_solve(ctx, x1, bd, mf, tol, 20000, policy)
+    assert st["iterations"] >= st1["iterations"]
+    if policy == SOLVE_F64:
+        # the oracle's CG stops on its recursive normal residual; run it to the
+        # GPU's final true residual and compare counts
+        _, it2, hist = krylov.rbcg2_solve(U, b, M5, mf, 1e-10)
+        assert abs(st["iterations"] - it2) <= 0.1 * it2 + 8
+    ctx.close()
+
+
 @pytest.mark.parametrize("Ls,mf", [(4, 0.05), (8, 0.01)])
 def test_rbcg_mixed_reaches_tight_tolerance(Ls, mf):
     """A gauge field (4^4, eps 0.3, seed 43) on which the FP32-inner CG,
@@ -248,6 +280,21 @@ def test_power_method(case):
     got = ops.dwf_power_max(ctx, full_dev(v0, L, F64), mf, 30)
     want = krylov.power_max(lambda v: dwf.mdagm(U, v, M5, mf), v0, 30)
     assert got == pytest.approx(want, rel=1e-10)
+
+
+def test_power_method_f32(case):
+    """The FP32 power method (the option the multigrid setup uses to bound
+    its filter interval) against the FP64 oracle's iteration from the same
+    start: the power iteration contracts towards the top eigenvector, so the
+    FP32 roundings of each step (relative 1e-7) do not accumulate, and the
+    Rayleigh quotient is accurate to the FP32 operator bound."""
+    L, Ls, U, ctx = case
+    mf = 0.05
+    v0 = synth.gaussian_spinor(L, Ls, 17)
+    got = ops.dwf_power_max(ctx, full_dev(v0, L, F64), mf, 30, F32)
+    want = krylov.power_max(lambda v: dwf.mdagm(U, v, M5, mf), v0, 30)
+    print(f"power method F32: rel err {abs(got - want) / want:.3e}")
+    assert got == pytest.approx(want, rel=1e-6)
 
 
 @pytest.mark.parametrize("prec", [F32, F16S])

@@ -40,7 +40,7 @@ def small():
     ctx.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(F64, 1e-11), (F32, 2e-5)])
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-11), (F32, 1e-5)])
 def test_cheby_filter_batched(small, prec, tol):
     L, Ls, mf, U, ctx, lmax = small
     vs = [synth.gaussian_spinor(L, Ls, 50 + i) for i in range(3)]
@@ -51,10 +51,12 @@ def test_cheby_filter_batched(small, prec, tol):
     got = fulls_canon(out, L, Ls, 3)
     appA = lambda v: dwf.mdagm(U, v, M5, mf)
     for g, v in zip(got, vs):
-        assert rel(g, cheby.cheby_filter(appA, v, order, lo, lmax)) < tol
+        err = rel(g, cheby.cheby_filter(appA, v, order, lo, lmax))
+        print(f"cheby_filter prec={prec} order={order}: rel err {err:.3e}")
+        assert err < tol
 
 
-@pytest.mark.parametrize("prec,tol", [(F64, 1e-10), (F32, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-10), (F32, 1e-5)])
 def test_recursive_basis(small, prec, tol):
     L, Ls, mf, U, ctx, lmax = small
     eta = synth.gaussian_spinor(L, Ls, 60)
@@ -65,7 +67,9 @@ def test_recursive_basis(small, prec, tol):
     got = fulls_canon(phi, L, Ls, nvec)
     want = cheby.recursive_basis(lambda v: dwf.mdagm(U, v, M5, mf), eta, m, delta, nvec, lo, lmax)
     for g, w in zip(got, want):
-        assert rel(g, w) < tol
+        err = rel(g, w)
+        print(f"recursive_basis prec={prec}: rel err {err:.3e}")
+        assert err < tol
 
 
 def test_chiral_projection(small):
@@ -117,12 +121,14 @@ def coarse_case(request):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(F64, 1e-12), (F32, 2e-6)])
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-12), (F32, 1e-6)])
 def test_coarse_build(coarse_case, prec, tol):
     L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
     C = ops.coarse_build(ctx, fulls_dev(basis, L, prec), nb, nb // 2, block, mf)
     got = C.export()
-    assert rel(got, Aflat) < tol
+    err = rel(got, Aflat)
+    print(f"coarse_build prec={prec}: rel err {err:.3e}")
+    assert err < tol
     C.close()
 
 
@@ -355,3 +361,103 @@ def test_coarse_apply_tensor_cores_rejects_unsupported_shapes(coarse_case):
     with pytest.raises(DWFError):  # nb != 32 here
         ops.coarse_apply(C, v.clone(), v, 32, prec=TF32)
     C.close()
+
+
+# ---------------------------------------------------------------- the benchmarked shapes
+def _ortho_basis_oracle(L, Ls, block, nb, seed):
+    """Chirality-projected Gaussians orthonormalised per (block, chirality) by
+    the oracle (MGS2): the same FP64 basis goes to both sides."""
+    vecs = [coarse.chiral_project(synth.gaussian_spinor(L, Ls, seed + i), 1 if i < nb // 2 else -1)
+            for i in range(nb)]
+    return coarse.block_orthonormalise(vecs, block, [list(range(nb // 2)), list(range(nb // 2, nb))])
+
+
+@pytest.mark.parametrize("Ls,nb", [(16, 32), (24, 8), (8, 8)])
+@pytest.mark.parametrize("prec,tol", [(F64, 1e-12), (F32, 1e-6)])
+def test_coarse_build_at_benchmark_ls(Ls, nb, prec, tol):
+    """The face-split hopping kernels k_face_hop<P, Ls> at Ls = 8, 16, 24 and
+    the 32-vector build (the benchmark's multigrid shape) against the oracle's
+    9-point stencil; the F32 bound is c12's FP32 operator bound (FP32 basis and
+    hops, FP64 block sums)."""
+    L, block, mf = (4, 4, 4, 4), (2, 2, 2, 2), 0.1
+    U = synth.random_gauge(L, 0.5, 45)
+    ctx = ops.Context(L, Ls, M5, U)
+    basis = _ortho_basis_oracle(L, Ls, block, nb, 400)
+    A = coarse.coarse_build(U, basis, block, M5, mf)
+    Aflat = np.moveaxis(A.reshape(9, -1, nb, nb), 0, 1)
+    C = ops.coarse_build(ctx, fulls_dev(basis, L, prec), nb, nb // 2, block, mf)
+    err = rel(C.export(), Aflat)
+    print(f"coarse_build Ls={Ls} nb={nb} prec={prec}: rel err {err:.3e}")
+    assert err < tol
+    C.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("nb", [32, 64])
+def test_coarse_solve_fixed_width_kernels(nb):
+    """The persistent coarse CG with the basis width fixed at compile time
+    (k_coarse_cg<32>, which the benchmark's multigrid runs, and <64>): 8^4 x
+    Ls 4 with 2^4 blocks gives 256 coarse sites, each CTA owning many rows.
+    Same checks as test_coarse_solve: the normal residual bound, the oracle's
+    iteration count for the same rule on the same (exported) operator, and
+    the exact solution."""
+    L, Ls, block, mf = (8, 8, 8, 8), 4, (2, 2, 2, 2), 0.1
+    U = synth.random_gauge(L, 0.5, 46)
+    ctx = ops.Context(L, Ls, M5, U)
+    # the basis (an input of the coarse solve) is built on the GPU: Gaussians
+    # filtered towards the low modes of D^dag D, chirality-projected and
+    # block-orthonormalised, so that the coarse operator is ill-conditioned
+    # enough for the CG to take many iterations
+    g = fulls_dev([synth.gaussian_spinor(L, Ls, 500 + i) for i in range(nb)], L, F64)
+    d = torch.zeros_like(g)
+    ops.cheby_filter(ctx, d, g, nb, 0.5, 70.0, 8, mf)
+    half = d.numel() // 2
+    ops.dwf_chiral_project(ctx, d[:half], d[:half], 1, nb // 2)
+    ops.dwf_chiral_project(ctx, d[half:], d[half:], -1, nb // 2)
+    ops.block_orthonormalise(ctx, d, nb, nb // 2, block)
+    C = ops.coarse_build(ctx, d, nb, nb // 2, block, mf)
+    Ast = np.moveaxis(C.export(), 1, 0).reshape((9,) + tuple(C.Lc[::-1]) + (nb, nb))
+    r = synth.complex_gaussian(8, (C.nc, nb))
+    rd = torch.from_numpy(layout.complex_to_real(r, F32).reshape(-1)).cuda()
+    e = torch.zeros_like(rd)
+    tol = 1e-5
+    it = ops.coarse_solve(C, e, rd, tol, 5000)
+    eg = layout.real_to_complex(e.double().cpu().numpy()).reshape(r.shape)
+    Ar = coarse.coarse_apply(Ast, r.reshape(tuple(C.Lc[::-1]) + (nb,)))
+    AAe = coarse.coarse_apply(Ast, coarse.coarse_apply(Ast, eg.reshape(Ar.shape)))
+    assert np.linalg.norm(AAe - Ar) <= 2 * tol * np.linalg.norm(Ar)
+    e_or, it_or = coarse.coarse_cgnr(Ast, r.reshape(Ar.shape), tol, 5000)
+    print(f"coarse_solve nb={nb}: {it} iterations (oracle {it_or})")
+    assert abs(it - it_or) <= max(4, it_or // 20)
+    # the exact solution, from the oracle's CG run far past the tolerance (a
+    # dense solve of 256 x nb unknowns is too large here)
+    want, _ = coarse.coarse_cgnr(Ast, r.reshape(Ar.shape), 1e-12, 50000)
+    assert rel(eg.ravel(), want.ravel()) < 10 * rel(e_or.ravel(), want.ravel()) + 1e-5
+    C.close()
+    ctx.close()
+
+
+def test_mg_solve_at_ls16():
+    """The whole HDCR solve at Ls = 16 (the benchmark's fifth-dimension
+    extent; every other multigrid test runs Ls = 4): FP64 true residual and
+    the oracle's red-black solution."""
+    L, Ls, mf = (4, 4, 4, 4), 16, 0.05
+    block, nb = (2, 2, 2, 2), 8
+    U = synth.random_gauge(L, 0.5, 52)
+    ctx = ops.Context(L, Ls, M5, U)
+    etas = [synth.gaussian_spinor(L, Ls, 700 + i) for i in range(nb)]
+    p = ops.mg_params(block, nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=0.5, lambda_max=70.0,
+                      filter_order=4, smooth=(0.5, 60.0, 6), coarse_tol=0.02, coarse_maxiter=500,
+                      nkrylov=8, maxiter=300)
+    G = ops.MG(ctx, p, fulls_dev(etas, L, F64))
+    b = synth.gaussian_spinor(L, Ls, 74)
+    bd = full_dev(b, L, F64)
+    xd = torch.zeros_like(bd)
+    st = ops.mg_solve(G, xd, bd, 1e-8)
+    x = dev_to_full_canon(xd, L, Ls)
+    res = krylov.true_residual(U, x, b, M5, mf)
+    assert res <= 1e-8 * 1.01, st
+    xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert rel(x, xr) < 1e-6
+    G.close()
+    ctx.close()

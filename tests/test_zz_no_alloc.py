@@ -15,7 +15,7 @@ import torch
 
 import synth
 from paper_2103_05034_gb300 import _lib, layout, ops
-from paper_2103_05034_gb300._lib import DWF_EINVAL, F32, F64
+from paper_2103_05034_gb300._lib import DWF_EINVAL, F16S, F32, F64
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +27,7 @@ def _call(a, n, prec):
     return code, r.value
 
 
-@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("prec", [F64, F32, F16S])
 def test_noalloc_norm2_matches_allocating_entry_point(prec):
     L, Ls = (4, 4, 4, 8), 8
     ctx = ops.Context(L, Ls, 1.8, synth.random_gauge(L, 0.3, 3))
@@ -35,9 +35,10 @@ def test_noalloc_norm2_matches_allocating_entry_point(prec):
         layout.to_full(synth.gaussian_spinor(L, Ls, 91), L), prec).reshape(-1)).cuda()
     small = big[: big.numel() // 3 // 2 * 2].clone()
     # FP64 data: both sum the squares in FP64, in different orders.  FP32
-    # data: the allocating reduction accumulates each thread's share in
-    # compensated FP32 (a few ulp of FP32, 1e-7 relative at most) and the
-    # allocation-free one in FP64.
+    # and FP16-storage data (the same half values read by both): the
+    # allocating reduction accumulates each thread's share in compensated
+    # FP32 (a few ulp of FP32, 1e-7 relative at most) and the allocation-free
+    # one in FP64.
     tol = 1e-12 if prec == F64 else 1e-6
     for a in (big, small):  # two calls in a row; the second sees the first's scratch contents
         n = a.numel() // 2
