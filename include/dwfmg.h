@@ -418,6 +418,42 @@ int coarse_apply_status(dwf_coarse* coarse, void* stream);
  * initial value or after maxiter iterations (*iters receives the count). */
 int coarse_solve(dwf_coarse* coarse, void* e, const void* r, double tol, int maxiter, int* iters,
                  void* stream);
+/* Red-black coarse solve (Sec. 5.3: the red-black coarse solver of the
+ * physical-point runs): with even coarse extents the 9-point stencil couples
+ * a coarse site only to itself and to the other coarse parity, so A e = r is
+ * solved by CG on S^2 e_e = S r'_e with the even Schur complement
+ * S = A_ee - A_eo A_oo^-1 A_oe (hermitian; A_oo^-1 = the nb x nb self-block
+ * inverses), r'_e = r_e - A_eo A_oo^-1 r_o, then e_o = A_oo^-1 (r_o - A_oe
+ * e_e).  Stops when |S^2 e_e - S r'_e| <= tol |S r'_e| or after maxiter
+ * iterations (*iters).  Parity of a coarse site: (xc + yc + zc + tc) mod 2.
+ * The first call inverts the odd self blocks in FP64 (Gauss-Jordan with
+ * partial pivoting) and keeps A_oo^-1 and A_oo^-1 A_oe with the operator
+ * (FP32, the size of the operator).  FP32 vectors [nc][nb].  DWF_EINVAL for
+ * odd coarse extents or nb > 64, DWF_ERANGE for a singular self block.
+ * Synchronises. */
+int coarse_solve_rb(dwf_coarse* coarse, void* e, const void* r, double tol, int maxiter, int* iters,
+                    void* stream);
+/* Coarse-space deflation (Sec. 3.5: eigenvector deflation of the coarse
+ * operator with Chebyshev-polynomial-preconditioned Lanczos).  Lanczos with
+ * full reorthogonalisation runs nk steps on B = T_order(y(A^2)),
+ * y(t) = 2 (t - lam_lo) / (lam_max - lam_lo) - 1 (order even, >= 2), from the
+ * caller's start vector v0 (FP32 coarse vector [nc][nb], device); the nev
+ * Ritz vectors of B's largest Ritz values are then diagonalised with A^2
+ * (Rayleigh-Ritz), giving pairs (theta_i, v_i), theta ascending, written to
+ * theta (host, may be NULL).  lam_max <= 0: a 30-step power method on A^2
+ * (+10 %) sets it.  The operator keeps the v_i (nev FP32 coarse vectors) and
+ * from then on coarse_solve -- and the multigrid's plain coarse CG -- start
+ * from x0 = sum_i v_i <v_i, A r> / theta_i, with the stopping rule still
+ * relative to the residual of the zero start.  nev = 0 drops the space.
+ * Needs 1 <= nev <= nk <= min(1024, nc nb); DWF_EINVAL otherwise,
+ * DWF_ERANGE if the Krylov space closes before nev vectors or a Ritz value
+ * is not positive.  Small dense eigenproblems on the host (Jacobi).
+ * Synchronises. */
+int coarse_deflate(dwf_coarse* coarse, const void* v0, int nev, int nk, int order, double lam_lo,
+                   double lam_max, double* theta, void* stream);
+/* The deflation space of coarse_deflate: *nev vectors (FP32 [nev][nc][nb],
+ * copied to V, host or device, when V is not NULL) and 1/theta_i (host). */
+int coarse_export_deflation(const dwf_coarse* coarse, void* V, double* theta_inv, int* nev);
 /* Restriction P^dag (out: FP32 coarse [nc][nb][nrhs]) and prolongation P
  * (out: nrhs full fields, += when accumulate) with a block basis of nb full
  * fields of precision prec (DWF_F64 or DWF_F32). */
@@ -450,7 +486,21 @@ typedef struct dwf_mg_params {
   int maxiter;           /* outer iterations */
   int no_graph;          /* 0: mg_solve captures the V-cycle in a CUDA graph
                             once per solve and replays it; 1: plain launches */
+  int coarse_solver;     /* DWF_COARSE_CG: CG on A^2 (Table 1); DWF_COARSE_RB:
+                            red-black CG on S^2 (coarse_solve_rb, Sec. 5.3);
+                            DWF_COARSE_DEFLATED: CG on A^2 started from the
+                            deflation guess (coarse_deflate, Sec. 3.5), the
+                            space built by mg_setup from the restriction of the
+                            first eta */
+  int coarse_nev;        /* deflation: Ritz vectors kept */
+  int coarse_lanczos;    /* deflation: Lanczos steps */
+  int coarse_cheb_order; /* deflation: even Chebyshev order of the Lanczos operator */
+  double coarse_cheb_lo; /* deflation: modes of A^2 below this are enhanced */
 } dwf_mg_params;
+
+#define DWF_COARSE_CG 0
+#define DWF_COARSE_RB 1
+#define DWF_COARSE_DEFLATED 2
 
 /* Build the multigrid setup: filtered vectors from eta (nbasis FP64 full fields
  * in batch mode, one in recursive mode; device memory), chirality projection

@@ -35,6 +35,7 @@ class SolveStats(C.Structure):
 
 
 SUBSPACE_BATCH, SUBSPACE_RECURSIVE = 0, 1
+COARSE_CG, COARSE_RB, COARSE_DEFLATED = 0, 1, 2
 
 
 class MGParams(C.Structure):
@@ -43,7 +44,8 @@ class MGParams(C.Structure):
                 ("filter_order", C.c_int), ("delta", C.c_int), ("smooth_lo", C.c_double),
                 ("smooth_hi", C.c_double), ("smooth_order", C.c_int), ("coarse_tol", C.c_double),
                 ("coarse_maxiter", C.c_int), ("nkrylov", C.c_int), ("maxiter", C.c_int),
-                ("no_graph", C.c_int)]
+                ("no_graph", C.c_int), ("coarse_solver", C.c_int), ("coarse_nev", C.c_int),
+                ("coarse_lanczos", C.c_int), ("coarse_cheb_order", C.c_int), ("coarse_cheb_lo", C.c_double)]
 
 
 def header_functions():
@@ -129,6 +131,9 @@ _SIGS = {
     "coarse_apply": (I, [P, P, P, I, I, P]),
     "coarse_apply_status": (I, [P, P]),
     "coarse_solve": (I, [P, P, P, D, I, C.POINTER(C.c_int), P]),
+    "coarse_solve_rb": (I, [P, P, P, D, I, C.POINTER(C.c_int), P]),
+    "coarse_deflate": (I, [P, P, I, I, I, D, D, C.POINTER(D), P]),
+    "coarse_export_deflation": (I, [P, P, C.POINTER(D), C.POINTER(C.c_int)]),
     "dwf_restrict": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, P]),
     "dwf_prolong": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, I, P]),
     "mg_setup": (I, [P, C.POINTER(MGParams), P, C.POINTER(P), P]),

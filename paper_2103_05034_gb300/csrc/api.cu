@@ -220,13 +220,15 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
   {
     // z-chunk: the largest even divisor of Lz whose input slab (zc planes of
     // one time slice, over the t-1, t, t+1 slices plus the output) stays
-    // within ~48 MB of L2; the whole Lz (lexicographic order) when it fits.
+    // within the L2 budget (48 MB unless the autotuner chose another); the
+    // whole Lz (lexicographic order) when it fits.
+    const double budget = c->hop_l2_budget[prec] > 0 ? c->hop_l2_budget[prec] : 48e6;
     const double plane = (double)c->g.L[1] * c->g.Lxh * c->g.Ls * h.nrhs * 12.0 * dwf_complex_bytes(prec);
     int zc = c->g.L[2];
-    if (4.0 * plane * zc > 48e6) {
+    if (4.0 * plane * zc > budget) {
       zc = 2;
       for (int q = 2; q <= c->g.L[2]; q += 2)
-        if (c->g.L[2] % q == 0 && 4.0 * plane * q <= 48e6) zc = q;
+        if (c->g.L[2] % q == 0 && 4.0 * plane * q <= budget) zc = q;
     }
     hp.zc = zc;
   }
@@ -339,9 +341,35 @@ extern "C" int dwf_autotune(dwf_ctx* c, int prec, int reps, double* best_ms, voi
       best = v;
     }
   }
+  // then the L2 budget of the z-chunked traversal for the chosen variant
+  c->hop_variant[prec] = best;
+  const double budgets[5] = {48e6, 16e6, 32e6, 80e6, 120e6};
+  double best_budget = 48e6;
+  for (int bi = 1; bi < 5 && nv > 1; bi++) {
+    c->hop_l2_budget[prec] = budgets[bi];
+    HopLaunch h;
+    memset(&h, 0, sizeof(h));
+    h.out = b;
+    h.in = a;
+    h.nrhs = 1;
+    h.alpha = 1.0;
+    int rc = launch_hop(c, h, prec, st, nullptr);
+    if (rc) return rc;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; r++) launch_hop(c, h, prec, st, nullptr);
+    cudaEventRecord(e1, st);
+    DWF_CUDA(c, cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < 0.98f * best_t) {  // a clear gain over the default
+      best_t = ms;
+      best_budget = budgets[bi];
+    }
+  }
+  c->hop_l2_budget[prec] = best_budget;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->hop_variant[prec] = best;
   c->launches = launches0;  // tuning launches are not counted
   c->hop_bytes = bytes0;
   // the two tuning fields are released (at 48^3 x 96 x 24 they are 24 GB)

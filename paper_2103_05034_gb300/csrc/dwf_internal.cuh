@@ -126,6 +126,7 @@ struct dwf_ctx {
   double* dscal;      // device scalars for solvers
   double* hscal;      // pinned host mirror
   int hop_variant[3]; // tuned hopping-kernel variant per precision
+  double hop_l2_budget[3];  // L2 bytes the z-chunked traversal plans for (0: 48 MB)
   int64_t launches;   // kernel launches since the last counter reset
   double hop_bytes;   // algorithmic bytes of hopping-term launches
   std::string err;
@@ -142,6 +143,7 @@ int dwf_cuda_check(dwf_ctx* c, cudaError_t e, const char* where);
 
 size_t dwf_complex_bytes(int prec);
 void* dwf_workspace(dwf_ctx* c, int slot, size_t bytes);
+void dwf_ws_release(dwf_ctx* c, int slot);  // free one workspace slot (mg.cu)
 bool dwf_is_device_ptr(const void* p);
 
 // ------------------------------------------------------------------ launchers

@@ -9,33 +9,7 @@
 #include <new>
 #include <vector>
 
-#include "mg_kernels.cuh"
-
-using dwfmg::BlockGeom;
-
-struct dwf_coarse {
-  dwf_ctx* ctx;
-  BlockGeom g;
-  int nb, nplus;
-  double2* A64;  // [nc][9][nb][nb]
-  float2* A32;   // same layout, FP32
-  float* At;     // tensor-core copy (real form, TF32, K-major), built on first use
-  float* Bt;     // tensor-core right-hand sides (real form, TF32), per apply
-  size_t Bt_bytes;
-  int* err;      // device error flag of the tensor-core kernel (sticky)
-  int* err_host; // pinned mirror, copied after every tensor-core apply
-  cudaEvent_t err_ready;  // recorded after that copy
-  void* ws[6];
-  size_t ws_bytes[6];
-  int* cg_acc;   // when set: coarse CG runs without host synchronisation and
-                 // accumulates [iterations, error] here (graph capture)
-};
-
-int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, float** Bt,
-                    size_t* Bt_bytes, int nb, int nc, const int Lc[4], int nrhs, int* err_dev, cudaStream_t st);
-int coarse_cg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float2* A, const int Lc[4], int nc,
-                         int nb, double tol, int maxiter, float2* work, double* part, int part_cap,
-                         int* dev_small, int* acc, int* iters, cudaStream_t st);
+#include "coarse_internal.cuh"
 
 struct dwf_mg {
   dwf_ctx* ctx;
@@ -229,6 +203,58 @@ int block_combine(dwf_ctx* c, const BlockGeom& g, void* Y, int ny, int py, const
   return DWF_OK;
 }
 
+}  // namespace
+
+void dwf_ws_release(dwf_ctx* c, int slot) {
+  if (slot < 0 || slot >= DWF_NWS || !c->ws[slot]) return;
+  cudaFree(c->ws[slot]);
+  c->ws[slot] = nullptr;
+  c->ws_bytes[slot] = 0;
+}
+
+namespace {
+
+// Block Cholesky-QR on nb FP32 full fields in place (FP64 Gram matrices,
+// factorisation and update arithmetic): the basis orthonormalisation of the
+// multigrid setup without an FP64 copy of the basis.  Three passes, the first
+// with the Gram matrix shifted by 1e-5 of its largest diagonal entry (shifted
+// Cholesky-QR: the filtered vectors can be dependent to FP32 precision on a
+// block, and a plain Cholesky factorisation of their Gram matrix then fails);
+// the first pass brings the condition number to about 300, the next two
+// orthonormalise.  Every pass multiplies by an upper-triangular matrix with a
+// positive diagonal, so the result is the Q of the QR factorisation (the same
+// vectors as Gram-Schmidt in exact arithmetic).
+int ortho_inplace_f32(dwf_ctx* c, const BlockGeom& g, float2* basis, int nb, int nplus, cudaStream_t st) {
+  const int64_t n = full_elems(c);
+  const size_t gbytes = (size_t)g.nc * nb * nb * sizeof(double2);
+  double2* Gm = (double2*)ws(c, MW_T8, gbytes);
+  double2* Ri = (double2*)ws(c, MW_T9, gbytes);
+  int* fail = (int*)ws(c, MW_T11, sizeof(int) * 4);
+  if (!Gm || !Ri || !fail) return dwf_fail(c, DWF_ENOMEM, "orthonormalisation workspace");
+  for (int pass = 0; pass < 3; pass++) {
+    int rc = block_inner(c, g, basis, nb, basis, nb, DWF_F32, Gm, (long long)nb * nb, nb, 0, 0, st);
+    if (rc) return rc;
+    DWF_CUDA(c, cudaMemsetAsync(Ri, 0, gbytes, st));
+    DWF_CUDA(c, cudaMemsetAsync(fail, 0, sizeof(int), st));
+    c->launches++;
+    dwfmg::k_block_cholinv<<<dim3(g.nc, 2), 32, 0, st>>>(Gm, Ri, nb, nplus, fail, pass == 0 ? 1e-5 : 0.0);
+    for (int grp = 0; grp < 2; grp++) {
+      const int g0 = grp ? nplus : 0, ng = grp ? nb - nplus : nplus;
+      if (ng <= 0) continue;
+      c->launches++;
+      dwfmg::k_block_update_inplace<<<g.nc, 256, 0, st>>>(basis + (size_t)g0 * n, n, ng, g0, nb, Ri, g);
+    }
+    int hfail = 0;
+    DWF_CUDA(c, cudaMemcpyAsync(&hfail, fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DWF_CUDA(c, cudaStreamSynchronize(st));
+    if (hfail) return dwf_fail(c, DWF_ERANGE, "basis vectors linearly dependent on a block");
+  }
+  DWF_CUDA(c, cudaGetLastError());
+  return DWF_OK;
+}
+
+}  // namespace
+
 int coarse_ws(dwf_coarse* C, int slot, size_t bytes, void** out) {
   if (C->ws_bytes[slot] < bytes || !C->ws[slot]) {
     if (C->ws[slot]) cudaFree(C->ws[slot]);
@@ -257,6 +283,8 @@ int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cud
   return DWF_OK;
 }
 
+namespace {
+
 // CG on A^2 e = A r (one right-hand side, FP32 vectors), stopping when the
 // normal-equation residual falls below tol times its initial value: one
 // persistent cooperative launch (coarse_cg.cu).
@@ -268,8 +296,51 @@ int coarse_cg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxite
   if ((rc2 = coarse_ws(C, 0, 4 * n * sizeof(float2), &work)) || (rc2 = coarse_ws(C, 1, part_cap * sizeof(double), &part)) ||
       (rc2 = coarse_ws(C, 2, CG_SMALL_BYTES, &small)))
     return rc2;
+  // with a deflation space the CG starts from its guess (coarse_deflate)
+  const float2* x0 = nullptr;
+  if (C->defl_nev > 0) {
+    rc2 = coarse_defl_guess(C, rc, st);
+    if (rc2) return rc2;
+    x0 = C->defl_tmp + n;
+  }
   return coarse_cg_persistent(C->ctx, e, rc, C->A32, C->g.Lc, C->g.nc, C->nb, tol, maxiter, (float2*)work,
-                              (double*)part, part_cap, (int*)small, C->cg_acc, iters, st);
+                              (double*)part, part_cap, (int*)small, C->cg_acc, iters, st, x0);
+}
+
+// The red-black form of the operator, built once (synchronises when it is built).
+int coarse_rb_ready(dwf_coarse* C, cudaStream_t st) {
+  if (C->Arb) return DWF_OK;
+  for (int m = 0; m < 4; m++)
+    if (C->g.Lc[m] & 1) return dwf_fail(C->ctx, DWF_EINVAL, "red-black coarse solve needs even coarse extents");
+  const size_t na = (size_t)C->g.nc * 9 * C->nb * C->nb;
+  void* small;
+  int rc = coarse_ws(C, 2, CG_SMALL_BYTES, &small);
+  if (rc) return rc;
+  if (cudaMalloc(&C->Arb, na * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    C->Arb = nullptr;
+    return dwf_fail(C->ctx, DWF_ENOMEM, "red-black coarse operator");
+  }
+  rc = coarse_rb_prepare(C->ctx, C->A64, C->Arb, C->g.Lc, C->g.nc, C->nb, (int*)small, st);
+  if (rc) {
+    cudaFree(C->Arb);
+    C->Arb = nullptr;
+  }
+  return rc;
+}
+
+// Red-black CG on S^2 (coarse_cg.cu): same contract as coarse_cg.
+int coarse_rbcg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxiter, int* iters, cudaStream_t st) {
+  int r = coarse_rb_ready(C, st);
+  if (r) return r;
+  const int64_t n = (int64_t)C->g.nc * C->nb;
+  const int part_cap = 3 * 4096;
+  void *work, *part, *small;
+  if ((r = coarse_ws(C, 3, 7 * n * sizeof(float2), &work)) || (r = coarse_ws(C, 1, part_cap * sizeof(double), &part)) ||
+      (r = coarse_ws(C, 2, CG_SMALL_BYTES, &small)))
+    return r;
+  return coarse_rbcg_persistent(C->ctx, e, rc, C->Arb, C->g.Lc, C->g.nc, C->nb, tol, maxiter, (float2*)work,
+                                (double*)part, part_cap, (int*)small, C->cg_acc, iters, st);
 }
 
 }  // namespace
@@ -414,48 +485,56 @@ extern "C" int coarse_build(dwf_ctx* c, const void* basis, int nb, int nplus, co
     coarse_destroy(C);
     return dwf_fail(c, DWF_ENOMEM, "coarse operator");
   }
+  // H_DW phi_k and its eight face terms for a group of at most eight basis
+  // vectors at a time (bounded workspace: two groups of full fields); the
+  // block inner products with every basis vector fill those columns of A.
   const int64_t n = full_elems(c);
-  const size_t fb = (size_t)n * nb * dwf_complex_bytes(prec);
+  const int ngmax = nb < 8 ? nb : 8;
+  const size_t cbytes = dwf_complex_bytes(prec);
+  const size_t fb = (size_t)n * ngmax * cbytes;
   void* H = ws(c, MW_T8, fb);
   void* W = ws(c, MW_T9, fb);
   if (!H || !W) {
     coarse_destroy(C);
     return dwf_fail(c, DWF_ENOMEM, "coarse build workspace");
   }
-  std::vector<double> m(nb, mf);
-  // H_DW phi_k for all k; the eight face terms are split off one direction at a time
-  rc = ddw_apply(c, H, basis, m.data(), 0, 1, prec, nb, st);
   const long long bstride = 9LL * nb * nb;
-  for (int d = 1; d <= 8 && rc == DWF_OK; d++) {
-    const unsigned nblk = (unsigned)((2LL * g.Vh * g.Ls + 127) / 128);
-    dim3 grid(nblk, nb);
-    c->launches++;
+  for (int k0 = 0; k0 < nb && rc == DWF_OK; k0 += ngmax) {
+    const int ng = nb - k0 < ngmax ? nb - k0 : ngmax;
+    const void* bk = (const char*)basis + (size_t)k0 * n * cbytes;
+    std::vector<double> m(ng, mf);
+    rc = ddw_apply(c, H, bk, m.data(), 0, 1, prec, ng, st);
+    for (int d = 1; d <= 8 && rc == DWF_OK; d++) {
+      const unsigned nblk = (unsigned)((2LL * g.Vh * g.Ls + 127) / 128);
+      dim3 grid(nblk, ng);
+      c->launches++;
 #define DWF_FACE(PV, LSV)                                                                                  \
   dwfmg::k_face_hop<PV, LSV><<<grid, 128, 0, st>>>((typename Prec<PV>::S*)W,                                \
-                                                    (const typename Prec<PV>::S*)basis, n,                 \
+                                                    (const typename Prec<PV>::S*)bk, n,                    \
                                                     (const typename Prec<PV>::LS*)(PV == DWF_F64 ? (void*)c->links64[0] : (void*)c->links32[0]), \
                                                     (const typename Prec<PV>::LS*)(PV == DWF_F64 ? (void*)c->links64[1] : (void*)c->links32[1]), g, d)
-    if (prec == DWF_F64) {
-      switch (g.Ls) {
-        case 4: DWF_FACE(DWF_F64, 4); break;
-        case 8: DWF_FACE(DWF_F64, 8); break;
-        case 16: DWF_FACE(DWF_F64, 16); break;
-        default: DWF_FACE(DWF_F64, 24); break;
+      if (prec == DWF_F64) {
+        switch (g.Ls) {
+          case 4: DWF_FACE(DWF_F64, 4); break;
+          case 8: DWF_FACE(DWF_F64, 8); break;
+          case 16: DWF_FACE(DWF_F64, 16); break;
+          default: DWF_FACE(DWF_F64, 24); break;
+        }
+      } else {
+        switch (g.Ls) {
+          case 4: DWF_FACE(DWF_F32, 4); break;
+          case 8: DWF_FACE(DWF_F32, 8); break;
+          case 16: DWF_FACE(DWF_F32, 16); break;
+          default: DWF_FACE(DWF_F32, 24); break;
+        }
       }
-    } else {
-      switch (g.Ls) {
-        case 4: DWF_FACE(DWF_F32, 4); break;
-        case 8: DWF_FACE(DWF_F32, 8); break;
-        case 16: DWF_FACE(DWF_F32, 16); break;
-        default: DWF_FACE(DWF_F32, 24); break;
-      }
-    }
 #undef DWF_FACE
-    rc = block_inner(c, g, basis, nb, W, nb, prec, C->A64 + (size_t)d * nb * nb, bstride, nb, d, 0, st);
-    if (rc) break;
-    rc = blas_axpby(c, -1.0, W, prec, 1.0, H, prec, n * nb, st);
+      rc = block_inner(c, g, basis, nb, W, ng, prec, C->A64 + (size_t)d * nb * nb + k0, bstride, nb, d, 0, st);
+      if (rc) break;
+      rc = blas_axpby(c, -1.0, W, prec, 1.0, H, prec, n * ng, st);
+    }
+    if (rc == DWF_OK) rc = block_inner(c, g, basis, nb, H, ng, prec, C->A64 + k0, bstride, nb, 0, 0, st);
   }
-  if (rc == DWF_OK) rc = block_inner(c, g, basis, nb, H, nb, prec, C->A64, bstride, nb, 0, 0, st);
   if (rc == DWF_OK) rc = blas_copy(c, C->A32, DWF_F32, C->A64, DWF_F64, (int64_t)na, st);
   if (rc == DWF_OK) {
     cudaError_t e = cudaStreamSynchronize(st);
@@ -475,6 +554,8 @@ extern "C" int coarse_destroy(dwf_coarse* C) {
   if (C->A32) cudaFree(C->A32);
   if (C->At) cudaFree(C->At);
   if (C->Bt) cudaFree(C->Bt);
+  if (C->Arb) cudaFree(C->Arb);
+  coarse_defl_free(C);
   if (C->err) cudaFree(C->err);
   if (C->err_host) cudaFreeHost(C->err_host);
   if (C->err_ready) cudaEventDestroy(C->err_ready);
@@ -562,6 +643,17 @@ extern "C" int coarse_solve(dwf_coarse* C, void* e, const void* r, double tol, i
   if (!C || !e || !r || !(tol > 0) || maxiter < 1) return DWF_EINVAL;
   int it = 0;
   int rc = coarse_cg(C, (float2*)e, (const float2*)r, tol, maxiter, &it, (cudaStream_t)stream);
+  if (iters) *iters = it;
+  if (rc) return rc;
+  DWF_CUDA(C->ctx, cudaStreamSynchronize((cudaStream_t)stream));
+  return DWF_OK;
+}
+
+extern "C" int coarse_solve_rb(dwf_coarse* C, void* e, const void* r, double tol, int maxiter, int* iters,
+                               void* stream) {
+  if (!C || !e || !r || !(tol > 0) || maxiter < 1) return DWF_EINVAL;
+  int it = 0;
+  int rc = coarse_rbcg(C, (float2*)e, (const float2*)r, tol, maxiter, &it, (cudaStream_t)stream);
   if (iters) *iters = it;
   if (rc) return rc;
   DWF_CUDA(C->ctx, cudaStreamSynchronize((cudaStream_t)stream));
@@ -687,7 +779,9 @@ int vcycle(dwf_mg* G, void* x, const void* r0, cudaStream_t st, double* nH, int*
   rc = blas_copy(c, rc32, DWF_F32, t64, DWF_F64, ncv, st);
   if (rc) return rc;
   int it = 0;
-  rc = coarse_cg(C, (float2*)ec32, (const float2*)rc32, G->p.coarse_tol, G->p.coarse_maxiter, &it, st);
+  rc = G->p.coarse_solver == DWF_COARSE_RB
+           ? coarse_rbcg(C, (float2*)ec32, (const float2*)rc32, G->p.coarse_tol, G->p.coarse_maxiter, &it, st)
+           : coarse_cg(C, (float2*)ec32, (const float2*)rc32, G->p.coarse_tol, G->p.coarse_maxiter, &it, st);
   if (rc) return rc;
   *ncoarse += it;
   rc = blas_copy(c, t64, DWF_F64, ec32, DWF_F32, ncv, st);
@@ -821,6 +915,9 @@ extern "C" int mg_setup(dwf_ctx* c, const dwf_mg_params* p, const void* eta, dwf
   if (nb < 2 || (nb & 1) || nb > 64 || nb / 2 > 32) return dwf_fail(c, DWF_EINVAL, "nbasis must be even, <= 64");
   if (p->subspace_mode != DWF_SUBSPACE_BATCH && p->subspace_mode != DWF_SUBSPACE_RECURSIVE)
     return dwf_fail(c, DWF_EINVAL, "bad subspace mode");
+  if (p->coarse_solver != DWF_COARSE_CG && p->coarse_solver != DWF_COARSE_RB &&
+      p->coarse_solver != DWF_COARSE_DEFLATED)
+    return dwf_fail(c, DWF_EINVAL, "bad coarse solver");
   dwf_mg* G = new (std::nothrow) dwf_mg();
   if (!G) return DWF_ENOMEM;
   G->ctx = c;
@@ -833,59 +930,51 @@ extern "C" int mg_setup(dwf_ctx* c, const dwf_mg_params* p, const void* eta, dwf
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = full_elems(c);
   const int nplus = nb / 2;
-  void* f32 = nullptr;
-  double2* b64 = nullptr;
-  if (cudaMalloc(&G->basis, (size_t)n * nb * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc(&f32, (size_t)n * nplus * 2 * sizeof(float2)) != cudaSuccess ||
-      cudaMalloc(&b64, (size_t)n * nb * sizeof(double2)) != cudaSuccess) {
+  // Memory: the basis (nb FP32 full fields) is the only field-sized storage
+  // the setup keeps; the filter writes into it, the chirality projection and
+  // the orthonormalisation work on it in place, and the coarse build takes its
+  // H_DW images eight vectors at a time.
+  if (cudaMalloc(&G->basis, (size_t)n * nb * sizeof(float2)) != cudaSuccess) {
     cudaGetLastError();
-    if (f32) cudaFree(f32);
-    if (b64) cudaFree(b64);
     mg_destroy(G);
     return dwf_fail(c, DWF_ENOMEM, "mg basis");
   }
-  auto cleanup = [&]() {
-    cudaFree(f32);
-    cudaFree(b64);
-  };
-  // 1. filtered vectors (FP32): batch mode filters nb Gaussians; recursive mode
-  //    builds nb/2 vectors from one Gaussian.
+  float2* B = G->basis;
+  // 1. filtered vectors: batch mode filters nb Gaussians (eight at a time);
+  //    recursive mode builds nb/2 vectors from one Gaussian.
   double lmax = p->lambda_max;
+  const int chunk = 8;
   if (p->subspace_mode == DWF_SUBSPACE_BATCH) {
-    void* e32 = ws(c, MW_T10, (size_t)n * nb * sizeof(float2));
-    if (!e32) {
-      cleanup();
-      mg_destroy(G);
-      return dwf_fail(c, DWF_ENOMEM, "ws");
+    void* e32 = ws(c, MW_T10, (size_t)n * chunk * sizeof(float2));
+    rc = e32 ? DWF_OK : dwf_fail(c, DWF_ENOMEM, "ws");
+    for (int r0 = 0; r0 < nb && rc == DWF_OK; r0 += chunk) {
+      const int nr = nb - r0 < chunk ? nb - r0 : chunk;
+      rc = blas_copy(c, e32, DWF_F32, (const double2*)eta + (size_t)r0 * n, DWF_F64, n * nr, st);
+      if (rc == DWF_OK)
+        rc = filter_core(c, B + (size_t)r0 * n, e32, nr, p->lambda_lo, lmax, p->filter_order, p->mf, DWF_F32, true,
+                         st);
     }
-    rc = blas_copy(c, e32, DWF_F32, eta, DWF_F64, n * nb, st);
-    for (int r0 = 0; r0 < nb && rc == DWF_OK; r0 += DWF_MAX_RHS) {
-      const int nr = nb - r0 < DWF_MAX_RHS ? nb - r0 : DWF_MAX_RHS;
-      rc = filter_core(c, (float2*)f32 + (size_t)r0 * n, (float2*)e32 + (size_t)r0 * n, nr, p->lambda_lo, lmax,
-                       p->filter_order, p->mf, DWF_F32, true, st);
-    }
-    if (rc == DWF_OK) rc = normalise_fields(c, f32, nb, n, DWF_F32, st);
+    if (rc == DWF_OK) rc = normalise_fields(c, B, nb, n, DWF_F32, st);
   } else {
     void* e32 = ws(c, MW_T10, (size_t)n * sizeof(float2));
-    rc = e32 ? blas_copy(c, e32, DWF_F32, eta, DWF_F64, n, st) : DWF_ENOMEM;
+    rc = e32 ? blas_copy(c, e32, DWF_F32, eta, DWF_F64, n, st) : dwf_fail(c, DWF_ENOMEM, "ws");
     if (rc == DWF_OK)
-      rc = cheby_recursive_basis(c, f32, e32, p->lambda_lo, lmax, p->filter_order, p->delta, nplus, p->mf, DWF_F32,
+      rc = cheby_recursive_basis(c, B, e32, p->lambda_lo, lmax, p->filter_order, p->delta, nplus, p->mf, DWF_F32,
                                  stream);
   }
-  // 2. chirality projection into FP64: first nb/2 basis vectors take +, the rest -
-  if (rc == DWF_OK) rc = blas_copy(c, b64, DWF_F64, f32, DWF_F32, n * (p->subspace_mode == DWF_SUBSPACE_BATCH ? nb : nplus), st);
+  // 2. chirality projection in place: the first nb/2 basis vectors take +, the rest -
   if (rc == DWF_OK) {
     if (p->subspace_mode == DWF_SUBSPACE_BATCH) {
-      rc = chiral(c, b64, b64, +1, DWF_F64, nplus, st);
-      if (rc == DWF_OK) rc = chiral(c, b64 + (size_t)nplus * n, b64 + (size_t)nplus * n, -1, DWF_F64, nplus, st);
+      rc = chiral(c, B, B, +1, DWF_F32, nplus, st);
+      if (rc == DWF_OK) rc = chiral(c, B + (size_t)nplus * n, B + (size_t)nplus * n, -1, DWF_F32, nplus, st);
     } else {
-      rc = chiral(c, b64 + (size_t)nplus * n, b64, -1, DWF_F64, nplus, st);
-      if (rc == DWF_OK) rc = chiral(c, b64, b64, +1, DWF_F64, nplus, st);
+      rc = chiral(c, B + (size_t)nplus * n, B, -1, DWF_F32, nplus, st);
+      if (rc == DWF_OK) rc = chiral(c, B, B, +1, DWF_F32, nplus, st);
     }
   }
-  // 3. FP64 block orthonormalisation (Cholesky-QR twice per block and chirality)
-  if (rc == DWF_OK) rc = block_orthonormalise(c, b64, nb, nplus, p->block, stream);
-  if (rc == DWF_OK) rc = blas_copy(c, G->basis, DWF_F32, b64, DWF_F64, n * nb, st);
+  // 3. block orthonormalisation in place: Cholesky-QR twice per block and
+  //    chirality, Gram matrices, factorisation and updates in FP64 arithmetic
+  if (rc == DWF_OK) rc = ortho_inplace_f32(c, G->g, B, nb, nplus, st);
   if (rc == DWF_OK) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = dwf_cuda_check(c, e, "mg_setup");
@@ -894,9 +983,29 @@ extern "C" int mg_setup(dwf_ctx* c, const dwf_mg_params* p, const void* eta, dwf
   // 4. little Dirac operator of H_DW from the FP32 basis
   Timer t2;
   if (rc == DWF_OK) rc = coarse_build(c, G->basis, nb, nplus, p->block, p->mf, DWF_F32, &G->coarse, stream);
+  if (rc == DWF_OK && p->coarse_solver == DWF_COARSE_RB) rc = coarse_rb_ready(G->coarse, st);
+  if (rc == DWF_OK && p->coarse_solver == DWF_COARSE_DEFLATED) {
+    // Lanczos start vector: the restriction of the first eta (the setup's
+    // own random input)
+    const int64_t ncv = (int64_t)G->g.nc * nb;
+    double2* t64 = (double2*)ws(c, MW_T7, ncv * sizeof(double2));
+    void* e1 = ws(c, MW_T10, (size_t)n * sizeof(float2));
+    void* v0 = nullptr;
+    rc = (!t64 || !e1) ? dwf_fail(c, DWF_ENOMEM, "ws") : coarse_ws(G->coarse, 4, ncv * sizeof(float2), &v0);
+    if (rc == DWF_OK) rc = blas_copy(c, e1, DWF_F32, eta, DWF_F64, n, st);
+    if (rc == DWF_OK) rc = block_inner(c, G->g, B, nb, e1, 1, DWF_F32, t64, nb, 1, 0, 0, st);
+    if (rc == DWF_OK) rc = blas_copy(c, v0, DWF_F32, t64, DWF_F64, ncv, st);
+    if (rc == DWF_OK)
+      rc = coarse_deflate(G->coarse, v0, p->coarse_nev, p->coarse_lanczos, p->coarse_cheb_order, p->coarse_cheb_lo,
+                          0.0, nullptr, stream);
+  }
   G->coarse_op_seconds = t2.sec();
   G->lambda_max_used = lmax;
-  cleanup();
+  // the field-sized setup workspaces are released for the solve
+  if (rc == DWF_OK) {
+    DWF_CUDA(c, cudaStreamSynchronize(st));
+    for (int slot = MW_T0; slot <= MW_T11; slot++) dwf_ws_release(c, slot);
+  }
   if (rc) {
     mg_destroy(G);
     return rc;

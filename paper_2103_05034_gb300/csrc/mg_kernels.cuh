@@ -201,13 +201,58 @@ __global__ void __launch_bounds__(256) k_block_combine(typename Prec<PY>::S* Y, 
   }
 }
 
+// In-place form of the Cholesky-QR update for a group of n <= 32 FP32 fields
+// (x_k <- sum_{j <= k} x_j Rinv[xc][j][k], Rinv upper triangular within the
+// group, rows and columns offset by g0 in the nb x nb matrix): each thread
+// owns one element of the block, reads it from all n fields first and then
+// writes the n results, so no second copy of the basis is needed.  FP64
+// arithmetic on FP32 storage.
+static __global__ void __launch_bounds__(256) k_block_update_inplace(float2* X, long long xstride, int n, int g0, int nb,
+                                                              const double2* Rinv, BlockGeom g) {
+  __shared__ double2 sm[32 * 32];
+  const int xc = blockIdx.x;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int j = e / n, k = e - j * n;
+    sm[e] = Rinv[(long long)xc * nb * nb + (long long)(g0 + j) * nb + g0 + k];
+  }
+  __syncthreads();
+  const int row_len = 12 * g.Ls;
+  const int nel = g.b4 * row_len;
+  for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+    const int i = e / row_len, q = e - i * row_len;
+    bool face;
+    const long long off = block_site_offset(g, xc, i, 0, &face) + q;
+    float2 v[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++)
+      if (j < n) v[j] = X[(long long)j * xstride + off];
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+      if (k >= n) break;
+      double re = 0, im = 0;
+#pragma unroll
+      for (int j = 0; j < 32; j++) {
+        if (j > k) break;
+        const double2 m = sm[j * n + k];
+        re += (double)v[j].x * m.x - (double)v[j].y * m.y;
+        im += (double)v[j].x * m.y + (double)v[j].y * m.x;
+      }
+      X[(long long)k * xstride + off] = make_float2((float)re, (float)im);
+    }
+  }
+}
+
 // Cholesky G = R^dag R of each (block, group) Gram sub-matrix and R^-1 written
 // into Rinv[xc][j][k] (upper triangular within the group; entries across groups
 // are left untouched, so Rinv must be zeroed first).  One CTA per (block,
 // group); thread 0 factorises in shared memory (groups of at most 32 vectors).
 // Sets *fail if a pivot is not positive (the vectors are linearly dependent on
 // that block).
-static __global__ void k_block_cholinv(const double2* G, double2* Rinv, int nb, int nplus, int* fail) {
+// shift_rel > 0 factorises G + shift_rel * max_k G_kk * 1 instead (the first
+// pass of shifted Cholesky-QR for vectors stored in FP32, whose Gram matrices
+// may be numerically singular).
+static __global__ void k_block_cholinv(const double2* G, double2* Rinv, int nb, int nplus, int* fail,
+                                       double shift_rel = 0.0) {
   __shared__ double2 R[32][33];
   __shared__ double2 Ri[32][33];
   const int xc = blockIdx.x, grp = blockIdx.y;
@@ -220,8 +265,13 @@ static __global__ void k_block_cholinv(const double2* G, double2* Rinv, int nb, 
       R[a][b] = make_double2(0, 0);
       Ri[a][b] = make_double2(0, 0);
     }
+  double shift = 0.0;
+  if (shift_rel > 0) {
+    for (int k = 0; k < n; k++) shift = fmax(shift, Gb[(g0 + k) * nb + g0 + k].x);
+    shift *= shift_rel;
+  }
   for (int k = 0; k < n; k++) {
-    double dkk = Gb[(g0 + k) * nb + g0 + k].x;
+    double dkk = Gb[(g0 + k) * nb + g0 + k].x + shift;
     for (int i = 0; i < k; i++) dkk -= R[i][k].x * R[i][k].x + R[i][k].y * R[i][k].y;
     if (!(dkk > 0)) {
       atomicExch(fail, 1);

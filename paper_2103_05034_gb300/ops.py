@@ -258,6 +258,34 @@ def coarse_solve(coarse, e, r, tol, maxiter=1000):
     return it.value
 
 
+def coarse_solve_rb(coarse, e, r, tol, maxiter=1000):
+    """Red-black coarse solve (CG on the even Schur complement squared); returns
+    the iteration count."""
+    it = C.c_int()
+    check(lib().coarse_solve_rb(coarse.h, _ptr(e), _ptr(r), tol, maxiter, C.byref(it), _stream()),
+          coarse.ctx.h)
+    return it.value
+
+
+def coarse_deflate(coarse, v0, nev, nk, order, lam_lo, lam_max=0.0):
+    """Chebyshev-preconditioned Lanczos deflation space of A^2 kept by the
+    operator; returns the nev Ritz values (ascending).  nev = 0 drops it."""
+    th = (C.c_double * max(nev, 1))()
+    check(lib().coarse_deflate(coarse.h, _ptr(v0) if v0 is not None else None, nev, nk, order, lam_lo,
+                               lam_max, th, _stream()), coarse.ctx.h)
+    return [th[i] for i in range(nev)]
+
+
+def coarse_export_deflation(coarse):
+    """(V as complex128 numpy (nev, nc, nb), 1/theta) of the deflation space."""
+    n = C.c_int()
+    check(lib().coarse_export_deflation(coarse.h, None, None, C.byref(n)))
+    V = np.zeros((n.value, coarse.nc, coarse.nb, 2), np.float32)
+    ti = (C.c_double * max(n.value, 1))()
+    check(lib().coarse_export_deflation(coarse.h, _ptr(V), ti, C.byref(n)))
+    return V.astype(np.float64).view(np.complex128)[..., 0], np.array([ti[i] for i in range(n.value)])
+
+
 def dwf_restrict(ctx, out, inp, basis, nb, block, nrhs=1):
     check(lib().dwf_restrict(ctx.h, _ptr(out), _ptr(inp), _ptr(basis), nb, _ivec(block), nrhs,
                              _prec_of(basis), _stream()), ctx.h)
@@ -272,7 +300,8 @@ def dwf_prolong(ctx, out, inp, basis, nb, block, nrhs=1, accumulate=0):
 
 def mg_params(block, nbasis, mf, *, subspace_mode=_lib.SUBSPACE_BATCH, lambda_lo=0.02,
               lambda_max=60.0, filter_order=60, delta=100, smooth=(0.5, 60.0, 12),
-              coarse_tol=0.02, coarse_maxiter=500, nkrylov=8, maxiter=1000, graph=True):
+              coarse_tol=0.02, coarse_maxiter=500, nkrylov=8, maxiter=1000, graph=True,
+              coarse_solver=_lib.COARSE_CG, deflation=(0, 0, 0, 0.0)):
     p = _lib.MGParams()
     p.block = (C.c_int * 4)(*block)
     p.nbasis, p.subspace_mode, p.mf = nbasis, subspace_mode, mf
@@ -280,6 +309,8 @@ def mg_params(block, nbasis, mf, *, subspace_mode=_lib.SUBSPACE_BATCH, lambda_lo
     p.smooth_lo, p.smooth_hi, p.smooth_order = smooth
     p.coarse_tol, p.coarse_maxiter, p.nkrylov, p.maxiter = coarse_tol, coarse_maxiter, nkrylov, maxiter
     p.no_graph = 0 if graph else 1
+    p.coarse_solver = coarse_solver
+    p.coarse_nev, p.coarse_lanczos, p.coarse_cheb_order, p.coarse_cheb_lo = deflation
     return p
 
 

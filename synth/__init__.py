@@ -173,6 +173,15 @@ WORKLOADS = {
     # local statistics; generating 42M smeared links on the host is too slow)
     "dwf_48x48x48x96_ls24": dict(L=(48, 48, 48, 96), Ls=24, eps=0.5, ape=3, M5=1.8, mf=0.00078,
                                  tile_of="dwf_16x16x16x32_ls16", tile=(3, 3, 3, 3)),
+    # the largest volume on which the multigrid with 32 FP32 basis vectors fits
+    # one GPU (Ls = 24 and the mass of the physical-point workload); links: a
+    # smeared 8^3 x 16 field tiled 3 x 3 x 3 x 3
+    "dwf_24x24x24x48_ls24": dict(L=(24, 24, 24, 48), Ls=24, eps=0.5, ape=3, M5=1.8, mf=0.00078,
+                                 tile_of="dwf_8x8x8x16_ls24", tile=(3, 3, 3, 3)),
+    "dwf_8x8x8x16_ls24": dict(L=(8, 8, 8, 16), Ls=24, eps=0.5, ape=3, M5=1.8, mf=0.00078),
+    # an intermediate Ls = 24 volume for profiling (links: the 16^3 x 32 field tiled twice)
+    "dwf_32x32x32x64_ls24": dict(L=(32, 32, 32, 64), Ls=24, eps=0.5, ape=3, M5=1.8, mf=0.00078,
+                                 tile_of="dwf_16x16x16x32_ls16", tile=(2, 2, 2, 2)),
 }
 
 

@@ -461,3 +461,219 @@ def test_mg_solve_at_ls16():
     assert rel(x, xr) < 1e-6
     G.close()
     ctx.close()
+
+
+# ---------------------------------------------------------------- red-black coarse solve
+def test_coarse_solve_rb(coarse_case):
+    """coarse_solve_rb (CG on the even Schur complement squared) against the
+    oracle's coarse_rb_solve on the exported operator: the same iteration
+    count for the same stopping rule, and the dense solution of A e = r.  The
+    4428 blocking has a coarse extent of 1 (odd): the call must refuse it."""
+    from paper_2103_05034_gb300._lib import DWFError
+    L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
+    C = ops.coarse_build(ctx, fulls_dev(basis, L, F64), nb, nb // 2, block, mf)
+    r = coarse_vec(Aflat, nb, 1, 8)[:, :, 0]
+    rd = torch.from_numpy(layout.complex_to_real(r, F32).reshape(-1)).cuda()
+    e = torch.zeros_like(rd)
+    if any(n % 2 for n in C.Lc):
+        with pytest.raises(DWFError):
+            ops.coarse_solve_rb(C, e, rd, 1e-5, 2000)
+        C.close()
+        return
+    it = ops.coarse_solve_rb(C, e, rd, 1e-5, 2000)
+    Ast = np.moveaxis(C.export(), 1, 0).reshape((9,) + tuple(C.Lc[::-1]) + (nb, nb))
+    e_or, it_or = coarse.coarse_rb_solve(Ast, r.reshape(tuple(C.Lc[::-1]) + (nb,)), 1e-5, 2000)
+    assert abs(it - it_or) <= max(4, it_or // 20), (it, it_or)
+    eg = layout.real_to_complex(e.double().cpu().numpy()).reshape(r.shape)
+    dense = coarse.coarse_dense_from_stencil(Ast)
+    want = np.linalg.solve(dense, r.ravel())
+    assert rel(eg.ravel(), want) < 10 * rel(e_or.ravel(), want) + 1e-5
+    C.close()
+
+
+@pytest.mark.parametrize("nb", [32, 64])
+def test_coarse_solve_rb_fixed_width(nb):
+    """The red-black coarse CG with nb fixed at compile time (32, 64) on a 4^4
+    coarse lattice (8^4 x Ls 4, 2^4 blocks), filtered basis: iterations against
+    the oracle's red-black CG, the solution against the oracle's plain CG on
+    A^2 run far past the tolerance, and fewer iterations than the plain CG on
+    A^2 for the same relative tolerance."""
+    L, Ls, block, mf = (8, 8, 8, 8), 4, (2, 2, 2, 2), 0.01
+    U = synth.random_gauge(L, 0.5, 47)
+    ctx = ops.Context(L, Ls, M5, U)
+    g = fulls_dev([synth.gaussian_spinor(L, Ls, 520 + i) for i in range(nb)], L, F64)
+    d = torch.zeros_like(g)
+    ops.cheby_filter(ctx, d, g, nb, 0.2, 70.0, 12, mf)
+    half = d.numel() // 2
+    ops.dwf_chiral_project(ctx, d[:half], d[:half], 1, nb // 2)
+    ops.dwf_chiral_project(ctx, d[half:], d[half:], -1, nb // 2)
+    ops.block_orthonormalise(ctx, d, nb, nb // 2, block)
+    C = ops.coarse_build(ctx, d, nb, nb // 2, block, mf)
+    Ast = np.moveaxis(C.export(), 1, 0).reshape((9,) + tuple(C.Lc[::-1]) + (nb, nb))
+    r = synth.complex_gaussian(11, (C.nc, nb))
+    rd = torch.from_numpy(layout.complex_to_real(r, F32).reshape(-1)).cuda()
+    e = torch.zeros_like(rd)
+    tol = 1e-5
+    it = ops.coarse_solve_rb(C, e, rd, tol, 5000)
+    e_or, it_or = coarse.coarse_rb_solve(Ast, r.reshape(tuple(C.Lc[::-1]) + (nb,)), tol, 5000)
+    print(f"coarse_solve_rb nb={nb}: {it} iterations (oracle {it_or})")
+    assert abs(it - it_or) <= max(4, it_or // 20)
+    eg = layout.real_to_complex(e.double().cpu().numpy()).reshape(r.shape)
+    want, _ = coarse.coarse_cgnr(Ast, r.reshape(tuple(C.Lc[::-1]) + (nb,)), 1e-12, 50000)
+    assert rel(eg.ravel(), want.ravel()) < 10 * rel(e_or.ravel(), want.ravel()) + 1e-5
+    e2 = torch.zeros_like(rd)
+    it_plain = ops.coarse_solve(C, e2, rd, tol, 5000)
+    print(f"  plain CG on A^2: {it_plain} iterations")
+    assert it < it_plain
+    C.close()
+    ctx.close()
+
+
+def test_mg_solve_with_red_black_coarse_solver(mg_case):
+    """The HDCR solve with the red-black coarse solver reaches the tolerance
+    and the oracle's solution, as the plain coarse CG does."""
+    from paper_2103_05034_gb300._lib import COARSE_RB
+    L, Ls, mf, block, nb, U, ctx, etas, p, G = mg_case
+    prb = ops.mg_params(block, nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=0.5, lambda_max=70.0,
+                        filter_order=4, smooth=(0.5, 60.0, 6), coarse_tol=0.02, coarse_maxiter=500,
+                        nkrylov=8, maxiter=200, coarse_solver=COARSE_RB)
+    Grb = ops.MG(ctx, prb, fulls_dev(etas, L, F64))
+    b = synth.gaussian_spinor(L, Ls, 75)
+    bd = full_dev(b, L, F64)
+    xd = torch.zeros_like(bd)
+    st = ops.mg_solve(Grb, xd, bd, 1e-8)
+    x = dev_to_full_canon(xd, L, Ls)
+    assert krylov.true_residual(U, x, b, M5, mf) <= 1e-8 * 1.01, st
+    xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert rel(x, xr) < 1e-6
+    assert st["coarse_iterations"] > 0 and st["graph_replays"] > 0
+    Grb.close()
+
+
+# ---------------------------------------------------------------- coarse deflation
+@pytest.fixture(scope="module")
+def defl_case():
+    """A 4^4-site coarse lattice (8^4 x Ls 16, 2^4 blocks) with a 16-vector
+    basis filtered towards the low modes and a light mass (at Ls = 16 the
+    residual mass is small): an operator whose A^2 spans several decades."""
+    L, Ls, block, mf, nb = (8, 8, 8, 8), 16, (2, 2, 2, 2), 0.001, 16
+    U = synth.random_gauge(L, 0.5, 48, ape_steps=2)
+    ctx = ops.Context(L, Ls, M5, U)
+    g = fulls_dev([synth.gaussian_spinor(L, Ls, 540 + i) for i in range(nb)], L, F64)
+    d = torch.zeros_like(g)
+    ops.cheby_filter(ctx, d, g, nb, 0.05, 70.0, 24, mf)
+    half = d.numel() // 2
+    ops.dwf_chiral_project(ctx, d[:half], d[:half], 1, nb // 2)
+    ops.dwf_chiral_project(ctx, d[half:], d[half:], -1, nb // 2)
+    ops.block_orthonormalise(ctx, d, nb, nb // 2, block)
+    C = ops.coarse_build(ctx, d, nb, nb // 2, block, mf)
+    Ast = np.moveaxis(C.export(), 1, 0).reshape((9,) + tuple(C.Lc[::-1]) + (nb, nb))
+    yield ctx, C, Ast, nb
+    C.close()
+    ctx.close()
+
+
+def test_coarse_deflation_ritz_pairs(defl_case):
+    """Chebyshev-preconditioned Lanczos on A^2 (Sec. 3.5) from the same start
+    vector as the oracle's cheby_lanczos: the lowest Ritz values agree (FP32
+    Lanczos vectors against FP64), and every GPU pair is an eigenpair of the
+    exported operator's A^2 to a small residual."""
+    ctx, C, Ast, nb = defl_case
+    nev, nk, order, lo = 8, 60, 8, 0.05
+    v0 = synth.complex_gaussian(13, (C.nc, nb))
+    v0d = torch.from_numpy(layout.complex_to_real(v0, F32).reshape(-1)).cuda()
+    shape = tuple(C.Lc[::-1]) + (nb,)
+    appAA = lambda v: coarse.coarse_apply(Ast, coarse.coarse_apply(Ast, v.reshape(shape))).reshape(v.shape)
+    lam = 0.0
+    v = v0.ravel() / np.linalg.norm(v0)
+    for _ in range(30):  # the oracle's lambda_max from the same power method
+        w = appAA(v)
+        lam = np.linalg.norm(w)
+        v = w / lam
+    lmax = 1.1 * lam
+    th = ops.coarse_deflate(C, v0d, nev, nk, order, lo, lmax)
+    th_or, V_or = coarse.cheby_lanczos(appAA, v0.ravel(), nev, nk, order, lo, lmax)
+    print("GPU Ritz values", np.array(th)[:4], "oracle", th_or[:4])
+    assert np.allclose(np.sort(th)[:4], np.sort(th_or)[:4], rtol=1e-3)
+    V, thinv = ops.coarse_export_deflation(C)
+    Vm = V.reshape(nev, -1)
+    # orthonormal Ritz vectors whose Rayleigh quotients are the Ritz values
+    assert np.abs(Vm.conj() @ Vm.T - np.eye(nev)).max() < 1e-4
+    for i in range(nev):
+        assert np.vdot(Vm[i], appAA(Vm[i])).real == pytest.approx(1.0 / thinv[i], rel=1e-4)
+    # and the lowest pair approximates an eigenpair of A^2 (its residual is
+    # small on the scale of the spectrum)
+    r = appAA(Vm[0]) - Vm[0] / thinv[0]
+    print("lowest Ritz pair residual / lambda_max:", np.linalg.norm(r) / lmax)
+    assert np.linalg.norm(r) <= 5e-2 * lmax
+    ops.coarse_deflate(C, None, 0, 0, 0, 0.0)
+
+
+@pytest.fixture(scope="module")
+def mg16():
+    """The multigrid of the 16^3 x 32 x 16 workload (recursive subspace with
+    m = 300, Delta = 60; 4^4 x Ls blocks, 16 + 16 vectors): its coarse
+    operator has the low modes the deflation is for."""
+    from paper_2103_05034_gb300._lib import SUBSPACE_RECURSIVE
+    name = "dwf_16x16x16x32_ls16"
+    w = synth.WORKLOADS[name]
+    L, Ls, mf = w["L"], w["Ls"], w["mf"]
+    ctx = ops.Context(L, Ls, M5, synth.workload_gauge(name))
+    eta = full_dev(synth.gaussian_spinor(L, Ls, synth.SEED_BASIS), L, F64)
+    p = ops.mg_params((4, 4, 4, 4), 32, mf, subspace_mode=SUBSPACE_RECURSIVE, lambda_lo=0.05, lambda_max=80.0,
+                      filter_order=300, delta=60, smooth=(0.05, 80.0, 40), coarse_tol=2e-3)
+    G = ops.MG(ctx, p, eta)
+    yield ctx, G
+    G.close()
+    ctx.close()
+
+
+def test_coarse_deflated_solve(mg16):
+    """The coarse CG started from the deflation guess against the oracle's
+    coarse_deflated_cgnr with the GPU's own (exported) Ritz pairs, on the
+    16^3 multigrid's coarse operator: the same iteration count, the solution
+    (against the oracle's deflated CG run far past the tolerance), and far
+    fewer iterations than without deflation."""
+    ctx, G = mg16
+    C = G.coarse
+    nb = C.nb
+    Ast = np.moveaxis(C.export(), 1, 0).reshape((9,) + tuple(C.Lc[::-1]) + (nb, nb))
+    v0 = synth.complex_gaussian(14, (C.nc, nb))
+    v0d = torch.from_numpy(layout.complex_to_real(v0, F32).reshape(-1)).cuda()
+    ops.coarse_deflate(C, v0d, 32, 96, 10, 0.05)
+    V, thinv = ops.coarse_export_deflation(C)
+    shape = tuple(C.Lc[::-1]) + (nb,)
+    Vs = [V[i].reshape(shape) for i in range(len(thinv))]
+    r = synth.complex_gaussian(15, (C.nc, nb))
+    rd = torch.from_numpy(layout.complex_to_real(r, F32).reshape(-1)).cuda()
+    tol = 1e-5
+    e = torch.zeros_like(rd)
+    it = ops.coarse_solve(C, e, rd, tol, 5000)
+    e_or, it_or = coarse.coarse_deflated_cgnr(Ast, r.reshape(shape), 1.0 / thinv, Vs, tol, 5000)
+    ops.coarse_deflate(C, None, 0, 0, 0, 0.0)
+    e2 = torch.zeros_like(rd)
+    it_plain = ops.coarse_solve(C, e2, rd, tol, 5000)
+    print(f"deflated coarse CG: {it} iterations (oracle {it_or}), undeflated {it_plain}")
+    assert abs(it - it_or) <= max(4, it_or // 10)
+    assert 2 * it < it_plain
+    eg = layout.real_to_complex(e.double().cpu().numpy()).reshape(r.shape)
+    want, _ = coarse.coarse_deflated_cgnr(Ast, r.reshape(shape), 1.0 / thinv, Vs, 1e-11, 20000)
+    assert rel(eg.ravel(), want.ravel()) < 10 * rel(e_or.ravel(), want.ravel()) + 1e-5
+
+
+def test_mg_solve_with_deflated_coarse_solver(mg_case):
+    from paper_2103_05034_gb300._lib import COARSE_DEFLATED
+    L, Ls, mf, block, nb, U, ctx, etas, p, G = mg_case
+    pd = ops.mg_params(block, nb, mf, subspace_mode=SUBSPACE_BATCH, lambda_lo=0.5, lambda_max=70.0,
+                       filter_order=4, smooth=(0.5, 60.0, 6), coarse_tol=0.02, coarse_maxiter=500,
+                       nkrylov=8, maxiter=200, coarse_solver=COARSE_DEFLATED, deflation=(8, 24, 8, 0.5))
+    Gd = ops.MG(ctx, pd, fulls_dev(etas, L, F64))
+    b = synth.gaussian_spinor(L, Ls, 76)
+    bd = full_dev(b, L, F64)
+    xd = torch.zeros_like(bd)
+    st = ops.mg_solve(Gd, xd, bd, 1e-8)
+    x = dev_to_full_canon(xd, L, Ls)
+    assert krylov.true_residual(U, x, b, M5, mf) <= 1e-8 * 1.01, st
+    xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert rel(x, xr) < 1e-6
+    Gd.close()
