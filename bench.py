@@ -250,92 +250,95 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------- MG vs FP64 RB-CG
-# HDCR parameters for the 16^3x32, Ls=16 workload: 4^4 x Ls blocks, 16 + 16
-# basis vectors from the paper's recursive Chebyshev filter (m = 500,
-# Delta = 100, lambda_lo = 0.05, Tables 1 and 12), pGCR(32).  The smoother
-# interval is lowered to [0.05, lambda_max] with order 40 and the coarse CG
-# runs to 2e-3: on the smeared-random stand-in fields the Shamir bulk modes
-# reach H^2 ~ 0.04, below the paper's [0.5, 60] (with that interval the solve
-# stalls near 1e-4); among the orders 24-40 and coarse tolerances 0.02-1e-3
-# tried, this pair took the fewest seconds.
+# HDCR parameters: 4^4 x Ls blocks, 16 + 16 basis vectors from the paper's
+# recursive Chebyshev filter (m = 500, Delta = 100, lambda_lo = 0.05, Tables 1
+# and 12), pGCR(32), and the coarse CG on A^2 to 2e-3 started from the
+# Chebyshev-Lanczos deflation guess (Sec. 3.5).  The smoother interval is
+# lowered to [0.05, lambda_max] with order 40: on the smeared-random stand-in
+# fields the Shamir bulk modes reach H^2 ~ 0.04, below the paper's [0.5, 60]
+# (with [0.2, lambda_max] or [0.5, lambda_max] the solve stalls).  Deflation:
+# 64 Ritz vectors from 160 Lanczos steps at 16^3 x 32 x 16; 128 from 256 at
+# 24^3 x 48 x 24, where 64 did not keep the coarse solve short (the paper
+# notes the same growth with volume).
 MG_PARAMS = dict(block=(4, 4, 4, 4), nbasis=32, subspace="recursive", filter_order=500, delta=100,
                  lambda_lo=0.05, smooth=(0.05, None, 40), coarse_tol=2e-3, coarse_maxiter=5000,
-                 nkrylov=32, maxiter=300)
+                 nkrylov=32, maxiter=300, coarse_solver="deflated", deflation=(64, 160, 10, 0.05))
+MG_PARAMS_LARGE = dict(MG_PARAMS, deflation=(128, 256, 10, 0.05))
 
 
-def mg_vs_fp64(ctx, w, b, bd, tol):
+def mg_vs_fp64(ctx, w, bd, tol, params=MG_PARAMS, eta_seed=None):
     """Time to a true residual of `tol` on the same GPU and source: plain FP64
-    red-black CG against HDCR setup + solve (mixed precision).  One run each,
-    outside the timed steps; CUDA-event and host-clock times agree because
-    both calls synchronise."""
+    red-black CG (and the mixed-precision one) against HDCR setup + solve
+    (mixed precision), and setup + two solves (the second source a shifted
+    copy of the first).  One run each, outside the timed steps; every call
+    synchronises, so host-clock times are GPU times.  The multigrid's random
+    inputs (the power method's start vector and the subspace Gaussian) are
+    drawn on the device by torch's seeded generator."""
     import torch
 
     from paper_2103_05034_gb300 import ops
-    from paper_2103_05034_gb300._lib import F32, F64, SOLVE_F64, SUBSPACE_BATCH, SUBSPACE_RECURSIVE
+    from paper_2103_05034_gb300._lib import (COARSE_CG, COARSE_DEFLATED, COARSE_RB, F32, SOLVE_F64,
+                                             SOLVE_MIXED_F32, SUBSPACE_BATCH, SUBSPACE_RECURSIVE)
 
-    L, Ls, mf = w["L"], w["Ls"], w["mf"]
-    out = {}
+    mf = w["mf"]
+    out = {"workload": "x".join(map(str, w["L"])) + f"x{w['Ls']}", "mf": mf}
     x = torch.zeros_like(bd)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st = ops.rbcg_solve(ctx, x, bd, mf, tol, 100000, SOLVE_F64)
-    out["fp64_rbcg_s"] = time.perf_counter() - t0
-    out["fp64_rbcg_iterations"] = st["iterations"]
-    out["fp64_rbcg_true_residual"] = st["true_residual"]
-    from paper_2103_05034_gb300 import layout
-    p = dict(MG_PARAMS)
+    for pol, name in ((SOLVE_F64, "fp64_rbcg"), (SOLVE_MIXED_F32, "mixed_rbcg")):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ops.rbcg_solve(ctx, x, bd, mf, tol, 100000, pol)
+        out[name + "_s"] = time.perf_counter() - t0
+        out[name + "_iterations"] = st["iterations"]
+        out[name + "_true_residual"] = st["true_residual"]
+    p = dict(params)
     nb = p["nbasis"]
     recursive = p["subspace"] == "recursive"
-    neta = 1 if recursive else nb  # the recursive basis grows from one Gaussian
-    t0 = time.perf_counter()
-    v0 = torch.from_numpy(layout.complex_to_real(layout.to_full(synth.gaussian_spinor(L, Ls, 77), L), F64)).cuda()
-    eta = torch.cat([torch.from_numpy(layout.complex_to_real(
-        layout.to_full(synth.gaussian_spinor(L, Ls, synth.SEED_BASIS + i), L), F64).reshape(-1))
-        for i in range(neta)]).cuda()
+    gen = torch.Generator(device="cuda").manual_seed(77)
+    v0 = torch.randn(bd.numel(), generator=gen, device="cuda", dtype=torch.float64)
+    gen = torch.Generator(device="cuda").manual_seed(synth.SEED_BASIS if eta_seed is None else eta_seed)
+    eta = torch.randn(bd.numel() * (1 if recursive else nb), generator=gen, device="cuda", dtype=torch.float64)
     torch.cuda.synchronize()
-    t_in = time.perf_counter() - t0  # host-side input generation, not counted
     t0 = time.perf_counter()
     # lambda_max of D^dag D bounds the filter and smoother intervals (power
     # method in FP32, 100 iterations, 10 % margin: the Rayleigh quotient
     # approaches the top of the spectrum from below)
     lmax = ops.dwf_power_max(ctx, v0, mf, 100, F32) * 1.10
+    cs = {"cg": COARSE_CG, "rb": COARSE_RB, "deflated": COARSE_DEFLATED}[p["coarse_solver"]]
     prm = ops.mg_params(p["block"], nb, mf, subspace_mode=SUBSPACE_RECURSIVE if recursive else SUBSPACE_BATCH,
                         lambda_lo=p["lambda_lo"], lambda_max=lmax, filter_order=p["filter_order"],
                         delta=p["delta"], smooth=(p["smooth"][0], lmax, p["smooth"][2]),
-                        coarse_tol=p["coarse_tol"],
-                        coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"], maxiter=p["maxiter"])
+                        coarse_tol=p["coarse_tol"], coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"],
+                        maxiter=p["maxiter"], coarse_solver=cs,
+                        deflation=p["deflation"] if cs == COARSE_DEFLATED else (0, 0, 0, 0.0))
     G = ops.MG(ctx, prm, eta)
+    del eta
     torch.cuda.synchronize()
     out["mg_setup_s"] = time.perf_counter() - t0
-    x.zero_()
-    t0 = time.perf_counter()
-    sm = ops.mg_solve(G, x, bd, tol)
-    out["mg_solve_s"] = time.perf_counter() - t0
-    out["mg_outer_iterations"] = sm["iterations"]
-    out["mg_coarse_iterations"] = sm["coarse_iterations"]
-    out["mg_fine_matmuls"] = sm["fine_matmuls"]
-    out["mg_true_residual"] = sm["true_residual"]
-    out["mg_subspace_s"] = sm["setup_seconds"]
-    out["mg_coarse_op_s"] = sm["coarse_op_seconds"]
-    out["mg_total_s"] = out["mg_setup_s"] + out["mg_solve_s"]
-    out["speedup_fp64_over_mg"] = out["fp64_rbcg_s"] / out["mg_total_s"]
+    solves = []
+    for k in range(2):
+        src = bd if k == 0 else torch.roll(bd, 24)  # a second source: the first shifted by one complex spinor row
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sm = ops.mg_solve(G, x, src, tol)
+        solves.append((time.perf_counter() - t0, sm))
+    (t1, s1), (t2, s2) = solves
+    out.update({"mg_solve_s": t1, "mg_outer_iterations": s1["iterations"],
+                "mg_coarse_iterations": s1["coarse_iterations"], "mg_fine_matmuls": s1["fine_matmuls"],
+                "mg_true_residual": s1["true_residual"], "mg_subspace_s": s1["setup_seconds"],
+                "mg_coarse_op_s": s1["coarse_op_seconds"], "mg_graph_replays": s1["graph_replays"],
+                "mg_second_solve_s": t2, "mg_second_solve_outer_iterations": s2["iterations"],
+                "mg_second_solve_true_residual": s2["true_residual"]})
+    out["mg_total_s"] = out["mg_setup_s"] + t1
+    out["mg_setup_plus_two_solves_s"] = out["mg_total_s"] + t2
     # The two-flavour determinant needs two solves of the unsquared operator
     # (the MG solve) against one of the squared operator (CGNR): the paper's
     # break-even criterion is setup + two MG solves against one CGNR solve.
-    b2 = torch.from_numpy(layout.complex_to_real(layout.to_full(
-        synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE + 1), L), F64)).cuda()
-    x.zero_()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sm2 = ops.mg_solve(G, x, b2, tol)
-    out["mg_second_solve_s"] = time.perf_counter() - t0
-    out["mg_second_solve_outer_iterations"] = sm2["iterations"]
-    out["mg_second_solve_true_residual"] = sm2["true_residual"]
-    out["mg_setup_plus_two_solves_s"] = out["mg_total_s"] + out["mg_second_solve_s"]
+    out["speedup_fp64_over_mg"] = out["fp64_rbcg_s"] / out["mg_total_s"]
     out["speedup_fp64_over_mg_setup_two_solves"] = out["fp64_rbcg_s"] / out["mg_setup_plus_two_solves_s"]
     out["lambda_max"] = lmax
     out["params"] = {k: v for k, v in p.items()}
-    out["input_generation_s_not_counted"] = t_in
     G.close()
     return out
 
@@ -568,13 +571,29 @@ def run_ours(args):
             if args.mg_compare:
                 try:
                     bsd = device_source(cs, ws_, bs, 0, dev)
-                    line["mg_vs_fp64"] = mg_vs_fp64(cs, ws_, bs, bsd, args.tol)
+                    line["mg_vs_fp64"] = mg_vs_fp64(cs, ws_, bsd, args.tol)
                     del bsd
                 except Exception as e:  # reported, not hidden: the line says what failed
                     line["mg_vs_fp64"] = {"error": str(e)}
             cs.close()
         except Exception as e:
             line["small_workload_legs"] = {"error": str(e)}
+        torch.cuda.empty_cache()
+        if args.mg_compare and args.mg_large:
+            # the multigrid at the largest volume its 32-vector FP32 basis fits
+            # (24^3 x 48 x 24, the 48^3 workload's Ls and mass) against FP64 RB-CG
+            try:
+                large = "dwf_24x24x24x48_ls24"
+                wl, Ul, _ = build_workload(large, 0)
+                cl = ops.Context(wl["L"], wl["Ls"], wl["M5"], Ul)
+                del Ul
+                ops.dwf_autotune(cl, F32, 10)
+                bl = device_source(cl, wl, None, 0, dev)
+                line["mg_vs_fp64_large"] = mg_vs_fp64(cl, wl, bl, args.tol, MG_PARAMS_LARGE)
+                del bl
+                cl.close()
+            except Exception as e:
+                line["mg_vs_fp64_large"] = {"error": str(e)}
         if args.cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline_leg(args.workload)
             line["host"] = {"cpu_count": os.cpu_count(), "mem_available_gb": host_mem_available() / 1e9}
@@ -747,7 +766,11 @@ def run_rows(args):
     from paper_2103_05034_gb300 import layout, ops
     from paper_2103_05034_gb300._lib import F16S, F32, F64, SOLVE_MIXED_F32, SUBSPACE_BATCH
 
-    w, U, b = build_workload(args.workload, 0)
+    # the rows use host-side inputs: a paper-size workload is replaced by the
+    # 16^3 x 32 x 16 one
+    name = args.workload if int(np.prod(synth.WORKLOADS[args.workload]["L"])) <= (1 << 20) else "dwf_16x16x16x32_ls16"
+    args.workload = name
+    w, U, b = build_workload(name, 0)
     L, Ls, M5, mf = w["L"], w["Ls"], w["M5"], w["mf"]
     ctx = ops.Context(L, Ls, M5, U)
     ops.dwf_autotune(ctx, F32, 10)
@@ -1036,7 +1059,9 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-mg-compare", dest="mg_compare", action="store_false",
-                    help="skip the one-off FP64 RB-CG vs HDCR time-to-solution comparison")
+                    help="skip the one-off FP64 RB-CG vs HDCR time-to-solution comparisons")
+    ap.add_argument("--no-mg-large", dest="mg_large", action="store_false",
+                    help="skip the 24^3x48x24 comparison (about two minutes)")
     ap.add_argument("--kernel", default=None,
                     help="profile mode: dhop_f32, dhop_f64, dhop_f16, mpcdagmpc_f32, coarse_tf32 or coarse_f32 alone")
     ap.add_argument("--rows", action="store_true",

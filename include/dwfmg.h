@@ -94,7 +94,9 @@ typedef struct dwf_solve_stats {
   double seconds;            /* wall time of the call (host clock) */
   double setup_seconds;      /* mg_setup phases: subspace filter */
   double coarse_op_seconds;  /* mg_setup phases: coarse operator build */
-  int graph_replays;         /* mg_solve: V-cycles replayed from a CUDA graph */
+  int graph_replays;         /* mg_solve: V-cycles replayed from a CUDA graph;
+                                rbcg_solve, rbcg2_solve, rbcg_normal_solve: blocks
+                                of 8 CG iterations replayed from a CUDA graph */
   int pad_;
 } dwf_solve_stats;
 
@@ -418,6 +420,20 @@ int coarse_apply_status(dwf_coarse* coarse, void* stream);
  * initial value or after maxiter iterations (*iters receives the count). */
 int coarse_solve(dwf_coarse* coarse, void* e, const void* r, double tol, int maxiter, int* iters,
                  void* stream);
+/* Coarse solves for many right-hand sides (the multi-RHS use of the little
+ * Dirac operator, Sec. 3.1): CG on A^2 e_r = A rhs_r for nrhs independent
+ * FP32 right-hand sides at once (layout [nc][nb][nrhs], e the same), each
+ * with its own step lengths and FP64 scalars; every application of A covers
+ * all of them, on the tensor cores (prec DWF_TF32, the shapes coarse_apply
+ * accepts: nb = 32, nrhs 16 or 32 or 64) or on the CUDA cores (DWF_F32,
+ * nrhs dividing 256).  A right-hand side stops changing once its normal
+ * residual |A^2 e_r - A rhs_r| <= tol |A rhs_r| (checked every 8 iterations);
+ * iters (host, nrhs entries, may be NULL) receives the iteration at which each
+ * did.  The TF32 operator carries a relative error of about 5e-4, so tol
+ * below about 1e-3 is not reached with DWF_TF32 (DWF_ENOCONV after maxiter).
+ * Synchronises. */
+int coarse_solve_multi(dwf_coarse* coarse, void* e, const void* rhs, int nrhs, double tol, int maxiter,
+                       int* iters, int prec, void* stream);
 /* Red-black coarse solve (Sec. 5.3: the red-black coarse solver of the
  * physical-point runs): with even coarse extents the 9-point stencil couples
  * a coarse site only to itself and to the other coarse parity, so A e = r is

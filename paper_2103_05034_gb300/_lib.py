@@ -132,6 +132,7 @@ _SIGS = {
     "coarse_apply_status": (I, [P, P]),
     "coarse_solve": (I, [P, P, P, D, I, C.POINTER(C.c_int), P]),
     "coarse_solve_rb": (I, [P, P, P, D, I, C.POINTER(C.c_int), P]),
+    "coarse_solve_multi": (I, [P, P, P, I, D, I, C.POINTER(C.c_int), I, P]),
     "coarse_deflate": (I, [P, P, I, I, I, D, D, C.POINTER(D), P]),
     "coarse_export_deflation": (I, [P, P, C.POINTER(D), C.POINTER(C.c_int)]),
     "dwf_restrict": (I, [P, P, P, P, I, C.POINTER(C.c_int), I, I, P]),

@@ -713,6 +713,71 @@ static int cg_step_fused(dwf_ctx* c, void* x, void* r, const void* p, void* y, v
   return launch_hop(c, h2, prec, st, nparts);
 }
 
+// A block of CG iterations captured once as a CUDA graph and replayed (on a
+// private stream, ordered after and before the solver's stream by events);
+// the library's launch and byte counters advance by the block's own counts
+// at every replay.  If the capture cannot be made, the solve keeps plain
+// launches (state -1).
+struct CGGraph {
+  cudaStream_t gs = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0;
+  double bytes = 0;
+  int state = 0;  // 0: not built, 1: ready, -1: plain launches
+  template <class F>
+  void build(dwf_ctx* c, int n, F&& body) {
+    state = -1;
+    if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    const int64_t l0 = c->launches;
+    const double b0 = c->hop_bytes;
+    const std::string err_before = c->err;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    int rc = DWF_OK;
+    for (int k = 0; k < n && rc == DWF_OK; k++) rc = body(gs);
+    const cudaError_t ec = cudaStreamEndCapture(gs, &g);
+    launches = c->launches - l0;
+    bytes = c->hop_bytes - b0;
+    c->launches = l0;
+    c->hop_bytes = b0;
+    if (rc || ec != cudaSuccess || !g || cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      exec = nullptr;
+      c->err = err_before;
+      cudaGetLastError();
+      return;
+    }
+    cudaGraphDestroy(g);
+    state = 1;
+  }
+  int run(dwf_ctx* c, cudaStream_t st) {
+    DWF_CUDA(c, cudaEventRecord(e0, st));
+    DWF_CUDA(c, cudaStreamWaitEvent(gs, e0, 0));
+    DWF_CUDA(c, cudaGraphLaunch(exec, gs));
+    DWF_CUDA(c, cudaEventRecord(e1, gs));
+    DWF_CUDA(c, cudaStreamWaitEvent(st, e1, 0));
+    c->launches += launches;
+    c->hop_bytes += bytes;
+    return DWF_OK;
+  }
+  ~CGGraph() {
+    if (gs) cudaStreamSynchronize(gs);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (gs) cudaStreamDestroy(gs);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
 // CG on M_pc^dag M_pc x_e = rhs with FP64 reliable updates.  With bp set (the
 // red-black solve) the stopping residual is the Schur residual |b'_e - M_pc x|
 // / bnorm, which equals the full true residual after reconstruction; without
@@ -884,16 +949,34 @@ static int cg_core(dwf_ctx* c, double2* x_e, const CGBufs& B, double bnorm, doub
   int it = 0, last_reliable_it = 0;
   const int check_every = 8;
   bool converged = true_res <= tol;
-  while (!converged && it < maxiter) {
+  // One CG iteration is a fixed launch sequence on fixed buffers whose step
+  // lengths live in device scalars, so the check_every iterations between two
+  // host checks are captured once as a CUDA graph (after the first block has
+  // run with plain launches and sized every workspace) and replayed.
+  CGGraph graph;
+  auto one_iteration = [&](cudaStream_t s2) -> int {
     int np = 0;
-    rc = cg_step_fused(c, xin, rlo, p, B.ylo, B.olo, mfa, plo, st, &np, form, B.Ap);
-    if (rc) return rc;
-    rc = blas_finalize_mode(c, np, 1, S_RRNEW, 2, st);
-    if (rc) return rc;
-    rc = blas_cg_p(c, p, rlo, he, plo, S_BETA, st);
-    if (rc) return rc;
-    matmuls += 4;
-    it++;
+    int r = cg_step_fused(c, xin, rlo, p, B.ylo, B.olo, mfa, plo, s2, &np, form, B.Ap);
+    if (r) return r;
+    r = blas_finalize_mode(c, np, 1, S_RRNEW, 2, s2);
+    if (r) return r;
+    return blas_cg_p(c, p, rlo, he, plo, S_BETA, s2);
+  };
+  while (!converged && it < maxiter) {
+    if (it % check_every == 0 && it + check_every <= maxiter && it >= check_every && graph.state == 0)
+      graph.build(c, check_every, one_iteration);
+    if (it % check_every == 0 && it + check_every <= maxiter && graph.state == 1) {
+      rc = graph.run(c, st);
+      if (rc) return rc;
+      matmuls += 4 * check_every;
+      it += check_every;
+      S.graph_replays++;
+    } else {
+      rc = one_iteration(st);
+      if (rc) return rc;
+      matmuls += 4;
+      it++;
+    }
     if (it % check_every == 0 || it == maxiter) {
       rc = read_scalars(c, S_RR, 1, st);
       if (rc) return rc;

@@ -12,6 +12,7 @@ struct dwf_coarse {
   double2* A64;  // [nc][9][nb][nb]
   float2* A32;   // same layout, FP32
   float* At;     // tensor-core copy (real form, TF32, K-major), built on first use
+  float* At4;    // tensor-core copy (complex-split form per quad of sites), built on first use
   float* Bt;     // tensor-core right-hand sides (real form, TF32), per apply
   size_t Bt_bytes;
   int* err;      // device error flag of the tensor-core kernel (sticky)
@@ -39,8 +40,9 @@ int coarse_defl_guess(dwf_coarse* C, const float2* r, cudaStream_t st);
 void coarse_defl_free(dwf_coarse* C);
 
 
-int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, float** Bt,
-                    size_t* Bt_bytes, int nb, int nc, const int Lc[4], int nrhs, int* err_dev, cudaStream_t st);
+int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, float** At4,
+                    float** Bt, size_t* Bt_bytes, int nb, int nc, const int Lc[4], int nrhs, int* err_dev,
+                    cudaStream_t st);
 int coarse_cg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float2* A, const int Lc[4], int nc,
                          int nb, double tol, int maxiter, float2* work, double* part, int part_cap,
                          int* dev_small, int* acc, int* iters, cudaStream_t st, const float2* x0 = nullptr);

@@ -553,6 +553,7 @@ extern "C" int coarse_destroy(dwf_coarse* C) {
   if (C->A64) cudaFree(C->A64);
   if (C->A32) cudaFree(C->A32);
   if (C->At) cudaFree(C->At);
+  if (C->At4) cudaFree(C->At4);
   if (C->Bt) cudaFree(C->Bt);
   if (C->Arb) cudaFree(C->Arb);
   coarse_defl_free(C);
@@ -612,8 +613,8 @@ extern "C" int coarse_apply(dwf_coarse* C, void* out, const void* in, int nrhs, 
     return dwf_fail(c, DWF_ETIMEOUT, "tensor-core coarse apply: a bounded barrier wait gave up (earlier call)");
   }
   cudaGetLastError();  // cudaEventQuery's cudaErrorNotReady is not an error
-  int rc = coarse_apply_tc(c, (float2*)out, (const float2*)in, C->A32, &C->At, &C->Bt, &C->Bt_bytes, C->nb, C->g.nc, C->g.Lc, nrhs,
-                           C->err, st);
+  int rc = coarse_apply_tc(c, (float2*)out, (const float2*)in, C->A32, &C->At, &C->At4, &C->Bt, &C->Bt_bytes, C->nb,
+                           C->g.nc, C->g.Lc, nrhs, C->err, st);
   if (rc == DWF_EINVAL)
     return dwf_fail(c, rc, "tensor-core coarse apply needs nb = 32, an even number of coarse sites, nrhs 16/32/64");
   if (rc) return dwf_fail(c, rc, "tensor-core coarse apply");

@@ -258,6 +258,16 @@ def coarse_solve(coarse, e, r, tol, maxiter=1000):
     return it.value
 
 
+def coarse_solve_multi(coarse, e, rhs, nrhs, tol, maxiter=1000, prec=F32):
+    """CG on A^2 for nrhs right-hand sides at once ([nc][nb][nrhs] FP32);
+    prec F32 (CUDA cores) or TF32 (tensor cores).  Returns the per-rhs
+    iteration counts."""
+    its = (C.c_int * nrhs)()
+    check(lib().coarse_solve_multi(coarse.h, _ptr(e), _ptr(rhs), nrhs, tol, maxiter, its, prec, _stream()),
+          coarse.ctx.h)
+    return list(its)
+
+
 def coarse_solve_rb(coarse, e, r, tol, maxiter=1000):
     """Red-black coarse solve (CG on the even Schur complement squared); returns
     the iteration count."""

@@ -142,6 +142,8 @@ def test_rbcg_solution_parity(policy):
     assert st["true_residual"] == pytest.approx(res, rel=1e-3, abs=1e-14)
     xr, it, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
     assert rel(xg, xr) < 1e-7
+    # blocks of CG iterations replayed from a CUDA graph
+    assert st["graph_replays"] > 0
     # iteration counts of the two CGs agree closely in FP64
     if policy == SOLVE_F64:
         xo, it10, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-10)

@@ -677,3 +677,38 @@ def test_mg_solve_with_deflated_coarse_solver(mg_case):
     xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
     assert rel(x, xr) < 1e-6
     Gd.close()
+
+
+@pytest.mark.parametrize("prec_name", ["f32", "tf32"])
+def test_coarse_solve_multi(mg16, prec_name):
+    """CG on A^2 for 16 right-hand sides at once on the 16^3 multigrid's
+    coarse operator (the tensor-core stencil's solve-path caller): every
+    solution satisfies the stopping rule under the exported FP64 operator
+    (with the TF32 operator's error of about 5e-4 allowed for), and on the
+    CUDA cores the first two right-hand sides take the oracle's CG iteration
+    counts (to the 8-iteration granularity of the checks)."""
+    from paper_2103_05034_gb300._lib import TF32
+    ctx, G = mg16
+    C = G.coarse
+    nb, nrhs = C.nb, 16
+    prec = {"f32": F32, "tf32": TF32}[prec_name]
+    tol = 1e-4 if prec_name == "f32" else 2e-3
+    shape = tuple(C.Lc[::-1]) + (nb,)
+    Ast = np.moveaxis(C.export(), 1, 0).reshape((9,) + shape[:4] + (nb, nb))
+    r = synth.complex_gaussian(16, (C.nc, nb, nrhs))
+    rd = torch.from_numpy(layout.complex_to_real(r, F32).reshape(-1)).cuda()
+    e = torch.zeros_like(rd)
+    its = ops.coarse_solve_multi(C, e, rd, nrhs, tol, 5000, prec)
+    eg = layout.real_to_complex(e.double().cpu().numpy()).reshape(r.shape)
+    slack = 1.01 if prec_name == "f32" else 2.0
+    for k in range(nrhs):
+        Ar = coarse.coarse_apply(Ast, r[:, :, k].reshape(shape))
+        res = coarse.coarse_apply(Ast, coarse.coarse_apply(Ast, eg[:, :, k].reshape(shape))) - Ar
+        assert np.linalg.norm(res) <= slack * tol * np.linalg.norm(Ar) + (1e-3 if prec_name == "tf32" else 0) * \
+            np.linalg.norm(Ar), (k, its[k])
+    print(f"coarse_solve_multi {prec_name}: iterations {its}")
+    if prec_name == "f32":
+        for k in range(2):
+            _, it_or = coarse.coarse_cgnr(Ast, r[:, :, k].reshape(shape), tol, 5000)
+            slack_it = max(4, it_or // 20)
+            assert it_or - slack_it <= its[k] < it_or + 8 + slack_it
