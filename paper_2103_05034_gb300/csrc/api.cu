@@ -248,6 +248,15 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
     if (rc) return rc;
   }
   hp.partials = c->partials;
+  if (h.cheb_tp) {
+    hp.cheb_mode = 1;
+    hp.cheb_x = h.cheb_x;
+    hp.cheb_tp = h.cheb_tp;
+    hp.cheb_acc = h.cheb_acc;
+    hp.cheb_ta = h.cheb_ta;
+    hp.cheb_tb = h.cheb_tb;
+    hp.cheb_cacc = h.cheb_cacc;
+  }
   if (h.cg_x) {
     hp.cg_mode = 1;
     hp.cg_x = h.cg_x;
@@ -566,17 +575,25 @@ extern "C" int dwf_mpcdag_mpc(dwf_ctx* c, void* out, const void* in, double mf, 
 
 // Full-lattice D_DW (or D_DW^dag, or H_DW = Gamma_5 D_DW when g5 = 1) of nrhs full fields.
 int ddw_apply(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int g5, int prec,
-              int nrhs, cudaStream_t st) {
+              int nrhs, cudaStream_t st, const ChebFuse* cf) {
   const int64_t he = half_elems(c);
   const size_t cb = dwf_complex_bytes(prec);
   for (int po = 0; po < 2; po++) {
-    HopLaunch h = hop_base((char*)out + po * he * cb, (const char*)in + (1 - po) * he * cb, po, dagger,
-                           nrhs, -0.5);
+    HopLaunch h = hop_base(cf ? nullptr : (char*)out + po * he * cb, (const char*)in + (1 - po) * he * cb, po,
+                           dagger, nrhs, -0.5);
     h.rhs_stride = 2 * he;
     h.aux = (const char*)in + po * he * cb;
     h.aux_mode = dagger ? 3 : 2;
     h.mf = mf;
     h.g5r5 = g5;
+    if (cf) {
+      h.cheb_x = (const char*)cf->x + po * he * cb;
+      h.cheb_tp = (char*)cf->tp + po * he * cb;
+      h.cheb_acc = cf->acc ? (char*)cf->acc + po * he * cb : nullptr;
+      h.cheb_ta = cf->ta;
+      h.cheb_tb = cf->tb;
+      h.cheb_cacc = cf->cacc;
+    }
     int rc = launch_hop(c, h, prec, st, nullptr);
     if (rc) return rc;
   }

@@ -19,8 +19,8 @@ namespace {
 constexpr int MT = 256;
 constexpr int MBLK = 304;  // two CTAs per SM
 
-// part[b][r] (+ width) = per-CTA sums over rows of |v|^2 (width 1) or of
-// the two products |v|^2 and Re <w, v> ... here only |v|^2 is needed.
+// part[b][r] = the sum over CTA b's rows of |v[row][r]|^2, for every
+// right-hand side r (thread t takes r = t mod nrhs and every (256/nrhs)-th row).
 __global__ void __launch_bounds__(MT) k_mnorm(const float2* __restrict__ v, long long rows, int nrhs, double* part) {
   __shared__ double sh[MT];
   const int r = threadIdx.x % nrhs, lane_rows = MT / nrhs, rl = threadIdx.x / nrhs;

@@ -55,6 +55,14 @@ struct HopParams {
   const double* cg_alpha;  // device scalars, cg_alpha[rhs * cg_astride]
   int cg_astride;          // 0: one alpha for every rhs
   int cg_x32;              // x stored in FP32 (with FP16-storage r and p)
+  // fused Chebyshev recurrence step (cheb_mode = 1) instead of storing the
+  // operator output v (after the Gamma_5 store mapping):
+  //   tp = ta v + tb x - tp;  acc += cacc tp (acc may be null)
+  int cheb_mode;
+  const void* cheb_x;
+  void* cheb_tp;
+  void* cheb_acc;
+  double cheb_ta, cheb_tb, cheb_cacc;
   double m[DWF_MAX_RHS];
   double kappa[DWF_MAX_RHS];
   double dls1[DWF_MAX_RHS];
@@ -619,6 +627,32 @@ __global__ void __launch_bounds__(LS* SB* RY, (HopMinBlocks<LS, SB * RY, REGS>::
           st_c(xs + c * LS, xv);
         st_c(rs + c * LS, rv);
         v[c] = rv;
+      }
+    }
+  } else if (active && p.cheb_mode) {
+    const size_t base = (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS;
+    const int so = p.g5r5 ? LS - 1 - s : s;
+    const S* cx = (const S*)p.cheb_x + base;
+    S* ct = (S*)p.cheb_tp + base;
+    S* ca = p.cheb_acc ? (S*)p.cheb_acc + base : nullptr;
+    const R ta = (R)p.cheb_ta, tb = (R)p.cheb_tb, cc = (R)p.cheb_cacc;
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      cpx<R> o = v[c];
+      if (p.g5r5 && c >= 6) {
+        o.re = -o.re;
+        o.im = -o.im;
+      }
+      const cpx<R> xv = ld_c(cx + c * LS + so), tv = ld_c(ct + c * LS + so);
+      cpx<R> w;
+      w.re = fma(ta, o.re, fma(tb, xv.re, -tv.re));
+      w.im = fma(ta, o.im, fma(tb, xv.im, -tv.im));
+      st_c(ct + c * LS + so, w);
+      if (ca) {
+        cpx<R> av = ld_c(ca + c * LS + so);
+        av.re = fma(cc, w.re, av.re);
+        av.im = fma(cc, w.im, av.im);
+        st_c(ca + c * LS + so, av);
       }
     }
   } else if (active) {

@@ -449,6 +449,38 @@ __global__ void __launch_bounds__(LS / 2 * SB, (HopMinBlocks<LS / 2, SB, REGS>::
         vi[c] = ri;
       }
     }
+  } else if (active && p.cheb_mode) {
+    // tp = ta v + tb x - tp; acc += cacc tp, on the pair's store positions
+    const size_t base = (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS;
+    const int so = p.g5r5 ? LS - 2 - s0 : s0;
+    const S* cx = (const S*)p.cheb_x + base;
+    S* ct = (S*)p.cheb_tp + base;
+    S* ca = p.cheb_acc ? (S*)p.cheb_acc + base : nullptr;
+    const float ta = (float)p.cheb_ta, tb = (float)p.cheb_tb, cc = (float)p.cheb_cacc;
+    const f2p TA = pk2(ta, ta), TB = pk2(tb, tb), CC = pk2(cc, cc), NEG = pk2(-1.f, -1.f);
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      f2p r = vr[c], i = vi[c];
+      if (p.g5r5) {
+        r = swp2(r);
+        i = swp2(i);
+        if (c >= 6) {
+          r = mul2(NEG, r);
+          i = mul2(NEG, i);
+        }
+      }
+      f2p xr, xi, tr, ti;
+      PairIO<P>::ld(cx + c * LS + so, xr, xi);
+      PairIO<P>::ld(ct + c * LS + so, tr, ti);
+      const f2p wr = fma2(TA, r, fma2(TB, xr, mul2(NEG, tr)));
+      const f2p wi = fma2(TA, i, fma2(TB, xi, mul2(NEG, ti)));
+      PairIO<P>::st(ct + c * LS + so, wr, wi);
+      if (ca) {
+        f2p ar, ai;
+        PairIO<P>::ld(ca + c * LS + so, ar, ai);
+        PairIO<P>::st(ca + c * LS + so, fma2(CC, wr, ar), fma2(CC, wi, ai));
+      }
+    }
   } else if (active) {
     S* out = (S*)p.out + (size_t)rhs * p.rhs_stride + (size_t)site * 12 * LS;
     if (p.g5r5) {

@@ -175,6 +175,21 @@ struct HopLaunch {
   const double* cg_alpha;
   int cg_alpha_stride;  // doubles between consecutive rhs' alpha (0: shared)
   int cg_x32;          // x is FP32 whatever the field precision (FP16-storage CG)
+  // fused Chebyshev recurrence step instead of storing out (cheb_tp set):
+  // tp = ta out + tb x - tp, acc += cacc tp (acc may be null); same layout as out
+  const void* cheb_x;
+  void* cheb_tp;
+  void* cheb_acc;
+  double cheb_ta, cheb_tb, cheb_cacc;
+};
+
+// The Chebyshev step fused into the last hopping launch of an operator
+// application (ddw_apply): tp = ta (A x) + tb x - tp; acc += cacc tp.
+struct ChebFuse {
+  const void* x;
+  void* tp;
+  void* acc;
+  double ta, tb, cacc;
 };
 
 int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* nblocks);
@@ -221,9 +236,10 @@ int blas_cheb_step(dwf_ctx* c, void* tp, const void* Ax, const void* x, double t
 // y += (ar + i ai) x, precisions (F64|F32) x (F64|F32)
 int blas_caxpy(dwf_ctx* c, double ar, double ai, const void* x, int px, void* y, int py, int64_t n,
                cudaStream_t st);
-// Full-lattice D_DW / D_DW^dag / H_DW (g5 = 1) on nrhs full fields (api.cu).
+// Full-lattice D_DW / D_DW^dag / H_DW (g5 = 1) on nrhs full fields (api.cu);
+// with cf the result is not stored but folded into cf's Chebyshev step.
 int ddw_apply(dwf_ctx* c, void* out, const void* in, const double* mf, int dagger, int g5, int prec,
-              int nrhs, cudaStream_t st);
+              int nrhs, cudaStream_t st, const ChebFuse* cf = nullptr);
 int norm2_dev(dwf_ctx* c, const void* a, int64_t n, int prec, int dst, cudaStream_t st);
 // M_pc (dagger 0) or M_pc^dag (1) of nrhs even fields; tmp receives the odd
 // intermediate M_oo^-1 M_oe in (or its dagger form); reduce = |out|^2 partials.

@@ -53,20 +53,23 @@ enum { MW_T0 = 16, MW_T1, MW_T2, MW_T3, MW_T4, MW_T5, MW_T6, MW_T7, MW_T8, MW_T9
 
 void* ws(dwf_ctx* c, int slot, size_t bytes) { return dwf_workspace(c, slot, bytes); }
 
-// D^dag D on nrhs full fields via tmp.
-int mdagm(dwf_ctx* c, void* out, const void* in, void* tmp, double mf, int prec, int nrhs, cudaStream_t st) {
+// D^dag D on nrhs full fields via tmp; with cf the result feeds cf's
+// Chebyshev step instead of out (fused into the last hopping launches).
+int mdagm(dwf_ctx* c, void* out, const void* in, void* tmp, double mf, int prec, int nrhs, cudaStream_t st,
+          const ChebFuse* cf = nullptr) {
   std::vector<double> m(nrhs, mf);
   int rc = ddw_apply(c, tmp, in, m.data(), 0, 0, prec, nrhs, st);
   if (rc) return rc;
-  return ddw_apply(c, out, tmp, m.data(), 1, 0, prec, nrhs, st);
+  return ddw_apply(c, out, tmp, m.data(), 1, 0, prec, nrhs, st, cf);
 }
 
-// H_DW^2 on nrhs full fields via tmp.
-int hsq(dwf_ctx* c, void* out, const void* in, void* tmp, double mf, int prec, int nrhs, cudaStream_t st) {
+// H_DW^2 on nrhs full fields via tmp (cf as for mdagm).
+int hsq(dwf_ctx* c, void* out, const void* in, void* tmp, double mf, int prec, int nrhs, cudaStream_t st,
+        const ChebFuse* cf = nullptr) {
   std::vector<double> m(nrhs, mf);
   int rc = ddw_apply(c, tmp, in, m.data(), 0, 1, prec, nrhs, st);
   if (rc) return rc;
-  return ddw_apply(c, out, tmp, m.data(), 0, 1, prec, nrhs, st);
+  return ddw_apply(c, out, tmp, m.data(), 0, 1, prec, nrhs, st, cf);
 }
 
 int check_finite(dwf_ctx* c, const void* v, int64_t n, int prec, cudaStream_t st, double* norm2) {
@@ -100,9 +103,9 @@ int filter_core(dwf_ctx* c, void* out, const void* in, int nrhs, double lo, doub
   rc = blas_axpbypcz(c, a, ax, b, tp, 0.0, tc, n, prec, st);  // T1 = x(A) T0
   if (rc) return rc;
   for (int k = 2; k <= order; k++) {
-    rc = mdagm(c, ax, tc, tmp, mf, prec, nrhs, st);
-    if (rc) return rc;
-    rc = blas_cheb_step(c, tp, ax, tc, 2 * a, 2 * b, nullptr, 0.0, n, prec, st);  // tp <- T_k
+    // tp <- T_k = 2 x(A) T_{k-1} - T_{k-2}, the step fused into the last hops
+    const ChebFuse cf = {tc, tp, nullptr, 2 * a, 2 * b, 0.0};
+    rc = mdagm(c, ax, tc, tmp, mf, prec, nrhs, st, &cf);
     if (rc) return rc;
     void* t = tp;
     tp = tc;
@@ -392,9 +395,8 @@ extern "C" int cheby_recursive_basis(dwf_ctx* c, void* phi, const void* eta, dou
         if (rc) return rc;
         rc = blas_axpbypcz(c, a, ax, b, tp, 0.0, tc, n, prec, st);
       } else {
-        rc = mdagm(c, ax, tc, tmp, mf, prec, 1, st);
-        if (rc) return rc;
-        rc = blas_cheb_step(c, tp, ax, tc, 2 * a, 2 * b, nullptr, 0.0, n, prec, st);
+        const ChebFuse cf = {tc, tp, nullptr, 2 * a, 2 * b, 0.0};
+        rc = mdagm(c, ax, tc, tmp, mf, prec, 1, st, &cf);
         void* t = tp;
         tp = tc;
         tc = t;
@@ -740,11 +742,11 @@ int smoother(dwf_mg* G, void* z, const void* r, cudaStream_t st, double* nH) {
   rc = blas_axpby(c, cf[1], tc, DWF_F32, 1.0, z, DWF_F32, n, st);
   if (rc) return rc;
   for (int j = 2; j < N; j++) {
-    rc = hsq(c, ax, tc, tmp, G->p.mf, DWF_F32, 1, st);
+    // tp <- T_j, z += c_j T_j: the recurrence step fused into the last hops of H^2
+    const ChebFuse fz = {tc, tp, z, 2 * xa, 2 * xb, cf[j]};
+    rc = hsq(c, ax, tc, tmp, G->p.mf, DWF_F32, 1, st, &fz);
     if (rc) return rc;
     *nH += 2;
-    rc = blas_cheb_step(c, tp, ax, tc, 2 * xa, 2 * xb, z, cf[j], n, DWF_F32, st);
-    if (rc) return rc;
     void* t = tp;
     tp = tc;
     tc = t;
