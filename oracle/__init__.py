@@ -18,6 +18,9 @@ Modules:
   coarse  blocking, chirality projection, little Dirac operator (Sections 3.1,
           3.4)
   mg      composite V(1,1) preconditioner (Section 3.3) and flexible GCR
+  hybrid  the three-level hybrid multigrid (Algorithm F, Section 4): 4D D_W
+          coarsening, the coarse domain wall operator, H_DW coarsening of
+          the coarse space, fixed-iteration W-cycle
   force   pseudofermion action and its gauge-link derivative (HMC context,
           Section 6; derived from first principles)
 """

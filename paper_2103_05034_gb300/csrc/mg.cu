@@ -487,12 +487,28 @@ extern "C" int coarse_build(dwf_ctx* c, const void* basis, int nb, int nplus, co
     coarse_destroy(C);
     return dwf_fail(c, DWF_ENOMEM, "coarse operator");
   }
-  // H_DW phi_k and its eight face terms for a group of at most eight basis
-  // vectors at a time (bounded workspace: two groups of full fields); the
-  // block inner products with every basis vector fill those columns of A.
+  // H_DW phi_k and its eight face terms for a group of basis vectors at a
+  // time (workspace: two groups of full fields); the block inner products
+  // with every basis vector fill those columns of A.  Each group re-reads the
+  // whole basis once per direction, so the group is as wide as free device
+  // memory allows (all nb vectors at small volumes, 8 at the largest).
   const int64_t n = full_elems(c);
-  const int ngmax = nb < 8 ? nb : 8;
   const size_t cbytes = dwf_complex_bytes(prec);
+  int ngmax = nb < 8 ? nb : 8;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+      const size_t margin = (size_t)4 << 30;
+      for (int cand = nb; cand > ngmax; cand = (cand + 1) / 2) {
+        if (2 * (size_t)n * cand * cbytes + margin < fr) {
+          ngmax = cand;
+          break;
+        }
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
   const size_t fb = (size_t)n * ngmax * cbytes;
   void* H = ws(c, MW_T8, fb);
   void* W = ws(c, MW_T9, fb);
