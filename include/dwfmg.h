@@ -540,6 +540,75 @@ int mg_precondition(dwf_mg* mg, void* out, const void* in, void* stream);
  * fields, host or device.  stats->fine_matmuls counts H_DW applications. */
 int mg_solve(dwf_mg* mg, void* x, const void* b, double tol, dwf_solve_stats* stats, void* stream);
 
+/* ------------------------------------------------------------------ hybrid three-level multigrid */
+
+/* Algorithm F (Sec. 4 and its table; Hybrid-M^dag M): the first coarsening
+ * represents the 4D Wilson operator D_W (Eq. 1) on 4D blocks with the fifth
+ * dimension kept (blocks b^4 x 1); by the chirality of the 4D basis the level-1
+ * operator is a coarse domain wall operator
+ *   M_1 v(x,k,s) = sum_s' K_chi_k[s,s'] v(x,k,s') + sum_d sum_k' B_d(x)[k,k'] v(x+d,k',s),
+ * K_chi the Ls x Ls fifth-dimension matrix of Eq. (4) on chirality chi_k (+1
+ * for k < nbasis4/2) and B = P4^dag (-1/2 D_hop) P4 the 9-point stencil of the
+ * hopping term on the 4D basis.  The second coarsening represents
+ * H_1 = Gamma5_1 M_1 (Gamma5_1 v(x,k,s) = chi_k v(x,k,Ls-1-s)) on blocks of one
+ * level-1 site spanning all s, a 9-point stencil with nbasis1 x nbasis1
+ * blocks solved like the HDCR coarse operator (dwf_mg_params' coarse_*).
+ * The fine outer solve is that of mg_solve; its V(1,1) coarse correction is
+ * P1 e, e from kcycle iterations of flexible GCR on H_1 e = P1^dag r (no
+ * tolerance test: a fixed W-cycle), each iteration preconditioned by a
+ * level-1 V(1,1) whose coarse-coarse correction is the level-2 solve.
+ *
+ * Level-1 vectors: FP32 complex [nc1][nbasis4][Ls][nvec] (coarse site of the
+ * 4D blocking, 4D basis index, s, vector), nc1 = prod(L/block).  Level-2
+ * vectors: FP32 complex [nc1][nbasis1]. */
+typedef struct dwf_hybrid_params {
+  int block[4];          /* 4D blocks of the D_W coarsening (Algorithm F: 2^4) */
+  int nbasis4;           /* 4D basis vectors: 4, 8, 16 or 24 (half of each chirality) */
+  double mass4;          /* Wilson mass m of the filter operator D_W(m)^dag D_W(m), > -4 */
+  double lambda_lo4;     /* batch filter T_order4 on [lambda_lo4, lambda_max4] */
+  double lambda_max4;
+  int order4;
+  int nbasis1;           /* level-2 basis vectors (even, <= 64; half of each Gamma5_1 chirality) */
+  double lambda_lo1;     /* batch filter T_order1 of H_1^2 on [lambda_lo1, lambda_max1] */
+  double lambda_max1;
+  int order1;
+  double smooth1_lo;     /* level-1 smoother S_cheb([lo,hi],N) on H_1 (N = 0: none, */
+  double smooth1_hi;     /*   only with kcycle = 1: without a smoother the level-1 */
+  int smooth1_order;     /*   preconditioner K obeys K H_1 K = K) */
+  int kcycle;            /* GCR iterations of the level-1 solve (2: the W-cycle) */
+} dwf_hybrid_params;
+
+/* Build the three levels: eta4 = nbasis4 Gaussian 4D fields (FP64, the layout
+ * of a full field with Ls = nbasis4: [parity][Vh][4][3][nbasis4], vector
+ * innermost), filtered in FP32 by T_order4 of D_W^dag D_W, projected with
+ * (1 +- gamma_5)/2 (first half +), block orthonormalised and the stencil B
+ * built in FP64; eta1 = nbasis1 Gaussian level-1 vectors (FP64
+ * [nc1][nbasis4][Ls][nbasis1]) filtered in FP32 by T_order1 of H_1^2,
+ * projected with (1 +- Gamma5_1)/2, orthonormalised per level-1 site (FP64
+ * arithmetic, FP32 storage), and the level-2 stencil built (FP64 sums).
+ * params supplies mf, the fine smoother, nkrylov, maxiter and the coarse
+ * (level-2) solver and its deflation; its block, nbasis and subspace fields
+ * are not used.  The solve runs without CUDA-graph replay.  Synchronises. */
+int mg_setup_hybrid(dwf_ctx* ctx, const dwf_mg_params* params, const dwf_hybrid_params* hybrid,
+                    const void* eta4, const void* eta1, dwf_mg** mg, void* stream);
+/* Copies of the hybrid setup's parts (host or device out):
+ *   what 0: the 4D basis, FP64 [2][Vh][12][nbasis4];
+ *   what 1: B, FP64 [nc1][9][nbasis4][nbasis4] (the coarse_export layout);
+ *   what 2: the level-2 basis, FP32 [nc1][nbasis4][Ls][nbasis1];
+ *   what 3: the level-2 stencil, FP64 [nc1][9][nbasis1][nbasis1].
+ * DWF_EINVAL for a setup that is not hybrid. */
+int mg_hybrid_export(const dwf_mg* mg, int what, void* out);
+/* The hybrid setup's level operators on device vectors (stream-ordered):
+ *   op 0: out = M_1 in, nvec level-1 vectors;  op 1: out = H_1 in;
+ *   op 2: out = P1^dag in (in: nvec FP32 full fine fields; out: level-1);
+ *   op 3: out = P1 in (in: level-1; out: nvec FP32 full fields);
+ *   op 4: out = P2^dag in (nvec = 1; out: level-2 vector);
+ *   op 5: out = P2 in (nvec = 1; in: level-2 vector);
+ *   op 6: out = the fixed-iteration level-1 solve of H_1 out = in (nvec = 1;
+ *         synchronises).
+ * out must not alias in. */
+int mg_hybrid_level1(dwf_mg* mg, int op, void* out, const void* in, int nvec, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

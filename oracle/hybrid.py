@@ -45,10 +45,12 @@ Readings (the paper does not spell these out):
     H_1 e = P1^dag r.
   * Level-1 solve: kcycle (2) iterations of flexible GCR on H_1 from zero
     with no tolerance test, each preconditioned by a level-1 V(1,1): a
-    Chebyshev smoother on H_1 (order 0: none) around the coarse-coarse
-    correction P2 A_2^-1 P2^dag, A_2^-1 by CG on A_2^2 to the coarse
-    tolerance.  So every fine outer iteration makes kcycle coarse-coarse
-    solves.
+    Chebyshev smoother on H_1 around the coarse-coarse correction
+    P2 A_2^-1 P2^dag, A_2^-1 by CG on A_2^2 to the coarse tolerance.  So
+    every fine outer iteration makes kcycle coarse-coarse solves.  The
+    smoother may be left out (order 0) only with kcycle = 1: without it the
+    preconditioner K = P2 A_2^-1 P2^dag satisfies K H_1 K = K, and a second
+    GCR direction would vanish.
 
 Layouts: 4D fields (T,Z,Y,X,4,3); level-1 fields (Tc,Zc,Yc,Xc, nb4, Ls)
 (basis index, then s); level-2 vectors (Tc,Zc,Yc,Xc, nb2).
@@ -251,6 +253,11 @@ class Hybrid:
         self.nplus4 = len(b4) // 2
         self.smooth, self.smooth1 = smooth, smooth1
         self.kcycle, self.coarse_tol, self.coarse_maxiter = kcycle, coarse_tol, coarse_maxiter
+        if kcycle > 1 and smooth1[2] == 0:
+            # without a level-1 smoother the preconditioner is K = P2 A_2^-1 P2^dag
+            # and K H_1 K = K (A_2 = P2^dag H_1 P2), so the second GCR direction
+            # vanishes in exact arithmetic and only rounding would be amplified
+            raise ValueError("kcycle > 1 needs a level-1 smoother")
 
     def H1(self, v):
         return level1_herm(self.B, v, self.M5, self.mf, self.nplus4)

@@ -48,6 +48,14 @@ class MGParams(C.Structure):
                 ("coarse_lanczos", C.c_int), ("coarse_cheb_order", C.c_int), ("coarse_cheb_lo", C.c_double)]
 
 
+class HybridParams(C.Structure):
+    _fields_ = [("block", C.c_int * 4), ("nbasis4", C.c_int), ("mass4", C.c_double),
+                ("lambda_lo4", C.c_double), ("lambda_max4", C.c_double), ("order4", C.c_int),
+                ("nbasis1", C.c_int), ("lambda_lo1", C.c_double), ("lambda_max1", C.c_double),
+                ("order1", C.c_int), ("smooth1_lo", C.c_double), ("smooth1_hi", C.c_double),
+                ("smooth1_order", C.c_int), ("kcycle", C.c_int)]
+
+
 def header_functions():
     """Names of the functions declared in include/dwfmg.h."""
     txt = open(HEADER).read()
@@ -144,5 +152,8 @@ _SIGS = {
     "mg_smooth": (I, [P, P, P, P]),
     "mg_precondition": (I, [P, P, P, P]),
     "mg_solve": (I, [P, P, P, D, C.POINTER(SolveStats), P]),
+    "mg_setup_hybrid": (I, [P, C.POINTER(MGParams), C.POINTER(HybridParams), P, P, C.POINTER(P), P]),
+    "mg_hybrid_export": (I, [P, I, P]),
+    "mg_hybrid_level1": (I, [P, I, P, P, I, P]),
 }
 

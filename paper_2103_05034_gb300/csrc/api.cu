@@ -168,6 +168,48 @@ extern "C" int dwf_ctx_create(dwf_ctx** out, const int L[4], int Ls, double M5, 
   return DWF_OK;
 }
 
+// A context on the same lattice and links with another fifth-dimension
+// extent (used to apply the 4D hopping term to a batch of ls 4D fields stored
+// as the s-slices of one field).
+int dwf_ctx_clone_ls(const dwf_ctx* src, int ls, dwf_ctx** out, cudaStream_t st) {
+  *out = nullptr;
+  if (ls != 4 && ls != 8 && ls != 16 && ls != 24) return DWF_EINVAL;
+  dwf_ctx* c = new (std::nothrow) dwf_ctx();
+  if (!c) return DWF_ENOMEM;
+  c->g = src->g;
+  c->g.Ls = ls;
+  c->M5 = src->M5;
+  c->device = src->device;
+  int rc = DWF_OK;
+  const size_t lb = (size_t)c->g.Vh * 72;
+  for (int p = 0; p < 2 && rc == DWF_OK; p++) {
+    if (cudaMalloc(&c->links64[p], lb * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc(&c->links32[p], lb * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      rc = DWF_ENOMEM;
+      break;
+    }
+    if (cudaMemcpyAsync(c->links64[p], src->links64[p], lb * sizeof(double2), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->links32[p], src->links32[p], lb * sizeof(float2), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+      rc = DWF_ECUDA;
+  }
+  if (rc == DWF_OK && (cudaMalloc(&c->dscal, S_NSCAL * sizeof(double)) != cudaSuccess ||
+                       cudaMallocHost(&c->hscal, S_NSCAL * sizeof(double)) != cudaSuccess)) {
+    cudaGetLastError();
+    rc = DWF_ENOMEM;
+  }
+  if (rc == DWF_OK) rc = dwf_reserve_partials(c, 1 << 16);
+  if (rc == DWF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = DWF_ECUDA;
+  if (rc != DWF_OK) {
+    dwf_ctx_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return DWF_OK;
+}
+
 extern "C" int dwf_ctx_destroy(dwf_ctx* c) {
   if (!c) return DWF_OK;
   for (int p = 0; p < 2; p++) {

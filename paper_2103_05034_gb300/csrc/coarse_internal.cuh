@@ -40,6 +40,14 @@ int coarse_defl_guess(dwf_coarse* C, const float2* r, cudaStream_t st);
 void coarse_defl_free(dwf_coarse* C);
 
 
+// The coarse solves of the V-cycle on one FP32 right-hand side (mg.cu): CG on
+// A^2 (from the deflation guess when a deflation space is set) and red-black
+// CG on the even Schur complement squared; stream-ordered, the iteration
+// count is read back unless cg_acc is set.
+int coarse_cg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxiter, int* iters, cudaStream_t st);
+int coarse_rb_ready(dwf_coarse* C, cudaStream_t st);
+int coarse_rbcg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxiter, int* iters, cudaStream_t st);
+
 int coarse_apply_tc(dwf_ctx* c, float2* out, const float2* in, const float2* A32, float** At, float** At4,
                     float** Bt, size_t* Bt_bytes, int nb, int nc, const int Lc[4], int nrhs, int* err_dev,
                     cudaStream_t st);
@@ -52,3 +60,15 @@ int coarse_rbcg_persistent(dwf_ctx* c, float2* e, const float2* rhs, const float
                            int nb, double tol, int maxiter, float2* work, double* part, int part_cap, int* dev_small,
                            int* acc, int* iters, cudaStream_t st);
 
+// Hybrid three-level multigrid (hybrid.cu): the levels below the fine one.
+struct dwf_hybrid;
+int hybrid_build(dwf_ctx* c, const dwf_mg_params* p, const dwf_hybrid_params* hp, const void* eta4, const void* eta1,
+                 dwf_hybrid** out, cudaStream_t st);
+void hybrid_free(dwf_hybrid* H);
+// x += P1 e, e from the fixed-iteration level-1 solve of H_1 e = P1^dag r (FP32 full fields).
+int hybrid_correction(dwf_hybrid* H, void* x, const void* r, cudaStream_t st, int* ncoarse);
+int hybrid_level1_op(dwf_hybrid* H, int op, void* out, const void* in, int nvec, cudaStream_t st);
+int hybrid_export(const dwf_hybrid* H, int what, void* out);
+dwf_coarse* hybrid_coarse(dwf_hybrid* H);
+double hybrid_setup_seconds(const dwf_hybrid* H);
+double hybrid_coarse_seconds(const dwf_hybrid* H);

@@ -142,6 +142,8 @@ int dwf_cuda_check(dwf_ctx* c, cudaError_t e, const char* where);
   } while (0)
 
 size_t dwf_complex_bytes(int prec);
+// A context on the same lattice and links with fifth-dimension extent ls (api.cu).
+int dwf_ctx_clone_ls(const dwf_ctx* src, int ls, dwf_ctx** out, cudaStream_t st);
 void* dwf_workspace(dwf_ctx* c, int slot, size_t bytes);
 void dwf_ws_release(dwf_ctx* c, int slot);  // free one workspace slot (mg.cu)
 bool dwf_is_device_ptr(const void* p);

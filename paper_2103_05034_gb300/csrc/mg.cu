@@ -17,6 +17,7 @@ struct dwf_mg {
   BlockGeom g;
   float2* basis;  // nb full FP32 fields
   dwf_coarse* coarse;
+  dwf_hybrid* hyb;  // the levels of the hybrid three-level multigrid, or null
   double lambda_max_used;
   double setup_seconds, coarse_op_seconds;
 };
@@ -286,8 +287,6 @@ int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cud
   return DWF_OK;
 }
 
-namespace {
-
 // CG on A^2 e = A r (one right-hand side, FP32 vectors), stopping when the
 // normal-equation residual falls below tol times its initial value: one
 // persistent cooperative launch (coarse_cg.cu).
@@ -345,8 +344,6 @@ int coarse_rbcg(dwf_coarse* C, float2* e, const float2* rc, double tol, int maxi
   return coarse_rbcg_persistent(C->ctx, e, rc, C->Arb, C->g.Lc, C->g.nc, C->nb, tol, maxiter, (float2*)work,
                                 (double*)part, part_cap, (int*)small, C->cg_acc, iters, st);
 }
-
-}  // namespace
 
 // ====================================================================== ABI
 
@@ -772,22 +769,12 @@ int smoother(dwf_mg* G, void* z, const void* r, cudaStream_t st, double* nH) {
 
 // V(1,1) of Eqs. (26)-(28) on residual r0 with x0 = 0: x1 = S r0, r1 = r0 - H x1,
 // x2 = x1 + P A^-1 P^dag r1, r2 = r0 - H x2, x3 = x2 + S r2.  FP32.
-int vcycle(dwf_mg* G, void* x, const void* r0, cudaStream_t st, double* nH, int* ncoarse) {
+// The HDCR coarse correction x += P A^-1 P^dag r1 (block restriction, coarse
+// solve, block prolongation).
+int coarse_correction(dwf_mg* G, void* x, const void* rr, cudaStream_t st, int* ncoarse) {
   dwf_ctx* c = G->ctx;
   dwf_coarse* C = G->coarse;
-  const int64_t n = full_elems(c);
-  const size_t bytes = n * sizeof(float2);
-  void* rr = ws(c, MW_T5, bytes);
-  void* s2 = ws(c, MW_T6, bytes);
-  if (!rr || !s2) return dwf_fail(c, DWF_ENOMEM, "vcycle workspace");
-  const double mf[1] = {G->p.mf};
-  int rc = smoother(G, x, r0, st, nH);
-  if (rc) return rc;
-  rc = ddw_apply(c, rr, x, mf, 0, 1, DWF_F32, 1, st);
-  if (rc) return rc;
-  *nH += 1;
-  rc = blas_axpby(c, 1.0, r0, DWF_F32, -1.0, rr, DWF_F32, n, st);  // r1
-  if (rc) return rc;
+  int rc = DWF_OK;
   const int64_t ncv = (int64_t)C->g.nc * C->nb;
   double2* t64 = (double2*)ws(c, MW_T7, ncv * sizeof(double2));
   void *rc32, *ec32;
@@ -805,7 +792,26 @@ int vcycle(dwf_mg* G, void* x, const void* r0, cudaStream_t st, double* nH, int*
   *ncoarse += it;
   rc = blas_copy(c, t64, DWF_F64, ec32, DWF_F32, ncv, st);
   if (rc) return rc;
-  rc = block_combine(c, C->g, x, 1, DWF_F32, G->basis, C->nb, DWF_F32, t64, C->nb, 1, 1, st);  // x2 = x1 + P e
+  return block_combine(c, C->g, x, 1, DWF_F32, G->basis, C->nb, DWF_F32, t64, C->nb, 1, 1, st);
+}
+
+int vcycle(dwf_mg* G, void* x, const void* r0, cudaStream_t st, double* nH, int* ncoarse) {
+  dwf_ctx* c = G->ctx;
+  const int64_t n = full_elems(c);
+  const size_t bytes = n * sizeof(float2);
+  void* rr = ws(c, MW_T5, bytes);
+  void* s2 = ws(c, MW_T6, bytes);
+  if (!rr || !s2) return dwf_fail(c, DWF_ENOMEM, "vcycle workspace");
+  const double mf[1] = {G->p.mf};
+  int rc = smoother(G, x, r0, st, nH);
+  if (rc) return rc;
+  rc = ddw_apply(c, rr, x, mf, 0, 1, DWF_F32, 1, st);
+  if (rc) return rc;
+  *nH += 1;
+  rc = blas_axpby(c, 1.0, r0, DWF_F32, -1.0, rr, DWF_F32, n, st);  // r1
+  if (rc) return rc;
+  // x2 = x1 + P e: the HDCR coarse solve, or the hybrid levels (Algorithm F)
+  rc = G->hyb ? hybrid_correction(G->hyb, x, rr, st, ncoarse) : coarse_correction(G, x, rr, st, ncoarse);
   if (rc) return rc;
   rc = ddw_apply(c, rr, x, mf, 0, 1, DWF_F32, 1, st);
   if (rc) return rc;
@@ -1037,12 +1043,59 @@ extern "C" int mg_destroy(dwf_mg* G) {
   if (!G) return DWF_OK;
   if (G->basis) cudaFree(G->basis);
   if (G->coarse) coarse_destroy(G->coarse);
+  if (G->hyb) hybrid_free(G->hyb);
   delete G;
+  return DWF_OK;
+}
+
+// Algorithm F: the fine level of mg_solve (pGCR, V(1,1) with the Chebyshev
+// smoother on H_DW) over the hybrid levels built by hybrid.cu.
+extern "C" int mg_setup_hybrid(dwf_ctx* c, const dwf_mg_params* p, const dwf_hybrid_params* hp, const void* eta4,
+                               const void* eta1, dwf_mg** out, void* stream) {
+  if (!c || !p || !hp || !eta4 || !eta1 || !out) return DWF_EINVAL;
+  *out = nullptr;
+  if (p->coarse_solver != DWF_COARSE_CG && p->coarse_solver != DWF_COARSE_RB &&
+      p->coarse_solver != DWF_COARSE_DEFLATED)
+    return dwf_fail(c, DWF_EINVAL, "bad coarse solver");
+  if (p->smooth_order < 1 || !(p->smooth_hi > p->smooth_lo && p->smooth_lo > 0))
+    return dwf_fail(c, DWF_EINVAL, "bad smoother");
+  dwf_mg* G = new (std::nothrow) dwf_mg();
+  if (!G) return DWF_ENOMEM;
+  G->ctx = c;
+  G->p = *p;
+  G->p.no_graph = 1;  // the level-1 GCR reads its scalars on the host
+  G->p.nbasis = 0;
+  int rc = hybrid_build(c, p, hp, eta4, eta1, &G->hyb, (cudaStream_t)stream);
+  if (rc) {
+    delete G;
+    return rc;
+  }
+  G->setup_seconds = hybrid_setup_seconds(G->hyb);
+  G->coarse_op_seconds = hybrid_coarse_seconds(G->hyb);
+  G->lambda_max_used = hp->lambda_max4;
+  *out = G;
+  return DWF_OK;
+}
+
+extern "C" int mg_hybrid_export(const dwf_mg* G, int what, void* out) {
+  if (!G || !out) return DWF_EINVAL;
+  if (!G->hyb) return dwf_fail(G->ctx, DWF_EINVAL, "not a hybrid setup");
+  return hybrid_export(G->hyb, what, out);
+}
+
+extern "C" int mg_hybrid_level1(dwf_mg* G, int op, void* out, const void* in, int nvec, void* stream) {
+  if (!G || !out || !in) return DWF_EINVAL;
+  if (!G->hyb) return dwf_fail(G->ctx, DWF_EINVAL, "not a hybrid setup");
+  if (out == in) return dwf_fail(G->ctx, DWF_EINVAL, "out must not alias in");
+  int rc = hybrid_level1_op(G->hyb, op, out, in, nvec, (cudaStream_t)stream);
+  if (rc) return rc;
+  DWF_CUDA(G->ctx, cudaGetLastError());
   return DWF_OK;
 }
 
 extern "C" int mg_export_basis(const dwf_mg* G, void* out) {
   if (!G || !out) return DWF_EINVAL;
+  if (G->hyb) return dwf_fail(G->ctx, DWF_EINVAL, "hybrid setup: mg_hybrid_export");
   const size_t bytes = (size_t)full_elems(G->ctx) * G->p.nbasis * sizeof(float2);
   if (cudaMemcpy(out, G->basis, bytes, cudaMemcpyDefault) != cudaSuccess) {
     cudaGetLastError();
@@ -1051,7 +1104,7 @@ extern "C" int mg_export_basis(const dwf_mg* G, void* out) {
   return DWF_OK;
 }
 
-extern "C" dwf_coarse* mg_coarse(dwf_mg* G) { return G ? G->coarse : nullptr; }
+extern "C" dwf_coarse* mg_coarse(dwf_mg* G) { return G ? (G->hyb ? hybrid_coarse(G->hyb) : G->coarse) : nullptr; }
 
 extern "C" int mg_precondition(dwf_mg* G, void* out, const void* in, void* stream) {
   if (!G || !out || !in) return DWF_EINVAL;

@@ -363,6 +363,59 @@ def mg_precondition(mg, out, inp):
     return out
 
 
+def hybrid_params(block, nbasis4, nbasis1, *, mass4=-0.95, filter4=(1.0, 60.0, 60),
+                  filter1=(0.5, 60.0, 40), smooth1=(0.5, 60.0, 4), kcycle=2):
+    """Parameters of the hybrid levels (Algorithm F): 4D blocks and basis size,
+    the Wilson mass and filter (lo, hi, order) of the 4D subspace, the level-2
+    basis size and its filter of H_1^2, the level-1 smoother (lo, hi, order;
+    order 0, none, only with kcycle = 1) and the level-1 GCR iteration count."""
+    h = _lib.HybridParams()
+    h.block = (C.c_int * 4)(*block)
+    h.nbasis4, h.mass4 = nbasis4, mass4
+    h.lambda_lo4, h.lambda_max4, h.order4 = filter4
+    h.nbasis1 = nbasis1
+    h.lambda_lo1, h.lambda_max1, h.order1 = filter1
+    h.smooth1_lo, h.smooth1_hi, h.smooth1_order = smooth1
+    h.kcycle = kcycle
+    return h
+
+
+class HybridMG(MG):
+    """A dwf_mg of the hybrid three-level multigrid (Algorithm F): eta4 holds
+    nbasis4 FP64 4D fields as the slices of a full field with Ls = nbasis4,
+    eta1 nbasis1 FP64 level-1 vectors ([nc1][nbasis4][Ls][nbasis1])."""
+
+    def __init__(self, ctx, params, hparams, eta4, eta1):
+        h = C.c_void_p()
+        check(lib().mg_setup_hybrid(ctx.h, C.byref(params), C.byref(hparams), _ptr(eta4), _ptr(eta1), C.byref(h),
+                                    _stream()), ctx.h)
+        self.h = h
+        self.ctx = ctx
+        self.params = params
+        self.hparams = hparams
+        self.coarse = Coarse(C.c_void_p(lib().mg_coarse(h)), ctx, owned=False)
+        L = ctx.L
+        self.Lc = tuple(L[m] // hparams.block[m] for m in range(4))
+        self.nc1 = int(np.prod(self.Lc))
+        self.n1 = self.nc1 * hparams.nbasis4 * ctx.Ls
+
+    def export(self, what):
+        """0: the 4D basis (FP64); 1: B (FP64 [nc1][9][nb4][nb4]); 2: the level-2
+        basis (FP32 [nc1][nb4][Ls][nb1]); 3: the level-2 stencil (FP64)."""
+        hp = self.hparams
+        n = {0: 2 * self.ctx.Vh * 12 * hp.nbasis4,
+             1: self.nc1 * 9 * hp.nbasis4 ** 2, 2: self.n1 * hp.nbasis1, 3: self.nc1 * 9 * hp.nbasis1 ** 2}[what]
+        dt = torch.float32 if what == 2 else torch.float64
+        out = torch.zeros(2 * n, dtype=dt, device="cuda")
+        check(lib().mg_hybrid_export(self.h, what, _ptr(out)), self.ctx.h)
+        return out
+
+    def level1(self, op, out, inp, nvec=1):
+        """0: M_1, 1: H_1, 2: P1^dag, 3: P1, 4: P2^dag, 5: P2, 6: the level-1 W-cycle solve."""
+        check(lib().mg_hybrid_level1(self.h, op, _ptr(out), _ptr(inp), nvec, _stream()), self.ctx.h)
+        return out
+
+
 def mg_solve(mg, x, b, tol):
     st = SolveStats()
     check(lib().mg_solve(mg.h, _ptr(x), _ptr(b), tol, C.byref(st), _stream()), mg.ctx.h)

@@ -185,8 +185,8 @@ def test_complete_bases_give_the_exact_solve_in_one_step():
     assert krylov.true_residual(U, x, b, M5, mf) <= 1e-9
 
 
-@pytest.mark.parametrize("smooth1", [(0.5, 60.0, 0), (0.5, 60.0, 3)])
-def test_hybrid_solve_converges_to_dense_solution(smooth1):
+@pytest.mark.parametrize("smooth1,kcycle", [((0.5, 60.0, 0), 1), ((0.5, 60.0, 3), 2)])
+def test_hybrid_solve_converges_to_dense_solution(smooth1, kcycle):
     L, Ls, mf, block = (4, 4, 4, 4), 4, 0.05, (2, 2, 2, 2)
     U = synth.random_gauge(L, 0.5, 101)
     b4 = hybrid.basis4(U, [gauss4(L, 700 + i) for i in range(8)], -0.95, 1.0, 60.0, 6, block)
@@ -194,7 +194,7 @@ def test_hybrid_solve_converges_to_dense_solution(smooth1):
     shape = (2, 2, 2, 2, 8, Ls)
     b2 = hybrid.basis2(B, [synth.complex_gaussian(800 + i, shape) for i in range(8)], M5, mf, 4, 0.5, 60.0, 6)
     A2 = hybrid.coarse_build2(B, b2, M5, mf, 4)
-    h = hybrid.Hybrid(U, M5, mf, block, b4, B, b2, A2, smooth=(0.5, 60.0, 6), smooth1=smooth1, kcycle=2,
+    h = hybrid.Hybrid(U, M5, mf, block, b4, B, b2, A2, smooth=(0.5, 60.0, 6), smooth1=smooth1, kcycle=kcycle,
                       coarse_tol=0.02)
     b = synth.gaussian_spinor(L, Ls, 11)
     x, it, hist, cnt = hybrid.hybrid_solve(h, b, 1e-8)
@@ -202,7 +202,7 @@ def test_hybrid_solve_converges_to_dense_solution(smooth1):
     xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
     assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e-6
     # the W-cycle: kcycle coarse-coarse solves per fine outer iteration
-    assert cnt.solves2 == 2 * it
+    assert cnt.solves2 == kcycle * it
 
 
 def test_paper_counts_for_algorithm_f():
@@ -214,3 +214,23 @@ def test_paper_counts_for_algorithm_f():
     assert g["coarse_coarse_solves_per_outer"] == 2
     comp = [a * b for a, b in zip(g["block1"], g["block2"])]
     assert comp == [2, 2, 2, 2, 16]
+
+
+def test_degenerate_wcycle_is_rejected():
+    """Without a level-1 smoother the preconditioner K = P2 A_2^-1 P2^dag
+    satisfies K H_1 K = K: a second GCR step would add nothing (the setup
+    rejects kcycle > 1 then).  Checked on the dense level-1 operator."""
+    L, Ls, mf, block = (4, 4, 4, 4), 4, 0.3, (2, 2, 2, 2)
+    U = synth.random_gauge(L, 0.5, 111)
+    b4 = hybrid.basis4(U, [gauss4(L, 900 + i) for i in range(4)], -0.95, 1.0, 60.0, 3, block)
+    B = hybrid.coarse_build4(U, b4, block)
+    shape = (2, 2, 2, 2, 4, Ls)
+    b2 = hybrid.basis2(B, [synth.complex_gaussian(950 + i, shape) for i in range(8)], M5, mf, 2, 0.5, 60.0, 3)
+    A2 = hybrid.coarse_build2(B, b2, M5, mf, 2)
+    H1 = dense_of(lambda v: hybrid.level1_herm(B, v, M5, mf, 2), shape)
+    n2 = int(np.prod(shape[:4])) * len(b2)
+    P2 = np.stack([hybrid.prolong2(b2, e.reshape(shape[:4] + (len(b2),))).ravel() for e in np.eye(n2)], axis=1)
+    K = P2 @ np.linalg.solve(coarse.coarse_dense_from_stencil(A2), P2.conj().T)
+    assert np.allclose(K @ H1 @ K, K, atol=1e-10)
+    with pytest.raises(ValueError):
+        hybrid.Hybrid(U, M5, mf, block, b4, B, b2, A2, smooth1=(0.5, 60.0, 0), kcycle=2)
