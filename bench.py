@@ -264,6 +264,13 @@ MG_PARAMS = dict(block=(4, 4, 4, 4), nbasis=32, subspace="recursive", filter_ord
                  lambda_lo=0.05, smooth=(0.05, None, 40), coarse_tol=2e-3, coarse_maxiter=5000,
                  nkrylov=32, maxiter=300, coarse_solver="deflated", deflation=(64, 160, 10, 0.05))
 MG_PARAMS_LARGE = dict(MG_PARAMS, deflation=(128, 256, 10, 0.05))
+# Algorithm F (Table 3): 2^4 x 1 blocks with 24 4D vectors (Wilson mass
+# -0.95, lambda_lo 4), then one level-1 site x Ls with 32 vectors; the fine
+# smoother as for HDCR; a level-1 smoother of order 4; the W-cycle of two
+# level-1 GCR iterations; red-black CG on the level-2 operator
+HYBRID_PARAMS = dict(block=(2, 2, 2, 2), nbasis4=24, nbasis1=32, mass4=-0.95, filter4=(4.0, 60.0, 60),
+                     filter1=(0.5, None, 40), smooth=(0.05, None, 40), smooth1=(0.05, None, 4), kcycle=2,
+                     coarse_tol=0.02, coarse_maxiter=5000, nkrylov=32, maxiter=300, coarse_solver="rb")
 
 
 def mg_vs_fp64(ctx, w, bd, tol, params=MG_PARAMS, eta_seed=None):
@@ -337,6 +344,84 @@ def mg_vs_fp64(ctx, w, bd, tol, params=MG_PARAMS, eta_seed=None):
     # break-even criterion is setup + two MG solves against one CGNR solve.
     out["speedup_fp64_over_mg"] = out["fp64_rbcg_s"] / out["mg_total_s"]
     out["speedup_fp64_over_mg_setup_two_solves"] = out["fp64_rbcg_s"] / out["mg_setup_plus_two_solves_s"]
+    out["lambda_max"] = lmax
+    out["params"] = {k: v for k, v in p.items()}
+    G.close()
+    return out
+
+
+def hop_variant_label(v, Ls):
+    """The FP32 hopping kernel that tuning variant v launches (the variant table
+    of csrc/dhop_impl.cuh: register cap and inner-loop form)."""
+    regs = {1: 96, 2: 80, 3: 64, 4: 128, 5: 96, 6: 64, 7: 80, 8: 64, 9: 80, 10: 128, 11: 112, 12: 96, 14: 64, 15: 80,
+            16: 64, 17: 80, 18: 56, 19: 48, 23: 64, 24: 64, 25: 80}.get(v, 0)
+    if 10 <= v <= 13 or 20 <= v <= 22:
+        form = "two s-slices per thread, packed FP32" + (", cp.async staging" if v >= 20 else "")
+        name = "hop_kernel_pair"
+    else:
+        form = ("scalar" if v in (0, 1, 2, 3, 18, 19) else "neighbour prefetch" if v in (4, 5)
+                else "packed FP32 (re, im)" if v in (6, 7) else "2^4 hypercube tiles" if v in (8, 9)
+                else "y-row CTAs" if 14 <= v <= 17 else "L2 prefetch")
+        name = "hop_kernel"
+    cap = f"{regs} registers" if regs else "no register cap"
+    return f"dwfk::{name}<F32, Ls={Ls}> (dwf_dhop, plain epilogue; variant {v}: {form}, {cap})"
+
+
+def hybrid_vs_fp64(ctx, w, bd, tol, fp64_s, params=HYBRID_PARAMS):
+    """Algorithm F (the hybrid three-level multigrid) on the source of
+    mg_vs_fp64: setup (4D level and level-2 parts), two solves, against the
+    FP64 red-black CG time measured there.  One run each, host clock around
+    synchronising calls."""
+    import torch
+
+    from paper_2103_05034_gb300 import ops
+    from paper_2103_05034_gb300._lib import COARSE_CG, COARSE_RB, F32
+
+    p = dict(params)
+    mf = w["mf"]
+    L, Ls = w["L"], w["Ls"]
+    gen = torch.Generator(device="cuda").manual_seed(77)
+    v0 = torch.randn(bd.numel(), generator=gen, device="cuda", dtype=torch.float64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lmax = ops.dwf_power_max(ctx, v0, mf, 100, F32) * 1.10
+    del v0
+    cs = {"cg": COARSE_CG, "rb": COARSE_RB}[p["coarse_solver"]]
+    prm = ops.mg_params(p["block"], 0, mf, smooth=(p["smooth"][0], lmax, p["smooth"][2]), coarse_tol=p["coarse_tol"],
+                        coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"], maxiter=p["maxiter"],
+                        coarse_solver=cs)
+    f1 = p["filter1"]
+    hp = ops.hybrid_params(p["block"], p["nbasis4"], p["nbasis1"], mass4=p["mass4"], filter4=p["filter4"],
+                           filter1=(f1[0], lmax, f1[2]), smooth1=(p["smooth1"][0], lmax, p["smooth1"][2]),
+                           kcycle=p["kcycle"])
+    nc1 = int(np.prod([L[m] // p["block"][m] for m in range(4)]))
+    gen = torch.Generator(device="cuda").manual_seed(synth.SEED_BASIS)
+    eta4 = torch.randn(2 * 2 * ctx.Vh * 12 * p["nbasis4"], generator=gen, device="cuda", dtype=torch.float64)
+    eta1 = torch.randn(2 * nc1 * p["nbasis4"] * Ls * p["nbasis1"], generator=gen, device="cuda", dtype=torch.float64)
+    G = ops.HybridMG(ctx, prm, hp, eta4, eta1)
+    del eta4, eta1
+    torch.cuda.synchronize()
+    out = {"workload": "x".join(map(str, L)) + f"x{Ls}", "mf": mf, "setup_s": time.perf_counter() - t0}
+    x = torch.zeros_like(bd)
+    for k in range(2):
+        src = bd if k == 0 else torch.roll(bd, 24)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = ops.mg_solve(G, x, src, tol)
+        key = "solve" if k == 0 else "second_solve"
+        out[key + "_s"] = time.perf_counter() - t0
+        out[key + "_outer_iterations"] = st["iterations"]
+        out[key + "_level2_iterations"] = st["coarse_iterations"]
+        out[key + "_fine_matmuls"] = st["fine_matmuls"]
+        out[key + "_true_residual"] = st["true_residual"]
+    out["setup_4d_level_s"] = st["setup_seconds"]
+    out["setup_level2_s"] = st["coarse_op_seconds"]
+    out["total_s"] = out["setup_s"] + out["solve_s"]
+    out["setup_plus_two_solves_s"] = out["total_s"] + out["second_solve_s"]
+    out["fp64_rbcg_s"] = fp64_s
+    out["speedup_fp64_over_hybrid"] = fp64_s / out["total_s"]
+    out["speedup_fp64_over_hybrid_setup_two_solves"] = fp64_s / out["setup_plus_two_solves_s"]
     out["lambda_max"] = lmax
     out["params"] = {k: v for k, v in p.items()}
     G.close()
@@ -429,7 +514,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": profile_traffic(f"hop_kernel_f32_ls{Ls}_{args.workload}", shash),
-                "kernel": f"dwfk::hop_kernel<F32, Ls={Ls}> (dwf_dhop, plain epilogue, variant {hop_variant})",
+                "kernel": hop_variant_label(hop_variant, Ls),
                 "launch_ms": hop_ms, "algorithmic_bytes_per_launch": hop_alg_bytes,
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "source_hash": shash}
 
@@ -574,9 +659,11 @@ def run_ours(args):
                 try:
                     bsd = device_source(cs, ws_, bs, 0, dev)
                     line["mg_vs_fp64"] = mg_vs_fp64(cs, ws_, bsd, args.tol)
+                    line["hybrid_vs_fp64"] = hybrid_vs_fp64(cs, ws_, bsd, args.tol, line["mg_vs_fp64"]["fp64_rbcg_s"])
                     del bsd
                 except Exception as e:  # reported, not hidden: the line says what failed
-                    line["mg_vs_fp64"] = {"error": str(e)}
+                    line.setdefault("mg_vs_fp64", {"error": str(e)})
+                    line.setdefault("hybrid_vs_fp64", {"error": str(e)})
             cs.close()
         except StopIteration:
             pass
@@ -594,6 +681,12 @@ def run_ours(args):
                 ops.dwf_autotune(cl, F32, 10)
                 bl = device_source(cl, wl, None, 0, dev)
                 line["mg_vs_fp64_large"] = mg_vs_fp64(cl, wl, bl, args.tol, MG_PARAMS_LARGE)
+                if args.hybrid_large:
+                    try:
+                        line["hybrid_vs_fp64_large"] = hybrid_vs_fp64(cl, wl, bl, args.tol,
+                                                                      line["mg_vs_fp64_large"]["fp64_rbcg_s"])
+                    except Exception as e:
+                        line["hybrid_vs_fp64_large"] = {"error": str(e)}
                 del bl
                 cl.close()
             except Exception as e:
@@ -1068,6 +1161,9 @@ def main(argv=None):
                     help="only the timed steps, the roofline kernel and e2e (for profiling the step)")
     ap.add_argument("--no-mg-large", dest="mg_large", action="store_false",
                     help="skip the 24^3x48x24 comparison (about two minutes)")
+    ap.add_argument("--hybrid-large", action="store_true",
+                    help="add Algorithm F (hybrid three-level multigrid) to the 24^3x48x24 comparison "
+                         "(about four minutes)")
     ap.add_argument("--kernel", default=None,
                     help="profile mode: dhop_f32, dhop_f64, dhop_f16, mpcdagmpc_f32, coarse_tf32 or coarse_f32 alone")
     ap.add_argument("--rows", action="store_true",
