@@ -861,7 +861,8 @@ def run_rows(args):
     from oracle import cheby as o_cheby
     from oracle import dwf as o_dwf
     from paper_2103_05034_gb300 import layout, ops
-    from paper_2103_05034_gb300._lib import F16S, F32, F64, SOLVE_MIXED_F32, SUBSPACE_BATCH
+    from paper_2103_05034_gb300._lib import (ARITH_FLOAT_FLOAT, ARITH_FP64, F16S, F32, F64, SOLVE_MIXED_F32,
+                                             SUBSPACE_BATCH)
 
     # the rows use host-side inputs: a paper-size workload is replaced by the
     # 16^3 x 32 x 16 one
@@ -874,7 +875,9 @@ def run_rows(args):
     ops.dwf_autotune(ctx, F16S, 10)
     peaks, kind = measured_peaks()
     hbm = peaks["hbm_gbs"]
-    fp64_peak = 1.25  # TFLOP/s, nominal dense FP64 of GB300 (no measured figure)
+    # FP64 and FP32 FMA rates of this GPU, measured by the library's own
+    # FMA-chain microbenchmark (the denominators of the ALU-bound rows)
+    fp64_peak, fp32_peak = ops.dwf_measure_fma_peaks()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     gen = torch.Generator(device="cuda").manual_seed(synth.SEED_SOURCE)
     nh = ctx.half_numel()  # reals of one half field
@@ -931,6 +934,7 @@ def run_rows(args):
         rows.append(d)
         print(json.dumps(d), flush=True)
 
+    emit("peaks", "FMA microbenchmark (dwf_measure_fma_peaks)", 0.0, fp64_tflops=fp64_peak, fp32_tflops=fp32_peak)
     V5h = ctx.Vh * Ls
     pe = o_dwf.project_parity(spsi, sL, 1)
     a32 = field(nh, torch.float32)
@@ -943,7 +947,13 @@ def run_rows(args):
     f = lambda: ops.dwf_dhop(ctx, o16, a16, 0)
     emit("a1", "dwf_dhop F16 storage", timed(f), hop_bytes(f), "GB/s", hbm, "hbm")
     f = lambda: ops.dwf_dhop(ctx, o64, a64, 0)
-    emit("a1", "dwf_dhop F64", timed(f, 5), 1320.0 * V5h, "TFLOP/s", fp64_peak, "fp64 alu (nominal 1.25)")
+    emit("a1", "dwf_dhop F64", timed(f, 5), 1320.0 * V5h, "TFLOP/s", fp64_peak, "fp64 alu (measured FMA rate)")
+    # the same FP64 fields in float-float arithmetic on the FP32 units
+    ops.set_f64_arithmetic(ctx, ARITH_FLOAT_FLOAT)
+    v64, _ = ops.dwf_autotune(ctx, F64, 5)
+    emit("a1", "dwf_dhop F64 storage, float-float arithmetic", timed(f, 5), 1320.0 * V5h, "TFLOP/s", fp64_peak,
+         "fp64-equivalent flop over the measured FP64 rate", variant=v64)
+    ops.set_f64_arithmetic(ctx, ARITH_FP64)
     f = lambda: ops.dwf_mooee_inv(ctx, o32, a32, mf)
     emit("a2", "dwf_mooee_inv F32", timed(f), V5h * 24 * 8.0, "GB/s", hbm, "hbm",
          oracle_ns_per_site(lambda: o_dwf.mooee_inv(spsi, M5, mf)))
@@ -1015,7 +1025,7 @@ def run_rows(args):
     copy_ms = timed(lambda: work.copy_(basis), 3)
     nfull_c = nh  # complex numbers of one full field (= reals of one half field)
     emit("a9", "block_orthonormalise FP64, 32 vectors, 4^4 x Ls blocks", ms - copy_ms,
-         2 * 2 * 8.0 * nb * nb * nfull_c, "TFLOP/s", fp64_peak, "fp64 alu (nominal 1.25)",
+         2 * 2 * 8.0 * nb * nb * nfull_c, "TFLOP/s", fp64_peak, "fp64 alu (measured FMA rate)",
          note="work = Cholesky-QR2: two passes of a Gram matrix and an R^-1 application, 8 nb^2 flop per"
               " complex entry each, all in FP64 as the orthonormalisation requires")
     del g64, basis

@@ -133,7 +133,9 @@ int dwf_reset_counters(dwf_ctx* ctx);
  * 4 or 8 neighbours in flight), CTAs of 2 or 4 y-rows, the scalar form
  * with an L2 prefetch of the rows a CTA a wave later reads first; DWF_HOP_VARIANTS
  * variants for FP32 and FP16
- * storage at Ls >= 16, one otherwise) on this context's lattice, `reps`
+ * storage at Ls >= 16, one otherwise; for DWF_F64 the one FP64 kernel, or
+ * with DWF_ARITH_FLOAT_FLOAT the float-float kernel under four register
+ * caps) on this context's lattice, `reps`
  * launches each, keeps the fastest for precision `prec` and returns its time
  * per launch in *best_ms (may be NULL).  Variants that do not tile the
  * lattice are skipped.  Uses two half fields of context workspace, released
@@ -142,6 +144,21 @@ int dwf_reset_counters(dwf_ctx* ctx);
  * dwf_set_hop_variant returns DWF_EINVAL for a variant that does not tile
  * the lattice). */
 #define DWF_HOP_VARIANTS 26
+
+/* Arithmetic of the FP64-precision hopping launches of a context (every
+ * DWF_F64 D_hop, M_pc, D_DW and H_DW application, including the FP64
+ * operator of the solvers: source preparation, reliable updates,
+ * reconstruction, true residual).  DWF_ARITH_FP64 (default): FP64 units.
+ * DWF_ARITH_FLOAT_FLOAT: the same FP64 fields computed on the FP32 units in
+ * float-float arithmetic (pairs of FP32 numbers with error-free sums and
+ * products, about 46 significant bits; Eq. 2 and Eq. 4 unchanged), several
+ * times faster on GB300, whose FP64 rate is 1/74 of its FP32 rate.  FP64
+ * inputs below 2^-126 in magnitude enter as zero.  The site-local kernel
+ * and the BLAS stay FP64.  Host-side, no sync. */
+#define DWF_ARITH_FP64 0
+#define DWF_ARITH_FLOAT_FLOAT 1
+int dwf_set_f64_arithmetic(dwf_ctx* ctx, int mode);
+int dwf_get_f64_arithmetic(const dwf_ctx* ctx);
 int dwf_autotune(dwf_ctx* ctx, int prec, int reps, double* best_ms, void* stream);
 int dwf_set_hop_variant(dwf_ctx* ctx, int prec, int variant);
 int dwf_get_hop_variant(const dwf_ctx* ctx, int prec);

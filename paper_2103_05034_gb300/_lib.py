@@ -36,6 +36,7 @@ class SolveStats(C.Structure):
 
 SUBSPACE_BATCH, SUBSPACE_RECURSIVE = 0, 1
 COARSE_CG, COARSE_RB, COARSE_DEFLATED = 0, 1, 2
+ARITH_FP64, ARITH_FLOAT_FLOAT = 0, 1
 
 
 class MGParams(C.Structure):
@@ -105,6 +106,8 @@ _SIGS = {
     "dwf_counters": (I, [P, C.POINTER(I64), C.POINTER(D)]),
     "dwf_reset_counters": (I, [P]),
     "dwf_autotune": (I, [P, I, I, C.POINTER(D), P]),
+    "dwf_set_f64_arithmetic": (I, [P, I]),
+    "dwf_get_f64_arithmetic": (I, [P]),
     "dwf_set_hop_variant": (I, [P, I, I]),
     "dwf_get_hop_variant": (I, [P, I]),
     "dwf_dhop": (I, [P, P, P, I, I, I, I, P]),

@@ -311,7 +311,8 @@ int launch_hop(dwf_ctx* c, const HopLaunch& h, int prec, cudaStream_t st, int* n
   int rc;
   switch (prec) {
     case DWF_F64:
-      rc = dwf_launch_hop_f64(hp, c->g.Ls, h.nrhs, c->hop_variant[0], st, nblocks);
+      rc = c->f64_arith == DWF_ARITH_FLOAT_FLOAT ? dwf_launch_hop_df(hp, c->g.Ls, h.nrhs, c->hop_variant[0], st, nblocks)
+                                                 : dwf_launch_hop_f64(hp, c->g.Ls, h.nrhs, c->hop_variant[0], st, nblocks);
       break;
     case DWF_F32:
       rc = dwf_launch_hop_f32(hp, c->g.Ls, h.nrhs, c->hop_variant[1], st, nblocks);
@@ -340,6 +341,14 @@ static bool hop_variant_fits(const dwf_ctx* c, int prec, int v) {
   return ry == 1 || (c->g.Lxh % sb == 0 && c->g.L[1] % ry == 0);
 }
 
+extern "C" int dwf_set_f64_arithmetic(dwf_ctx* c, int mode) {
+  if (!c || (mode != DWF_ARITH_FP64 && mode != DWF_ARITH_FLOAT_FLOAT)) return DWF_EINVAL;
+  c->f64_arith = mode;
+  return DWF_OK;
+}
+
+extern "C" int dwf_get_f64_arithmetic(const dwf_ctx* c) { return c ? c->f64_arith : DWF_EINVAL; }
+
 extern "C" int dwf_set_hop_variant(dwf_ctx* c, int prec, int variant) {
   if (!c || prec < DWF_F64 || prec > DWF_F16S || variant < 0 || variant >= DWF_HOP_VARIANTS) return DWF_EINVAL;
   if (!hop_variant_fits(c, prec, variant)) return dwf_fail(c, DWF_EINVAL, "hop variant does not tile the lattice");
@@ -363,7 +372,8 @@ extern "C" int dwf_autotune(dwf_ctx* c, int prec, int reps, double* best_ms, voi
   cudaEvent_t e0, e1;
   DWF_CUDA(c, cudaEventCreate(&e0));
   DWF_CUDA(c, cudaEventCreate(&e1));
-  const int nv = (prec == DWF_F64 || c->g.Ls < 16) ? 1 : DWF_HOP_VARIANTS;
+  // FP64: one kernel, or four register caps of the float-float kernel
+  const int nv = c->g.Ls < 16 ? 1 : prec == DWF_F64 ? (c->f64_arith == DWF_ARITH_FLOAT_FLOAT ? 4 : 1) : DWF_HOP_VARIANTS;
   int best = 0;
   float best_t = 1e30f;
   const int64_t launches0 = c->launches;

@@ -74,6 +74,17 @@ __device__ __forceinline__ void cacc(cpx<R>& a, const cpx<R>& b) {
   a.im += b.im;
 }
 
+// Products with the hopping sign sg = +-1 (overloaded for arithmetic types
+// in which a product costs more than a sign change).
+template <class R>
+__device__ __forceinline__ R sg_mul(R sg, R x) {
+  return sg * x;
+}
+template <class R>
+__device__ __forceinline__ R sg_fma(R sg, R x, R y) {
+  return fma(sg, x, y);
+}
+
 // acc += (1 - sg gamma_mu) U psi, spin-projected.
 template <class R, int MU>
 __device__ __forceinline__ void hop_dir(cpx<R> (&acc)[12], const cpx<R> (&ps)[12],
@@ -83,17 +94,17 @@ __device__ __forceinline__ void hop_dir(cpx<R> (&acc)[12], const cpx<R> (&ps)[12
   for (int c = 0; c < 3; c++) {
     const cpx<R> p0 = ps[c], p1 = ps[3 + c], p2 = ps[6 + c], p3 = ps[9 + c];
     if (MU == 0) {  // A = -i sigma_1: h0 = p0 + s i p3, h1 = p1 + s i p2
-      h0[c] = cmake<R>(p0.re - sg * p3.im, p0.im + sg * p3.re);
-      h1[c] = cmake<R>(p1.re - sg * p2.im, p1.im + sg * p2.re);
+      h0[c] = cmake<R>(p0.re - sg_mul(sg, p3.im), p0.im + sg_mul(sg, p3.re));
+      h1[c] = cmake<R>(p1.re - sg_mul(sg, p2.im), p1.im + sg_mul(sg, p2.re));
     } else if (MU == 1) {  // A = -i sigma_2: h0 = p0 + s p3, h1 = p1 - s p2
-      h0[c] = cmake<R>(p0.re + sg * p3.re, p0.im + sg * p3.im);
-      h1[c] = cmake<R>(p1.re - sg * p2.re, p1.im - sg * p2.im);
+      h0[c] = cmake<R>(p0.re + sg_mul(sg, p3.re), p0.im + sg_mul(sg, p3.im));
+      h1[c] = cmake<R>(p1.re - sg_mul(sg, p2.re), p1.im - sg_mul(sg, p2.im));
     } else if (MU == 2) {  // A = -i sigma_3: h0 = p0 + s i p2, h1 = p1 - s i p3
-      h0[c] = cmake<R>(p0.re - sg * p2.im, p0.im + sg * p2.re);
-      h1[c] = cmake<R>(p1.re + sg * p3.im, p1.im - sg * p3.re);
+      h0[c] = cmake<R>(p0.re - sg_mul(sg, p2.im), p0.im + sg_mul(sg, p2.re));
+      h1[c] = cmake<R>(p1.re + sg_mul(sg, p3.im), p1.im - sg_mul(sg, p3.re));
     } else {  // A = 1: h0 = p0 - s p2, h1 = p1 - s p3
-      h0[c] = cmake<R>(p0.re - sg * p2.re, p0.im - sg * p2.im);
-      h1[c] = cmake<R>(p1.re - sg * p3.re, p1.im - sg * p3.im);
+      h0[c] = cmake<R>(p0.re - sg_mul(sg, p2.re), p0.im - sg_mul(sg, p2.im));
+      h1[c] = cmake<R>(p1.re - sg_mul(sg, p3.re), p1.im - sg_mul(sg, p3.im));
     }
   }
 #pragma unroll
@@ -115,25 +126,25 @@ __device__ __forceinline__ void hop_dir(cpx<R> (&acc)[12], const cpx<R> (&ps)[12
     cacc(acc[3 + a], g1);
     // lower spins: -s A^dag g
     if (MU == 0) {  // A^dag g = (i g1, i g0)
-      acc[6 + a].re = fma(sg, g1.im, acc[6 + a].re);
-      acc[6 + a].im = fma(-sg, g1.re, acc[6 + a].im);
-      acc[9 + a].re = fma(sg, g0.im, acc[9 + a].re);
-      acc[9 + a].im = fma(-sg, g0.re, acc[9 + a].im);
+      acc[6 + a].re = sg_fma(sg, g1.im, acc[6 + a].re);
+      acc[6 + a].im = sg_fma(-sg, g1.re, acc[6 + a].im);
+      acc[9 + a].re = sg_fma(sg, g0.im, acc[9 + a].re);
+      acc[9 + a].im = sg_fma(-sg, g0.re, acc[9 + a].im);
     } else if (MU == 1) {  // A^dag g = (g1, -g0)
-      acc[6 + a].re = fma(-sg, g1.re, acc[6 + a].re);
-      acc[6 + a].im = fma(-sg, g1.im, acc[6 + a].im);
-      acc[9 + a].re = fma(sg, g0.re, acc[9 + a].re);
-      acc[9 + a].im = fma(sg, g0.im, acc[9 + a].im);
+      acc[6 + a].re = sg_fma(-sg, g1.re, acc[6 + a].re);
+      acc[6 + a].im = sg_fma(-sg, g1.im, acc[6 + a].im);
+      acc[9 + a].re = sg_fma(sg, g0.re, acc[9 + a].re);
+      acc[9 + a].im = sg_fma(sg, g0.im, acc[9 + a].im);
     } else if (MU == 2) {  // A^dag g = (i g0, -i g1)
-      acc[6 + a].re = fma(sg, g0.im, acc[6 + a].re);
-      acc[6 + a].im = fma(-sg, g0.re, acc[6 + a].im);
-      acc[9 + a].re = fma(-sg, g1.im, acc[9 + a].re);
-      acc[9 + a].im = fma(sg, g1.re, acc[9 + a].im);
+      acc[6 + a].re = sg_fma(sg, g0.im, acc[6 + a].re);
+      acc[6 + a].im = sg_fma(-sg, g0.re, acc[6 + a].im);
+      acc[9 + a].re = sg_fma(-sg, g1.im, acc[9 + a].re);
+      acc[9 + a].im = sg_fma(sg, g1.re, acc[9 + a].im);
     } else {  // A^dag g = (g0, g1)
-      acc[6 + a].re = fma(-sg, g0.re, acc[6 + a].re);
-      acc[6 + a].im = fma(-sg, g0.im, acc[6 + a].im);
-      acc[9 + a].re = fma(-sg, g1.re, acc[9 + a].re);
-      acc[9 + a].im = fma(-sg, g1.im, acc[9 + a].im);
+      acc[6 + a].re = sg_fma(-sg, g0.re, acc[6 + a].re);
+      acc[6 + a].im = sg_fma(-sg, g0.im, acc[6 + a].im);
+      acc[9 + a].re = sg_fma(-sg, g1.re, acc[9 + a].re);
+      acc[9 + a].im = sg_fma(-sg, g1.im, acc[9 + a].im);
     }
   }
 }
@@ -859,6 +870,15 @@ inline int launch_hop_ls(const HopParams& hp, dim3 grid, int variant, cudaStream
   // FP64 is ALU-bound and the small-Ls cases are test sizes: one variant.
   if constexpr (P == DWF_F64 || LSV < 16) {
     launch_hop_v<P, LSV, 0>(hp, grid, st);
+  } else if constexpr (P == DWF_P_DF) {
+    // float-float: the plain kernel with register caps 96 / 80 / 64 (more
+    // resident warps for its long dependent FP32 chains)
+    switch (variant) {
+      case 1: launch_hop_v<P, LSV, 1>(hp, grid, st); break;
+      case 2: launch_hop_v<P, LSV, 2>(hp, grid, st); break;
+      case 3: launch_hop_v<P, LSV, 3>(hp, grid, st); break;
+      default: launch_hop_v<P, LSV, 0>(hp, grid, st); break;
+    }
   } else {
     switch (variant) {
       case 1: launch_hop_v<P, LSV, 1>(hp, grid, st); break;
@@ -900,7 +920,7 @@ int launch_hop_prec(const HopParams& hp, int Ls, int nrhs, int variant, cudaStre
 #define DWF_HOP_CASE(LSV)                                                        \
   case LSV: {                                                                    \
     constexpr int SB = HopShape<LSV>::SB;                                        \
-    const int ry = (P == DWF_F64 || LSV < 16) ? 1 : hop_variant_rows(variant);   \
+    const int ry = (P == DWF_F64 || P == DWF_P_DF || LSV < 16) ? 1 : hop_variant_rows(variant); \
     if (ry > 1 && (hp.Lxh % SB || hp.L1 % ry)) return DWF_EINVAL;                \
     grid.x = (hp.Vh + SB * ry - 1) / (SB * ry);                                  \
     if (nblocks) *nblocks = grid.x * grid.y;                                     \
@@ -946,6 +966,8 @@ int launch_mooee_prec(void* out, const void* in, const HopParams& hp, int dagger
 int dwf_launch_hop_f64(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nb);
 int dwf_launch_hop_f32(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nb);
 int dwf_launch_hop_f16(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nb);
+// FP64 storage, float-float arithmetic (dhop_df.cu)
+int dwf_launch_hop_df(const dwfk::HopParams& hp, int Ls, int nrhs, int variant, cudaStream_t st, int* nb);
 int dwf_launch_mooee_f64(void* out, const void* in, const dwfk::HopParams& hp, int dagger,
                          int inverse, int Ls, int nrhs, long long rs, cudaStream_t st);
 int dwf_launch_mooee_f32(void* out, const void* in, const dwfk::HopParams& hp, int dagger,

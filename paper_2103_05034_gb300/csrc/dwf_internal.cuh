@@ -11,6 +11,9 @@
 #include "../../include/dwfmg.h"
 
 #define DWF_MAX_RHS 64
+// Internal precision tag of the hopping kernel with FP64 storage and
+// float-float arithmetic (dfloat.cuh); not an ABI precision.
+#define DWF_P_DF 7
 #define DWF_NWS 40  // workspace slots
 #define CG_SMALL_BYTES 384  // status and barrier counters of the persistent coarse CG
 
@@ -126,6 +129,7 @@ struct dwf_ctx {
   double* dscal;      // device scalars for solvers
   double* hscal;      // pinned host mirror
   int hop_variant[3]; // tuned hopping-kernel variant per precision
+  int f64_arith;      // FP64 hopping launches: DWF_ARITH_FP64 or DWF_ARITH_FLOAT_FLOAT
   double hop_l2_budget[3];  // L2 bytes the z-chunked traversal plans for (0: 48 MB)
   int64_t launches;   // kernel launches since the last counter reset
   double hop_bytes;   // algorithmic bytes of hopping-term launches

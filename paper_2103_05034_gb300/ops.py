@@ -363,6 +363,12 @@ def mg_precondition(mg, out, inp):
     return out
 
 
+def set_f64_arithmetic(ctx, mode):
+    """ARITH_FP64 (FP64 units) or ARITH_FLOAT_FLOAT (float-float on the FP32
+    units) for the context's FP64-precision hopping launches."""
+    check(lib().dwf_set_f64_arithmetic(ctx.h, int(mode)), ctx.h)
+
+
 def hybrid_params(block, nbasis4, nbasis1, *, mass4=-0.95, filter4=(1.0, 60.0, 60),
                   filter1=(0.5, 60.0, 40), smooth1=(0.5, 60.0, 4), kcycle=2):
     """Parameters of the hybrid levels (Algorithm F): 4D blocks and basis size,

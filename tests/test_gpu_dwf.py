@@ -359,3 +359,98 @@ def test_bounded_waits_give_up_and_report():
     a.fill_(1.0)
     assert ops.dwf_norm2(ctx, a) == pytest.approx(a.numel() / 2 * 2.0, rel=1e-6)
     ctx.close()
+
+
+# ------------------------------------------------------------ float-float FP64 operator
+# FP64 storage with float-float arithmetic (pairs of FP32 numbers with
+# error-free sums and products, about 46 significant bits): a few dozen
+# roundings of relative size 2^-46 ~ 1.4e-14 per output, so 1e-12 as for FP64.
+@pytest.fixture
+def df_mode(case):
+    L, Ls, U, ctx = case
+    ops.set_f64_arithmetic(ctx, _lib.ARITH_FLOAT_FLOAT)
+    yield case
+    ops.set_f64_arithmetic(ctx, _lib.ARITH_FP64)
+
+
+@pytest.mark.parametrize("dagger", [0, 1])
+@pytest.mark.parametrize("out_parity", [0, 1])
+def test_dhop_float_float(df_mode, dagger, out_parity):
+    L, Ls, U, ctx = df_mode
+    from paper_2103_05034_gb300 import layout
+    psi = synth.gaussian_spinor(L, Ls, 11)
+    src = dwf.project_parity(psi, L, 1 - out_parity)
+    inp = half_dev(psi, L, 1 - out_parity, F64)
+    out = torch.zeros_like(inp)
+    ops.dwf_dhop(ctx, out, inp, out_parity, dagger)
+    want = layout.to_half(dwf.dhop(U, src, dag=bool(dagger)), L, out_parity)
+    got = dev_to_half(out, Ls)
+    assert rel(got, want) < 1e-12
+    # not the FP64 kernel: the result differs from it in the last bits
+    ops.set_f64_arithmetic(ctx, _lib.ARITH_FP64)
+    out64 = torch.zeros_like(inp)
+    ops.dwf_dhop(ctx, out64, inp, out_parity, dagger)
+    assert not torch.equal(out, out64)
+
+
+def test_mpc_ddw_hdw_float_float(df_mode):
+    """The fused epilogues (M_ee, M_ee^-1, Gamma_5) in float-float."""
+    L, Ls, U, ctx = df_mode
+    from paper_2103_05034_gb300 import layout
+    mf = 0.05
+    psi = dwf.project_parity(synth.gaussian_spinor(L, Ls, 13), L, 0)
+    inp = half_dev(psi, L, 0, F64)
+    out = torch.zeros_like(inp)
+    for dagger, fn in ((0, dwf.mpc), (1, dwf.mpc_dag)):
+        ops.dwf_mpc(ctx, out, inp, mf, dagger)
+        assert rel(dev_to_half(out, Ls), layout.to_half(fn(U, psi, M5, mf), L, 0)) < 1e-12
+    full = synth.gaussian_spinor(L, Ls, 14)
+    fin = full_dev(full, L, F64)
+    fout = torch.zeros_like(fin)
+    ops.dwf_ddw(ctx, fout, fin, mf, 1)
+    assert rel(dev_to_full_canon(fout, L, Ls), dwf.ddw(U, full, M5, mf, dag=True)) < 1e-12
+    ops.dwf_hdw(ctx, fout, fin, mf)
+    assert rel(dev_to_full_canon(fout, L, Ls), dwf.hdw(U, full, M5, mf)) < 1e-12
+
+
+@pytest.mark.parametrize("policy", [SOLVE_F64, SOLVE_MIXED_F32])
+def test_rbcg_float_float_operator(policy):
+    """The red-black CG with the FP64 operator in float-float arithmetic
+    (source preparation, reliable updates, reconstruction, true residual):
+    the true residual reaches 1e-10 and the solution matches the oracle's."""
+    L, Ls, mf = (4, 4, 4, 4), 8, 0.01
+    U = synth.random_gauge(L, 0.3, synth.SEED_GAUGE)
+    b = synth.gaussian_spinor(L, Ls, synth.SEED_SOURCE)
+    ctx = ops.Context(L, Ls, M5, U)
+    ops.set_f64_arithmetic(ctx, _lib.ARITH_FLOAT_FLOAT)
+    tol = 1e-10
+    bd = full_dev(b, L, F64)
+    x = torch.zeros_like(bd)
+    st = ops.rbcg_solve(ctx, x, bd, mf, tol, 20000, policy)
+    xg = dev_to_full_canon(x, L, Ls)
+    res = krylov.true_residual(U, xg, b, M5, mf)
+    assert res <= tol * 1.01, st
+    assert st["true_residual"] == pytest.approx(res, rel=1e-3, abs=1e-13)
+    xr, _, _ = krylov.rbcg_solve(U, b, M5, mf, 1e-13)
+    assert rel(xg, xr) < 1e-7
+    ctx.close()
+
+
+def test_float_float_small_and_large_values():
+    """Inputs spanning many binades (1e-20 .. 1e20 times a Gaussian): the
+    float-float hop keeps 1e-12 relative accuracy per output where the
+    inputs are within the FP32 exponent range."""
+    L, Ls = (4, 4, 2, 2), 16
+    U = synth.random_gauge(L, 0.5, 9)
+    ctx = ops.Context(L, Ls, M5, U)
+    ops.set_f64_arithmetic(ctx, _lib.ARITH_FLOAT_FLOAT)
+    from paper_2103_05034_gb300 import layout
+    for scale in (1e-20, 1e-3, 1e8, 1e20):
+        psi = scale * synth.gaussian_spinor(L, Ls, 17)
+        src = dwf.project_parity(psi, L, 1)
+        inp = half_dev(psi, L, 1, F64)
+        out = torch.zeros_like(inp)
+        ops.dwf_dhop(ctx, out, inp, 0, 0)
+        want = layout.to_half(dwf.dhop(U, src), L, 0)
+        assert rel(dev_to_half(out, Ls), want) < 1e-12, scale
+    ctx.close()
