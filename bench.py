@@ -1025,9 +1025,10 @@ def run_rows(args):
     copy_ms = timed(lambda: work.copy_(basis), 3)
     nfull_c = nh  # complex numbers of one full field (= reals of one half field)
     emit("a9", "block_orthonormalise FP64, 32 vectors, 4^4 x Ls blocks", ms - copy_ms,
-         2 * 2 * 8.0 * nb * nb * nfull_c, "TFLOP/s", fp64_peak, "fp64 alu (measured FMA rate)",
-         note="work = Cholesky-QR2: two passes of a Gram matrix and an R^-1 application, 8 nb^2 flop per"
-              " complex entry each, all in FP64 as the orthonormalisation requires")
+         2 * 1.5 * 8.0 * nb * nb * nfull_c, "TFLOP/s", fp64_peak, "fp64 alu (measured FMA rate)",
+         note="work = Cholesky-QR2: two passes of a Gram matrix (nb^2 complex multiply-adds per field"
+              " entry) and the R^-1 update of each chirality group (2 (nb/2)^2), 8 flop per complex"
+              " multiply-add, all in FP64 as the orthonormalisation requires")
     del g64, basis
     Cc = [None]
 

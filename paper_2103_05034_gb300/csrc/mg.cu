@@ -281,6 +281,12 @@ int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cud
   if (C->nb == 32)
     dwfmg::k_coarse_apply<32><<<blocks, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2],
                                                       C->g.Lc[3], C->nb, nrhs);
+  else if (C->nb == 24)  // the hybrid multigrid's 4D basis (Algorithm F)
+    dwfmg::k_coarse_apply<24><<<blocks, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2],
+                                                      C->g.Lc[3], C->nb, nrhs);
+  else if (C->nb == 16)
+    dwfmg::k_coarse_apply<16><<<blocks, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2],
+                                                      C->g.Lc[3], C->nb, nrhs);
   else
     dwfmg::k_coarse_apply<0><<<blocks, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2],
                                                      C->g.Lc[3], C->nb, nrhs);

@@ -90,7 +90,7 @@ class Case:
         self.ctx.close()
 
 
-@pytest.fixture(scope="module", params=[4, 8], ids=["nb4_4", "nb4_8"])
+@pytest.fixture(scope="module", params=[4, 16], ids=["nb4_4", "nb4_16"])
 def case(request):
     c = Case((4, 4, 4, 4), 4, 0.05, (2, 2, 2, 2), request.param, 8, (1.0, 60.0, 6), (0.5, 60.0, 6))
     yield c
