@@ -277,6 +277,20 @@ int coarse_ws(dwf_coarse* C, int slot, size_t bytes, void** out) {
 int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cudaStream_t st) {
   const long long n = (long long)C->g.nc * C->nb * nrhs;
   C->ctx->launches++;
+  if ((nrhs & 3) == 0 && (((uintptr_t)in | (uintptr_t)out) & 15) == 0) {
+    const unsigned b4 = (unsigned)((n / 4 + 255) / 256);
+#define DWF_CA4(NBV)                                                                                            \
+  dwfmg::k_coarse_apply4<NBV><<<b4, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2], C->g.Lc[3], \
+                                                  C->nb, nrhs)
+    switch (C->nb) {
+      case 16: DWF_CA4(16); break;
+      case 24: DWF_CA4(24); break;
+      case 32: DWF_CA4(32); break;
+      default: DWF_CA4(0); break;
+    }
+#undef DWF_CA4
+    return DWF_OK;
+  }
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (C->nb == 32)
     dwfmg::k_coarse_apply<32><<<blocks, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2],

@@ -425,4 +425,53 @@ __global__ void __launch_bounds__(256) k_coarse_apply(float2* out, const float2*
   out[e] = make_float2(re + re2, im + im2);
 }
 
+// The same stencil with four consecutive right-hand sides per thread (nrhs a
+// multiple of 4, vectors 16-byte aligned): each operator element feeds four
+// outputs and the vector loads are 16-byte, so the kernel issues 0.75 loads
+// per complex multiply-add instead of 2.
+template <int NB>
+__global__ void __launch_bounds__(256) k_coarse_apply4(float2* out, const float2* in, const float2* A, int Lc0,
+                                                       int Lc1, int Lc2, int Lc3, int nb_rt, int nrhs) {
+  const int nb = NB > 0 ? NB : nb_rt;
+  const int nq = nrhs >> 2;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = Lc0 * Lc1 * Lc2 * Lc3;
+  if (e >= (long long)nc * nb * nq) return;
+  const int q = (int)(e % nq);
+  const long long t = e / nq;
+  const int j = (int)(t % nb);
+  const int x = (int)(t / nb);
+  const int Lc[4] = {Lc0, Lc1, Lc2, Lc3};
+  float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int d = 0; d < 9; d++) {
+    const int y = coarse_nbr(Lc, x, d);
+    const float2* Ad = A + (((long long)x * 9 + d) * nb + j) * nb;
+    const float4* v = (const float4*)(in + (long long)y * nb * nrhs) + 2 * q;
+#pragma unroll 4
+    for (int k = 0; k < (NB > 0 ? NB : nb); k++) {
+      const float2 a = __ldg(Ad + k);
+      const float4 b0 = __ldg(v + (long long)k * (nrhs >> 1)), b1 = __ldg(v + (long long)k * (nrhs >> 1) + 1);
+      acc0.x = fmaf(a.x, b0.x, acc0.x);
+      acc0.x = fmaf(-a.y, b0.y, acc0.x);
+      acc0.y = fmaf(a.x, b0.y, acc0.y);
+      acc0.y = fmaf(a.y, b0.x, acc0.y);
+      acc0.z = fmaf(a.x, b0.z, acc0.z);
+      acc0.z = fmaf(-a.y, b0.w, acc0.z);
+      acc0.w = fmaf(a.x, b0.w, acc0.w);
+      acc0.w = fmaf(a.y, b0.z, acc0.w);
+      acc1.x = fmaf(a.x, b1.x, acc1.x);
+      acc1.x = fmaf(-a.y, b1.y, acc1.x);
+      acc1.y = fmaf(a.x, b1.y, acc1.y);
+      acc1.y = fmaf(a.y, b1.x, acc1.y);
+      acc1.z = fmaf(a.x, b1.z, acc1.z);
+      acc1.z = fmaf(-a.y, b1.w, acc1.z);
+      acc1.w = fmaf(a.x, b1.w, acc1.w);
+      acc1.w = fmaf(a.y, b1.z, acc1.w);
+    }
+  }
+  float4* o = (float4*)(out + ((long long)x * nb + j) * nrhs) + 2 * q;
+  o[0] = acc0;
+  o[1] = acc1;
+}
+
 }  // namespace dwfmg
