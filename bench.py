@@ -510,10 +510,10 @@ def run_ours(args):
     hop_alg_bytes = Vh * (Ls * 24 * 8 + 72 * 8)
     peaks, peak_kind = measured_peaks()
     achieved = hop_alg_bytes / (hop_ms / 1e3) / 1e9
-    shash = source_hash("paper_2103_05034_gb300/csrc/dhop_impl.cuh")
+    shash = source_hash("paper_2103_05034_gb300/csrc/dhop_impl.cuh", "paper_2103_05034_gb300/csrc/dhop_pair.cuh")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
-                "traffic": profile_traffic(f"hop_kernel_f32_ls{Ls}_{args.workload}", shash),
+                "traffic": profile_traffic(f"hop_kernel_f32_ls{Ls}_v{hop_variant}_{args.workload}", shash),
                 "kernel": hop_variant_label(hop_variant, Ls),
                 "launch_ms": hop_ms, "algorithmic_bytes_per_launch": hop_alg_bytes,
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "source_hash": shash}
