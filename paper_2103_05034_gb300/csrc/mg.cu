@@ -277,7 +277,10 @@ int coarse_ws(dwf_coarse* C, int slot, size_t bytes, void** out) {
 int coarse_apply_dev(dwf_coarse* C, float2* out, const float2* in, int nrhs, cudaStream_t st) {
   const long long n = (long long)C->g.nc * C->nb * nrhs;
   C->ctx->launches++;
-  if ((nrhs & 3) == 0 && (((uintptr_t)in | (uintptr_t)out) & 15) == 0) {
+  // fewer than 32 right-hand sides: a warp of the one-output kernel spans
+  // several operator rows, so four outputs per thread issue fewer loads; from
+  // 32 on, a warp shares one operator element and reads 256 contiguous bytes
+  if ((nrhs & 3) == 0 && nrhs < 32 && (((uintptr_t)in | (uintptr_t)out) & 15) == 0) {
     const unsigned b4 = (unsigned)((n / 4 + 255) / 256);
 #define DWF_CA4(NBV)                                                                                            \
   dwfmg::k_coarse_apply4<NBV><<<b4, 256, 0, st>>>(out, in, C->A32, C->g.Lc[0], C->g.Lc[1], C->g.Lc[2], C->g.Lc[3], \

@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(256) k_coarse_apply(float2* out, const float2*
 // The same stencil with four consecutive right-hand sides per thread (nrhs a
 // multiple of 4, vectors 16-byte aligned): each operator element feeds four
 // outputs and the vector loads are 16-byte, so the kernel issues 0.75 loads
-// per complex multiply-add instead of 2.
+// per complex multiply-add instead of 2 (used below 32 right-hand sides).
 template <int NB>
 __global__ void __launch_bounds__(256) k_coarse_apply4(float2* out, const float2* in, const float2* A, int Lc0,
                                                        int Lc1, int Lc2, int Lc3, int nb_rt, int nrhs) {

@@ -148,7 +148,7 @@ def oracle_coarse_apply(A, v, Lc):
     return out
 
 
-@pytest.mark.parametrize("nrhs", [1, 3, 32])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 32])
 def test_coarse_apply(coarse_case, nrhs):
     L, Ls, block, nb, mf, U, ctx, basis, A, Aflat = coarse_case
     C = ops.coarse_build(ctx, fulls_dev(basis, L, F64), nb, nb // 2, block, mf)
