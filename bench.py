@@ -587,12 +587,19 @@ def run_ours(args):
     e2e_steps = min(args.steps, args.e2e_steps)
     need = 2 * n_full * 8
     avail = host_mem_available()
-    pinned = avail > 3 * need  # pinned buffers only with ample host memory to spare
-    bh = torch.empty(n_full, dtype=torch.float64, pin_memory=pinned)
+    # page-locked buffers (full-speed DMA over the CPU-GPU link) when at least
+    # 64 GB of host memory stays free beside them; pageable otherwise
+    pinned = avail > need + 64e9
+    try:
+        bh = torch.empty(n_full, dtype=torch.float64, pin_memory=pinned)
+        xh = torch.zeros(n_full, dtype=torch.float64, pin_memory=pinned)
+    except RuntimeError:
+        pinned = False
+        bh = torch.empty(n_full, dtype=torch.float64)
+        xh = torch.zeros(n_full, dtype=torch.float64)
     bh.copy_(bd)  # the same source, now in host memory
     del bd, xd
     torch.cuda.empty_cache()
-    xh = torch.zeros(n_full, dtype=torch.float64, pin_memory=pinned)
     step(xh, bh)  # warm (workspace for host buffers)
     ops.dwf_reset_counters(ctx)
     torch.cuda.synchronize()
