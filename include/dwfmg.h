@@ -544,7 +544,8 @@ int mg_setup(dwf_ctx* ctx, const dwf_mg_params* params, const void* eta, dwf_mg*
 int mg_destroy(dwf_mg* mg);
 /* Copy the FP32 basis (nbasis full fields) to out (host or device). */
 int mg_export_basis(const dwf_mg* mg, void* out);
-/* The setup's coarse operator (owned by the setup). */
+/* The setup's coarse operator (owned by the setup); for a hybrid setup
+ * (mg_setup_hybrid) the level-2 operator. */
 dwf_coarse* mg_coarse(dwf_mg* mg);
 /* The Chebyshev smoother S_cheb (Sec. 3.2, Eqs. 24-25, with M = M^dag = H_DW)
  * and the V(1,1) preconditioner (Sec. 3.3, Eqs. 26-28, x0 = 0) applied to one
