@@ -1090,38 +1090,58 @@ def run_rows(args):
     ctx.close()
 
 
-def run_hybrid_vcycle(args):
-    """Profile mode `--kernel hybrid_vcycle`: the hybrid multigrid (Algorithm F,
-    HYBRID_PARAMS) set up on the workload, one warm-up V-cycle, then one
+def run_vcycle(args):
+    """Profile modes `--kernel mg_vcycle` (HDCR, MG_PARAMS, or MG_PARAMS_LARGE
+    above 2^24 4D sites) and `--kernel hybrid_vcycle` (Algorithm F,
+    HYBRID_PARAMS): the setup on the workload, one warm-up V-cycle, then one
     V-cycle inside the NVTX range "vcycle" (for `ncu --nvtx --nvtx-include
-    vcycle/`); prints its host-clock time."""
+    vcycle/`); prints the setup and V-cycle host-clock times."""
     import torch
 
     from paper_2103_05034_gb300 import ops
-    from paper_2103_05034_gb300._lib import COARSE_CG, COARSE_RB, F32
+    from paper_2103_05034_gb300._lib import COARSE_CG, COARSE_DEFLATED, COARSE_RB, F32, SUBSPACE_RECURSIVE
 
     w, U, b = build_workload(args.workload, 0)
     L, Ls, mf = w["L"], w["Ls"], w["mf"]
     ctx = ops.Context(L, Ls, w["M5"], U)
     del U
     ops.dwf_autotune(ctx, F32, 10)
-    p = dict(HYBRID_PARAMS)
     gen = torch.Generator(device="cuda").manual_seed(77)
     v0 = torch.randn(2 * ctx.half_numel(), generator=gen, device="cuda", dtype=torch.float64)
     lmax = ops.dwf_power_max(ctx, v0, mf, 100, F32) * 1.10
     del v0
-    prm = ops.mg_params(p["block"], 0, mf, smooth=(p["smooth"][0], lmax, p["smooth"][2]), coarse_tol=p["coarse_tol"],
-                        coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"], maxiter=p["maxiter"],
-                        coarse_solver={"cg": COARSE_CG, "rb": COARSE_RB}[p["coarse_solver"]])
-    hp = ops.hybrid_params(p["block"], p["nbasis4"], p["nbasis1"], mass4=p["mass4"], filter4=p["filter4"],
-                           filter1=(p["filter1"][0], lmax, p["filter1"][2]),
-                           smooth1=(p["smooth1"][0], lmax, p["smooth1"][2]), kcycle=p["kcycle"])
-    nc1 = int(np.prod([L[m] // p["block"][m] for m in range(4)]))
+    cs_of = {"cg": COARSE_CG, "rb": COARSE_RB, "deflated": COARSE_DEFLATED}
     gen = torch.Generator(device="cuda").manual_seed(synth.SEED_BASIS)
-    eta4 = torch.randn(2 * 2 * ctx.Vh * 12 * p["nbasis4"], generator=gen, device="cuda", dtype=torch.float64)
-    eta1 = torch.randn(2 * nc1 * p["nbasis4"] * Ls * p["nbasis1"], generator=gen, device="cuda", dtype=torch.float64)
-    G = ops.HybridMG(ctx, prm, hp, eta4, eta1)
-    del eta4, eta1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if args.kernel == "hybrid_vcycle":
+        p = dict(HYBRID_PARAMS)
+        prm = ops.mg_params(p["block"], 0, mf, smooth=(p["smooth"][0], lmax, p["smooth"][2]),
+                            coarse_tol=p["coarse_tol"], coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"],
+                            maxiter=p["maxiter"], coarse_solver=cs_of[p["coarse_solver"]])
+        hp = ops.hybrid_params(p["block"], p["nbasis4"], p["nbasis1"], mass4=p["mass4"], filter4=p["filter4"],
+                               filter1=(p["filter1"][0], lmax, p["filter1"][2]),
+                               smooth1=(p["smooth1"][0], lmax, p["smooth1"][2]), kcycle=p["kcycle"])
+        nc1 = int(np.prod([L[m] // p["block"][m] for m in range(4)]))
+        eta4 = torch.randn(2 * 2 * ctx.Vh * 12 * p["nbasis4"], generator=gen, device="cuda", dtype=torch.float64)
+        eta1 = torch.randn(2 * nc1 * p["nbasis4"] * Ls * p["nbasis1"], generator=gen, device="cuda",
+                           dtype=torch.float64)
+        G = ops.HybridMG(ctx, prm, hp, eta4, eta1)
+        del eta4, eta1
+    else:
+        p = dict(MG_PARAMS_LARGE if int(np.prod(L)) > (1 << 24) else MG_PARAMS)
+        cs = cs_of[p["coarse_solver"]]
+        prm = ops.mg_params(p["block"], p["nbasis"], mf, subspace_mode=SUBSPACE_RECURSIVE,
+                            lambda_lo=p["lambda_lo"], lambda_max=lmax, filter_order=p["filter_order"],
+                            delta=p["delta"], smooth=(p["smooth"][0], lmax, p["smooth"][2]),
+                            coarse_tol=p["coarse_tol"], coarse_maxiter=p["coarse_maxiter"], nkrylov=p["nkrylov"],
+                            maxiter=p["maxiter"], coarse_solver=cs,
+                            deflation=p["deflation"] if cs == COARSE_DEFLATED else (0, 0, 0, 0.0))
+        eta = torch.randn(2 * ctx.half_numel(), generator=gen, device="cuda", dtype=torch.float64)
+        G = ops.MG(ctx, prm, eta)
+        del eta
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
     r = torch.randn(2 * ctx.half_numel(), generator=gen, device="cuda", dtype=torch.float32)
     out = torch.zeros_like(r)
     ops.mg_precondition(G, out, r)
@@ -1131,7 +1151,8 @@ def run_hybrid_vcycle(args):
     ops.mg_precondition(G, out, r)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    print(json.dumps({"kernel": "hybrid_vcycle", "workload": args.workload, "vcycle_s": time.perf_counter() - t0}))
+    print(json.dumps({"kernel": args.kernel, "workload": args.workload, "setup_s": setup_s,
+                      "vcycle_s": time.perf_counter() - t0}))
     G.close()
     ctx.close()
     return 0
@@ -1231,7 +1252,7 @@ def main(argv=None):
                          "(about four minutes)")
     ap.add_argument("--kernel", default=None,
                     help="profile mode: dhop_f32, dhop_f64, dhop_f16, mpcdagmpc_f32, coarse_tf32 or coarse_f32 alone, "
-                         "or hybrid_vcycle (one Algorithm F V-cycle in an NVTX range)")
+                         "or mg_vcycle / hybrid_vcycle (one HDCR / Algorithm F V-cycle in an NVTX range)")
     ap.add_argument("--rows", action="store_true",
                     help="measure every step of the hot path alone (one JSON line per step)")
     ap.add_argument("--hop-variant", type=int, default=None,
@@ -1244,8 +1265,8 @@ def main(argv=None):
     if args.kernel:
         if args.kernel.startswith("coarse_"):
             return run_coarse_kernel(args)
-        if args.kernel == "hybrid_vcycle":
-            return run_hybrid_vcycle(args)
+        if args.kernel in ("hybrid_vcycle", "mg_vcycle"):
+            return run_vcycle(args)
         return run_kernel(args)
     if args.impl == "reference":
         return run_reference(args)

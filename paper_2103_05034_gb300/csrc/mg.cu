@@ -173,8 +173,25 @@ int chiral(dwf_ctx* c, void* out, const void* in, int sign, int prec, int nrhs, 
 int block_inner(dwf_ctx* c, const BlockGeom& g, const void* X, int nx, const void* Y, int ny, int prec,
                 double2* out, long long out_bstride, int out_ld, int d, int accumulate, cudaStream_t st) {
   const long long fs = full_elems(c);
-  dim3 grid(g.nc, (nx + 31) / 32, (ny + 31) / 32);
   c->launches++;
+  if (ny == 1 && d == 0 && !accumulate && nx <= 64 && (prec == DWF_F32 || prec == DWF_F64)) {
+    // restriction of one field: nx dot products per block in one pass
+#define DWF_RESTRICT(PV, NXV)                                                                                  \
+  dwfmg::k_block_restrict<PV, NXV><<<g.nc, 256, 0, st>>>((const typename Prec<PV>::S*)X, fs, nx,               \
+                                                         (const typename Prec<PV>::S*)Y, out, out_bstride, out_ld, g)
+    if (prec == DWF_F32) {
+      if (nx <= 8) DWF_RESTRICT(DWF_F32, 8);
+      else if (nx <= 32) DWF_RESTRICT(DWF_F32, 32);
+      else DWF_RESTRICT(DWF_F32, 64);
+    } else {
+      if (nx <= 8) DWF_RESTRICT(DWF_F64, 8);
+      else if (nx <= 32) DWF_RESTRICT(DWF_F64, 32);
+      else DWF_RESTRICT(DWF_F64, 64);
+    }
+#undef DWF_RESTRICT
+    return DWF_OK;
+  }
+  dim3 grid(g.nc, (nx + 31) / 32, (ny + 31) / 32);
   switch (prec) {
     case DWF_F64:
       dwfmg::k_block_inner<DWF_F64><<<grid, 256, 0, st>>>((const double2*)X, fs, nx, (const double2*)Y, fs, ny,
@@ -218,8 +235,8 @@ void dwf_ws_release(dwf_ctx* c, int slot) {
 
 namespace {
 
-// Block Cholesky-QR on nb FP32 full fields in place (FP64 Gram matrices,
-// factorisation and update arithmetic): the basis orthonormalisation of the
+// Block Cholesky-QR on nb FP32 full fields in place (FP64 Gram sums and
+// factorisation, FP32 update arithmetic): the basis orthonormalisation of the
 // multigrid setup without an FP64 copy of the basis.  Three passes, the first
 // with the Gram matrix shifted by 1e-5 of its largest diagonal entry (shifted
 // Cholesky-QR: the filtered vectors can be dependent to FP32 precision on a

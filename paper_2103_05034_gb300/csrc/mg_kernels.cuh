@@ -154,6 +154,69 @@ __global__ void __launch_bounds__(256) k_block_inner(const typename Prec<P>::S* 
   }
 }
 
+// Restriction of one field: out[xc][j] = sum over block xc of conj(X_j) Y,
+// for nx <= 64 basis fields (the Gram-matrix kernel above would compute 32
+// columns of which one is wanted).  One CTA per block, eight warps; warp w
+// owns the basis fields j = w*J .. w*J+J-1 (J = NX/8) and walks all of the
+// block's elements with its 32 lanes (coalesced), so every basis element is
+// read once; sums of 16 terms in the storage's arithmetic type are added in
+// FP64 and reduced across the warp in FP64.
+template <int P, int NX>
+__global__ void __launch_bounds__(256) k_block_restrict(const typename Prec<P>::S* X, long long xstride, int nx,
+                                                        const typename Prec<P>::S* Y, double2* out,
+                                                        long long out_bstride, int out_ld, BlockGeom g) {
+  typedef typename Prec<P>::R R;
+  constexpr int J = NX / 8;
+  const int xc = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j0 = w * J;
+  double2 acc[J];
+  cpx<R> part[J];
+#pragma unroll
+  for (int j = 0; j < J; j++) {
+    acc[j] = make_double2(0, 0);
+    part[j] = cmake<R>(0, 0);
+  }
+  const int row_len = 12 * g.Ls;
+  const int nel = g.b4 * row_len;
+  int cnt = 0;
+  for (int e = lane; e < nel; e += 32) {
+    const int i = e / row_len, q = e - i * row_len;
+    bool face;
+    const long long off = block_site_offset(g, xc, i, 0, &face) + q;
+    const cpx<R> y = ld_c(Y + off);
+#pragma unroll
+    for (int j = 0; j < J; j++) {
+      if (j0 + j < nx) {
+        const cpx<R> a = ld_c(X + (long long)(j0 + j) * xstride + off);
+        part[j].re = fma(a.re, y.re, part[j].re);
+        part[j].re = fma(a.im, y.im, part[j].re);
+        part[j].im = fma(a.re, y.im, part[j].im);
+        part[j].im = fma(-a.im, y.re, part[j].im);
+      }
+    }
+    if (++cnt == 16) {
+      cnt = 0;
+#pragma unroll
+      for (int j = 0; j < J; j++) {
+        acc[j].x += (double)part[j].re;
+        acc[j].y += (double)part[j].im;
+        part[j] = cmake<R>(0, 0);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < J; j++) {
+    double x = acc[j].x + (double)part[j].re, y = acc[j].y + (double)part[j].im;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0 && j0 + j < nx) out[xc * out_bstride + (long long)(j0 + j) * out_ld] = make_double2(x, y);
+  }
+}
+
 // Y_k(site) = sum_j X_j(site) M[xc][j][k] over every site of every block:
 // prolongation (M = coarse vector) and Cholesky-QR updates (M = R^-1).
 // One CTA per block; M staged in shared memory (nx * ny <= 1024).
@@ -205,15 +268,17 @@ __global__ void __launch_bounds__(256) k_block_combine(typename Prec<PY>::S* Y, 
 // (x_k <- sum_{j <= k} x_j Rinv[xc][j][k], Rinv upper triangular within the
 // group, rows and columns offset by g0 in the nb x nb matrix): each thread
 // owns one element of the block, reads it from all n fields first and then
-// writes the n results, so no second copy of the basis is needed.  FP64
-// arithmetic on FP32 storage.
+// writes the n results, so no second copy of the basis is needed.  FP32
+// arithmetic, the precision the fields are stored in (the Gram matrices and
+// their factorisation, which decide the result's orthogonality, stay FP64).
 static __global__ void __launch_bounds__(256) k_block_update_inplace(float2* X, long long xstride, int n, int g0, int nb,
                                                               const double2* Rinv, BlockGeom g) {
-  __shared__ double2 sm[32 * 32];
+  __shared__ float2 sm[32 * 32];
   const int xc = blockIdx.x;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int j = e / n, k = e - j * n;
-    sm[e] = Rinv[(long long)xc * nb * nb + (long long)(g0 + j) * nb + g0 + k];
+    const double2 r = Rinv[(long long)xc * nb * nb + (long long)(g0 + j) * nb + g0 + k];
+    sm[e] = make_float2((float)r.x, (float)r.y);
   }
   __syncthreads();
   const int row_len = 12 * g.Ls;
@@ -229,15 +294,17 @@ static __global__ void __launch_bounds__(256) k_block_update_inplace(float2* X, 
 #pragma unroll
     for (int k = 0; k < 32; k++) {
       if (k >= n) break;
-      double re = 0, im = 0;
+      float re = 0.f, im = 0.f;
 #pragma unroll
       for (int j = 0; j < 32; j++) {
         if (j > k) break;
-        const double2 m = sm[j * n + k];
-        re += (double)v[j].x * m.x - (double)v[j].y * m.y;
-        im += (double)v[j].x * m.y + (double)v[j].y * m.x;
+        const float2 m = sm[j * n + k];
+        re = fmaf(v[j].x, m.x, re);
+        re = fmaf(-v[j].y, m.y, re);
+        im = fmaf(v[j].x, m.y, im);
+        im = fmaf(v[j].y, m.x, im);
       }
-      X[(long long)k * xstride + off] = make_float2((float)re, (float)im);
+      X[(long long)k * xstride + off] = make_float2(re, im);
     }
   }
 }
