@@ -616,6 +616,8 @@ def run_ours(args):
            "note": f"rbcg_solve on {'pinned' if pinned else 'pageable'} host b and x: H2D of b and D2H of x "
                    f"inside the call, host clock"}
     del bh, xh
+    if pinned and hasattr(torch._C, "_host_emptyCache"):
+        torch._C._host_emptyCache()  # hand the page-locked buffers back to the host
     ctx.close()
     torch.cuda.empty_cache()
 
