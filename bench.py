@@ -1161,7 +1161,7 @@ def run_vcycle(args):
 
 
 def run_kernel(args):
-    """Kernel-only loop for profiling: `--kernel dhop_f32|dhop_f64|dhop_f16|mpcdagmpc_f32`
+    """Kernel-only loop for profiling: `--kernel dhop_f32|dhop_f64|dhop_f16|mpcdagmpc_f32|force_f32`
     at the workload's size, warmup + steps launches, no solver."""
     import torch
 
@@ -1186,8 +1186,13 @@ def run_kernel(args):
                           dtype=torch.float32).to({F64: torch.float64, F32: torch.float32,
                                                    F16S: torch.float16}[prec])
     out = torch.zeros_like(inp)
+    if kind == "force":  # the force workload: four pseudofermions (X drawn on the device)
+        gen = torch.Generator(device="cuda").manual_seed(synth.SEED_SOURCE)
+        X = torch.randn(4 * ctx.half_numel(), generator=gen, device="cuda", dtype=torch.float32).to(inp.dtype)
+        force = torch.zeros(int(np.prod(L)) * 4 * 9 * 2, dtype=torch.float64, device="cuda")
     fn = {"dhop": lambda: ops.dwf_dhop(ctx, out, inp, 0),
-          "mpcdagmpc": lambda: ops.dwf_mpcdag_mpc(ctx, out, inp, w["mf"])}[kind]
+          "mpcdagmpc": lambda: ops.dwf_mpcdag_mpc(ctx, out, inp, w["mf"]),
+          "force": lambda: ops.dwf_force(ctx, force, X, [0.01, 0.05, 0.2, 1.0])}[kind]
     if args.sweep_variants and kind == "dhop":
         # every tuning variant, one launch at a time with an L2 flush before each
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -1253,7 +1258,8 @@ def main(argv=None):
                     help="add Algorithm F (hybrid three-level multigrid) to the 24^3x48x24 comparison "
                          "(about four minutes)")
     ap.add_argument("--kernel", default=None,
-                    help="profile mode: dhop_f32, dhop_f64, dhop_f16, mpcdagmpc_f32, coarse_tf32 or coarse_f32 alone, "
+                    help="profile mode: dhop_f32, dhop_f64, dhop_f16, mpcdagmpc_f32, force_f32 (dwf_force, four "
+                         "pseudofermions), coarse_tf32 or coarse_f32 alone, "
                          "or mg_vcycle / hybrid_vcycle (one HDCR / Algorithm F V-cycle in an NVTX range)")
     ap.add_argument("--rows", action="store_true",
                     help="measure every step of the hot path alone (one JSON line per step)")

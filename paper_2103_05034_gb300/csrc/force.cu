@@ -108,8 +108,12 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
   const int tid = threadIdx.x, sl = tid / LS, s = tid - sl * LS;
   for (int i = tid; i < SB * 8 * 9; i += LS * SB) AB[i] = make_double2(0.0, 0.0);
   // (the first site_sum's barrier orders these stores before its additions)
-  const int p = blockIdx.y;
-  const int h = blockIdx.x * SB + sl;
+  // the two parities of a block of sites are neighbouring CTAs, so that what
+  // one reads as its own X, Y the other reads as neighbours while it is in L2
+  // (parity-major order read every field twice from DRAM)
+  const int p = blockIdx.x & 1;
+  const int blk = blockIdx.x >> 1;
+  const int h = blk * SB + sl;
   const bool active = h < Vh;
   const int hh = active ? h : 0;
   const int Lxh = L0 / 2;
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(LS* SB) k_force(double2* force, const typename
   // G_mu = TA(U A - B U^dag), one thread per (site, mu)
   for (int t = tid; t < SB * 4; t += LS * SB) {
     const int sl2 = t >> 2, mu = t & 3;
-    const int h2 = blockIdx.x * SB + sl2;
+    const int h2 = blk * SB + sl2;
     if (h2 >= Vh) continue;
     int r2 = h2 / Lxh;
     const int xh2 = h2 - r2 * Lxh;
@@ -232,7 +236,7 @@ int launch_force(dwf_ctx* c, double2* force, const void* Xe, const void* Xo, con
 #define DWF_FORCE_CASE(LSV)                                                                                  \
   case LSV: {                                                                                                \
     constexpr int SB = LSV >= 16 ? 8 : 64 / LSV;                                                             \
-    dim3 grid((unsigned)((c->g.Vh + SB - 1) / SB), 2);                                                       \
+    dim3 grid((unsigned)(2 * ((c->g.Vh + SB - 1) / SB)));                                                    \
     k_force<P, LSV, SB><<<grid, LSV * SB, 0, st>>>(force, (const S*)Xe, (const S*)Xo, (const S*)Ye,         \
                                                    (const S*)Yo, fs, npf, le, lo, c->g.L[0], c->g.L[1],      \
                                                    c->g.L[2], c->g.L[3], (int)c->g.Vh, coef);                \
