@@ -201,8 +201,8 @@ int dwf_hdw(dwf_ctx* ctx, void* out, const void* in, double mf, int prec,
 
 /* ------------------------------------------------------------------ BLAS-1 */
 
-/* Global reductions with FP64 accumulation over n complex numbers of the
- * given precision: *result = sum |a|^2, or (re, im) of sum conj(a) b.
+/* Global reductions of the Krylov solvers (Sec. 5.1, Sec. 3.3) with FP64
+ * accumulation over n complex numbers of the given precision: *result = sum |a|^2, or (re, im) of sum conj(a) b.
  * `result` is host memory; the call synchronises `stream`. */
 int dwf_norm2(dwf_ctx* ctx, double* result, const void* a, int64_t n, int prec, void* stream);
 int dwf_cdot(dwf_ctx* ctx, double* result2, const void* a, const void* b, int64_t n,
@@ -413,10 +413,11 @@ int block_orthonormalise(dwf_ctx* ctx, void* basis, int nb, int nplus, const int
 int coarse_build(dwf_ctx* ctx, const void* basis, int nb, int nplus, const int block[4], double mf,
                  int prec, dwf_coarse** coarse, void* stream);
 int coarse_destroy(dwf_coarse* coarse);
-/* Copy the FP64 operator to A (host or device, complex128 [nc][9][nb][nb],
- * row j, column k) and/or its shape to dims = {Lc_x, Lc_y, Lc_z, Lc_t, nb}. */
+/* Copy the FP64 operator of Eq. (18) (Sec. 3.1) to A (host or device,
+ * complex128 [nc][9][nb][nb], row j, column k) and/or its shape to dims = {Lc_x, Lc_y, Lc_z, Lc_t, nb}. */
 int coarse_export(const dwf_coarse* coarse, void* A, int* dims);
-/* out(x) = sum_d A_d(x) in(x+d) for nrhs coarse vectors, FP32 complex, layout
+/* The 9-point stencil of Eq. (18) (Sec. 3.1) on nrhs coarse vectors:
+ * out(x) = sum_d A_d(x) in(x+d), FP32 complex, layout
  * [nc][nb][nrhs] (coarse site lexicographic in Lc, basis index, rhs).
  * prec DWF_F32: CUDA cores, FP32 arithmetic (any nb, nrhs).  prec DWF_TF32:
  * 5th-generation tensor cores (tcgen05.mma kind::tf32, inputs rounded to TF32,
@@ -484,12 +485,13 @@ int coarse_solve_rb(dwf_coarse* coarse, void* e, const void* r, double tol, int 
  * Synchronises. */
 int coarse_deflate(dwf_coarse* coarse, const void* v0, int nev, int nk, int order, double lam_lo,
                    double lam_max, double* theta, void* stream);
-/* The deflation space of coarse_deflate: *nev vectors (FP32 [nev][nc][nb],
+/* The coarse deflation space of Sec. 3.5 (coarse_deflate): *nev vectors (FP32 [nev][nc][nb],
  * copied to V, host or device, when V is not NULL) and 1/theta_i (host). */
 int coarse_export_deflation(const dwf_coarse* coarse, void* V, double* theta_inv, int* nev);
 /* Restriction P^dag (out: FP32 coarse [nc][nb][nrhs]) and prolongation P
  * (out: nrhs full fields, += when accumulate) with a block basis of nb full
- * fields of precision prec (DWF_F64 or DWF_F32). */
+ * fields of precision prec (DWF_F64 or DWF_F32): the block projectors of
+ * Sec. 3.1 that Eqs. (26)-(28) use. */
 int dwf_restrict(dwf_ctx* ctx, void* out, const void* in, const void* basis, int nb,
                  const int block[4], int nrhs, int prec, void* stream);
 int dwf_prolong(dwf_ctx* ctx, void* out, const void* in, const void* basis, int nb,
@@ -542,7 +544,7 @@ typedef struct dwf_mg_params {
  * of H_DW.  Synchronises.  The context must outlive the setup. */
 int mg_setup(dwf_ctx* ctx, const dwf_mg_params* params, const void* eta, dwf_mg** mg, void* stream);
 int mg_destroy(dwf_mg* mg);
-/* Copy the FP32 basis (nbasis full fields) to out (host or device). */
+/* Copy the FP32 basis (nbasis full fields; Sec. 3.4) to out (host or device). */
 int mg_export_basis(const dwf_mg* mg, void* out);
 /* The setup's coarse operator (owned by the setup); for a hybrid setup
  * (mg_setup_hybrid) the level-2 operator. */
@@ -609,14 +611,15 @@ typedef struct dwf_hybrid_params {
  * are not used.  The solve runs without CUDA-graph replay.  Synchronises. */
 int mg_setup_hybrid(dwf_ctx* ctx, const dwf_mg_params* params, const dwf_hybrid_params* hybrid,
                     const void* eta4, const void* eta1, dwf_mg** mg, void* stream);
-/* Copies of the hybrid setup's parts (host or device out):
+/* Copies of the hybrid setup's parts (Algorithm F, Sec. 4; host or device out):
  *   what 0: the 4D basis, FP64 [2][Vh][12][nbasis4];
  *   what 1: B, FP64 [nc1][9][nbasis4][nbasis4] (the coarse_export layout);
  *   what 2: the level-2 basis, FP32 [nc1][nbasis4][Ls][nbasis1];
  *   what 3: the level-2 stencil, FP64 [nc1][9][nbasis1][nbasis1].
  * DWF_EINVAL for a setup that is not hybrid. */
 int mg_hybrid_export(const dwf_mg* mg, int what, void* out);
-/* The hybrid setup's level operators on device vectors (stream-ordered):
+/* The hybrid setup's level operators (Algorithm F, Sec. 4) on device vectors
+ * (stream-ordered):
  *   op 0: out = M_1 in, nvec level-1 vectors;  op 1: out = H_1 in;
  *   op 2: out = P1^dag in (in: nvec FP32 full fine fields; out: level-1);
  *   op 3: out = P1 in (in: level-1; out: nvec FP32 full fields);
