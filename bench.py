@@ -271,6 +271,10 @@ MG_PARAMS_LARGE = dict(MG_PARAMS, deflation=(128, 256, 10, 0.05))
 HYBRID_PARAMS = dict(block=(2, 2, 2, 2), nbasis4=24, nbasis1=32, mass4=-0.95, filter4=(4.0, 60.0, 60),
                      filter1=(0.5, None, 40), smooth=(0.05, None, 40), smooth1=(0.05, None, 4), kcycle=2,
                      coarse_tol=0.02, coarse_maxiter=5000, nkrylov=32, maxiter=300, coarse_solver="rb")
+# At 24^3 x 48 x 24 a level-1 smoother of order 8 and the level-2 CG to 0.05
+# (the paper's looser coarse tolerance) take the solve from 103 outer
+# iterations (21012 level-2 iterations) to 66 (5066)
+HYBRID_PARAMS_LARGE = dict(HYBRID_PARAMS, smooth1=(0.05, None, 8), coarse_tol=0.05)
 
 
 def mg_vs_fp64(ctx, w, bd, tol, params=MG_PARAMS, eta_seed=None):
@@ -693,7 +697,8 @@ def run_ours(args):
                 if args.hybrid_large:
                     try:
                         line["hybrid_vs_fp64_large"] = hybrid_vs_fp64(cl, wl, bl, args.tol,
-                                                                      line["mg_vs_fp64_large"]["fp64_rbcg_s"])
+                                                                      line["mg_vs_fp64_large"]["fp64_rbcg_s"],
+                                                                      HYBRID_PARAMS_LARGE)
                     except Exception as e:
                         line["hybrid_vs_fp64_large"] = {"error": str(e)}
                 del bl
